@@ -1,0 +1,80 @@
+"""One alternating time step of the SDD mesh generator -- oracle, TEST INFRASTRUCTURE.
+
+The domain decomposition solution (Sec. 3.6): with the monitor frozen on the current mesh
+(Sec. 3.2), the interface nodes are estimated stochastically (Sec. 3.4), the estimates are
+the Dirichlet data of independent subdomain solves (Sec. 3.5), and the new mesh is the union
+of interface values, subdomain interiors and the physical boundary.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from workloads import MONITOR_NODAL
+from .layout import interface_nodes, subdomains
+from .mc import interface_mc
+from .monitor import monitor_on_grid, wrap_copy
+from .solve import solve_box
+
+
+def monitor_on_mesh(prob, x, y, t, omega_nodal=None):
+    if prob.monitor_kind == MONITOR_NODAL:
+        if omega_nodal is None:
+            raise ValueError("nodal monitor needs omega")
+        om = np.asarray(omega_nodal, dtype=np.float64)
+        return wrap_copy(om) if prob.periodic else om
+    return monitor_on_grid(prob.monitor_kind, prob.monitor_params, x, y, t, prob.periodic,
+                            prob.Lx, prob.Ly)
+
+
+def scatter(prob, nodes, est):
+    """New-mesh arrays holding the Dirichlet data of every subdomain rim.
+
+    Dirichlet: the physical boundary keeps the identity mesh (Lx xi, Ly eta); interface
+    nodes take the estimates.  Periodic: interface nodes take the estimates and the wrap
+    column/row carries the period offset, x(1, eta) = x(0, eta) + Lx, y(xi, 1) = y(xi, 0) + Ly.
+    Nodes that are neither are left as NaN (they are subdomain interiors).
+    """
+    nx, ny = prob.nx, prob.ny
+    bx = np.full((ny, nx), np.nan)
+    by = np.full((ny, nx), np.nan)
+    if not prob.periodic:
+        xi = np.arange(nx) / (nx - 1)
+        eta = np.arange(ny) / (ny - 1)
+        bx[0, :] = prob.Lx * xi; bx[-1, :] = prob.Lx * xi
+        by[0, :] = 0.0; by[-1, :] = prob.Ly
+        bx[:, 0] = 0.0; bx[:, -1] = prob.Lx
+        by[:, 0] = prob.Ly * eta; by[:, -1] = prob.Ly * eta
+    for (i, j), (vx, vy) in zip(nodes, est):
+        bx[j, i] = vx
+        by[j, i] = vy
+        if prob.periodic:
+            if i == 0:
+                bx[j, nx - 1] = vx + prob.Lx; by[j, nx - 1] = vy
+            if j == 0:
+                bx[ny - 1, i] = vx; by[ny - 1, i] = vy + prob.Ly
+            if i == 0 and j == 0:
+                bx[ny - 1, nx - 1] = vx + prob.Lx; by[ny - 1, nx - 1] = vy + prob.Ly
+    return bx, by
+
+
+def subdomain_solves(prob, omega, bx, by, xn, yn):
+    """Fill every subdomain interior of (bx, by) by its backward-Euler solve (Sec. 3.5)."""
+    out_x, out_y = bx.copy(), by.copy()
+    for (i0, i1, j0, j1) in subdomains(prob.nx, prob.ny, prob.px, prob.py):
+        xs, ys, order = solve_box(omega, bx, by, xn, yn, i0, i1, j0, j1, prob.dt, prob.tau,
+                                  prob.form)
+        for P, (i, j) in enumerate(order):
+            out_x[j, i] = xs[P]
+            out_y[j, i] = ys[P]
+    return out_x, out_y
+
+
+def step(prob, x, y, t, tstep, omega_nodal=None, real=np.float64):
+    """x^n -> x^{n+1}.  Returns dict with the new mesh, interface estimates, SE, paths, steps."""
+    omega = monitor_on_mesh(prob, x, y, t, omega_nodal)
+    nodes = interface_nodes(prob.nx, prob.ny, prob.px, prob.py, prob.periodic)
+    est, se, n_used, steps = interface_mc(prob, x, y, omega, nodes, tstep, real)
+    bx, by = scatter(prob, nodes, est)
+    xn1, yn1 = subdomain_solves(prob, omega, bx, by, x, y)
+    return dict(x=xn1, y=yn1, est=est, se=se, n_used=n_used, steps=steps, omega=omega,
+                nodes=nodes)
