@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Benchmark of the SDD mesh generator's hot path on GB300.
+
+Workload (default): the 257x257 grid split 4x4 (1521 interface nodes), moving-front monitor
+u = tanh(50 (r - 0.25 - 0.1 t)), omega = sqrt(1 + 50 |grad u|^2), tau = 1e-2, dt = 1e-3,
+K = 100 substeps, paths stepped in FP32 with FP64 estimator sums, every interface node
+estimated to SE <= 1e-4 (adaptive: first chunk 1e5 paths), then the 16 backward-Euler
+subdomain solves.  One benchmark step = one alternating time step (sdd_step): monitor on
+the mesh, interface Monte Carlo, subdomain solves, new mesh.  Synthetic inputs only.
+
+Prints one JSON line.  value = interface-node estimates/s at SE <= 1e-4 over all ranks;
+path-steps/s, the roofline of the path kernel (CUDA events inside the library, on its
+stream), the end-to-end rate through the C ABI with host buffers, sampled clocks and the
+oracle timed on the host cores are reported beside it.  Multi-GPU (torchrun): every rank
+runs its own independent problem (seed + rank), no collective on the data path: weak
+scaling, max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "interface-node estimates/s & path-steps/s at SE≤1e-4; % FP32 peak; p99 latency"
+UNIT = "interface-node estimates/s"
+# Irreducible 32-bit lane operations of one FP32 path-step (Philox4x32-10, three uniforms,
+# Box-Muller, bilinear monitor gather, Euler-Maruyama update, endpoint and bridge tests, loop
+# control); itemised with the roofline in the design notes.
+OPS_PER_PATH_STEP = 230
+SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_OPS = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6  # lane-ops/s
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "kahan"])
+    ap.add_argument("--se-target", type=float, default=1e-4)
+    ap.add_argument("--paths", type=int, default=100000)
+    ap.add_argument("--max-paths", type=int, default=1 << 25)
+    ap.add_argument("--periodic", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    import workloads as W
+    prec = {"fp32": W.PREC_FP32_ACC64, "fp64": W.PREC_FP64, "kahan": W.PREC_FP32_KAHAN}[args.precision]
+    p = W.c1_front(prec, periodic=args.periodic)
+    return p.replace(se_target=args.se_target, paths_per_node=args.paths,
+                     max_paths_per_node=max(args.max_paths, args.paths), seed=p.seed + rank)
+
+
+def config_of(p, M):
+    return {"workload": f"{p.name}: {p.nx}x{p.ny} grid, {p.px}x{p.py} subdomains, moving-front monitor, "
+                        f"SE<=1e-4 per interface node",
+            "grid": [p.nx, p.ny], "subdomains": [p.px, p.py], "interface_nodes": M,
+            "periodic": p.periodic, "se_target": p.se_target, "paths_first_chunk": p.paths_per_node,
+            "max_paths_per_node": p.max_paths_per_node, "substeps": p.substeps, "tau": p.tau, "dt": p.dt,
+            "path_precision": {0: "fp64", 1: "fp32 (fp64 sums)", 2: "fp32 (kahan fp32 sums)"}[p.precision],
+            "l2": "256 MiB buffer written between timed steps (inputs are ~1 MB)"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(index)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [v.strip() for v in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
+    """The oracle (C core, OpenMP over nodes, all host cores) on a bounded sample of the same
+    workload: a spread of interface nodes, first time step, FP32 paths.  Converted to
+    interface-node estimates/s with the path-steps one estimate at SE <= target needs."""
+    import numpy as np
+
+    import oracle
+    from oracle import _clib, mc
+    from oracle.layout import interface_nodes
+    from oracle.step import monitor_on_mesh
+    import workloads as W
+
+    oracle.build()
+    x, y = W.identity_mesh(prob)
+    om = monitor_on_mesh(prob, x, y, prob.t0)
+    real = np.float64 if prob.precision == W.PREC_FP64 else np.float32
+    inp = mc.prepare(prob, x, y, om, 0, real)
+    nodes = interface_nodes(prob.nx, prob.ny, prob.px, prob.py, prob.periodic)
+    M = len(nodes)
+    pick = np.linspace(0, M - 1, 32).astype(int)
+    shift = np.stack([x[nodes[pick, 1], nodes[pick, 0]], y[nodes[pick, 1], nodes[pick, 0]]], 1)
+
+    def run(n):
+        t = time.perf_counter()
+        sums, steps = mc.interface_sums(inp, pick, nodes[pick], np.zeros(len(pick), np.int64),
+                                        np.full(len(pick), n, np.int64), shift)
+        return time.perf_counter() - t, sums, steps
+
+    dt0, _, st0 = run(512)
+    rate0 = st0.sum() / max(dt0, 1e-9)
+    n = int(max(512, min(1 << 20, seconds * rate0 / max(st0.sum() / 512, 1.0))))
+    dt, sums, steps = run(n)
+    rate = float(steps.sum() / dt)
+    _, _, se = mc.estimate(sums, np.full(len(pick), n), shift)
+    need = np.maximum((se.max(axis=1) / prob.se_target) ** 2, 1.0) * n  # paths for SE <= target
+    ps_per_est = float(np.mean(need * steps / n)) if ps_per_estimate_hint is None else ps_per_estimate_hint
+    return {"value": rate / ps_per_est, "unit": UNIT, "cores": int(_clib.lib().oracle_max_threads()),
+            "kind": "oracle",
+            "sample": f"{len(pick)} of {M} interface nodes x {n} paths, first time step, "
+                      f"{'fp64' if real is np.float64 else 'fp32'} paths, {dt:.1f} s; path-steps/s "
+                      f"{rate:.4g} divided by {ps_per_est:.4g} path-steps per node estimate at SE<=1e-4",
+            "path_steps_per_s": rate}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prob = workload(args)
+    K, Wm = args.steps, args.warmup
+    per = max(2.0, min(args.cpu_seconds, 60.0 / max(K + Wm, 1)))
+    vals = []
+    for i in range(Wm + K):
+        r = cpu_baseline(prob, per)
+        if i >= Wm:
+            vals.append(r)
+    value = statistics.median(v["value"] for v in vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": K, "warmup": Wm, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
+           "config": config_of(prob, None),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
+                            "sample": vals[0]["sample"]},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    prob = workload(args, rank)
+    x0, y0 = W.identity_mesh(prob)
+    stream = torch.cuda.current_stream()
+    h = S.SddProblem(S.params_from(prob), x0, y0, stream=stream)
+    h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
+    M = h.M
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        S.sdd_step(h.h)
+    torch.cuda.synchronize()
+
+    launches0 = h.stats()["kernel_launches"]
+    path_steps, mc_ms, mc_launches, paths = 0, 0.0, 0, 0
+    max_se, not_reached = 0.0, 0
+    sampler = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.zero_()
+        S.sdd_step(h.h)
+        st = h.stats()
+        path_steps += st["path_steps"]
+        paths += st["paths"]
+        mc_ms += st["mc_kernel_ms"]
+        mc_launches += st["mc_kernel_launches"]
+        max_se = max(max_se, st["max_se"])
+        not_reached += st["nodes_not_reached"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    T = max(dev_s, 1e-9)
+    launches = h.stats()["kernel_launches"] - launches0
+    if dist is not None:
+        t = torch.tensor([T, float(path_steps), float(M * args.steps)], device="cuda", dtype=torch.float64)
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        T_all, ps_all, est_all = float(tm[0]), float(t[1]), float(t[2])
+    else:
+        T_all, ps_all, est_all = T, float(path_steps), float(M * args.steps)
+
+    # end to end through the C ABI with host buffers: H2D of the step's mesh, D2H of the result
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(np.ascontiguousarray(h.mesh()[0])).pin_memory()
+        hy = torch.from_numpy(np.ascontiguousarray(h.mesh()[1])).pin_memory()
+        ox, oy = torch.empty_like(hx).pin_memory(), torch.empty_like(hy).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for _ in range(args.steps):
+            S.sdd_set_mesh(h.h, hx, hy)
+            S.sdd_step(h.h, ox, oy)
+            hx, ox = ox, hx
+            hy, oy = oy, hy
+        torch.cuda.synchronize()
+        barrier()
+        Te = time.perf_counter() - te
+        if dist is not None:
+            t = torch.tensor([Te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            Te = float(t[0])
+        nb = 2 * prob.nx * prob.ny * 8
+        e2e = {"value": est_all / Te, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
+
+    h.close()
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    achieved = OPS_PER_PATH_STEP * path_steps / (mc_ms / 1e3) if mc_ms > 0 else 0.0
+    out = {"metric": METRIC, "value": est_all / T_all, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * T_all / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp32": "f32", "fp64": "f64", "kahan": "f32"}[args.precision], "data": "synthetic",
+           "config": config_of(prob, M),
+           "path_steps_per_s": ps_all / T_all,
+           "paths_per_node_mean": paths / max(M * args.steps, 1),
+           "max_se": max_se, "nodes_not_reached": not_reached,
+           "wall_s": wall,
+           "gpu_launches": int(launches),
+           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK_OPS / 1e12,
+                        "unit": "Tops/s (32-bit lane ops)", "frac": achieved / ALU_PEAK_OPS,
+                        "traffic": None, "kernel": "mc_kernel<float>",
+                        "ops_per_path_step": OPS_PER_PATH_STEP,
+                        "kernel_ms": mc_ms, "kernel_launches": mc_launches,
+                        "kernel_share_of_step": (mc_ms / 1e3) / T if T > 0 else None,
+                        "peak_basis": "152 SMs x 128 lanes x 2070 MHz (recipe unit counts and max clock)"},
+           "clocks": clocks, "e2e": e2e}
+    if not args.no_cpu_baseline and world == 1:
+        ps_per_est = path_steps / max(M * args.steps, 1)
+        out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, ps_per_est)
+    print(json.dumps(out))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

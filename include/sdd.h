@@ -1,0 +1,203 @@
+/*
+ * sdd.h -- C ABI of the GB300 stochastic domain decomposition (SDD) mesh generator.
+ *
+ * The method (Bihlo, Haynes & Walsh, "Stochastic domain decomposition for time dependent
+ * adaptive mesh generation"): the mesh map x(xi, eta, t) of the linearised parabolic mesh
+ * generator (Eq. 4; monitor frozen over a step, Sec. 2 and Sec. 3.2) is advanced one time
+ * step by
+ *   1. Monte Carlo evaluation of its stochastic representation (Eq. 5a Dirichlet, Eq. 6
+ *      periodic) at the nodes of the artificial subdomain interfaces, with paths of the SDE
+ *      of Eq. (5b) stepped by the Euler-Maruyama scheme of Eq. (7) (Sec. 3.4), then
+ *   2. independent deterministic subdomain solves that take those values as Dirichlet data
+ *      (Sec. 3.5, Sec. 3.6).
+ *
+ * Generator forms.  SDD_FORM_DIV is  tau x_t = div(omega grad x)  with the SDE
+ * dX = grad(omega)/tau ds + sqrt(2 omega/tau) dW.  SDD_FORM_WINSLOW is the paper's Eq. (4),
+ * tau x_t = grad(omega)/omega . grad x + lap x  with dX = grad(omega)/(omega tau) ds +
+ * sqrt(2/tau) dW (tau = 1 gives Eq. 4 and Eq. 5b exactly).  Subdomains are stepped by
+ * backward Euler with centred 5-point differences and face-averaged coefficients.
+ *
+ * Conventions for every call.
+ *   - Every call returns an sdd_status; no exception crosses the ABI.  sdd_last_error()
+ *     returns a thread-local message for the last failing call of the calling thread.
+ *   - Grids are row-major, [j * nx + i], i along xi (fast), j along eta (slow).
+ *   - Array arguments may be host or device pointers (unified addressing decides);
+ *     the library copies inputs and never keeps a caller's pointer.  Outputs are
+ *     caller-owned.  When an output is host memory the call returns after it is written;
+ *     device outputs are written in order on the problem's stream.
+ *   - All device work runs on the stream given to sdd_create_problem / sdd_set_stream.
+ *   - A problem object owns its device memory and must be used from one host thread
+ *     at a time.
+ *   - Failures of the CUDA runtime return SDD_ERR_CUDA; the problem is then unusable
+ *     and should be destroyed.
+ */
+#ifndef SDD_H
+#define SDD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdd_problem sdd_problem;
+
+typedef enum {
+    SDD_OK = 0,
+    SDD_ERR_INVALID_ARG = 1,     /* a size, a flag or a pointer is out of its documented range */
+    SDD_ERR_OOM = 2,             /* device or pinned-host allocation failed                    */
+    SDD_ERR_CUDA = 3,            /* a CUDA runtime call failed (message in sdd_last_error)     */
+    SDD_ERR_NOT_CONVERGED = 4,   /* a subdomain solve hit solve_max_iter; the best iterate is kept */
+    SDD_ERR_SE_NOT_REACHED = 5,  /* adaptive MC hit max_paths_per_node before se_target at some node */
+    SDD_ERR_NO_DEVICE = 6        /* no CUDA device is visible                                  */
+} sdd_status;
+
+enum { SDD_FORM_DIV = 0, SDD_FORM_WINSLOW = 1 };
+
+/* Working precision of the paths and of the estimator sums (subdomain solves: FP64 PCG for
+ * SDD_FP64, FP32 PCG with FP64 residuals and iterative refinement otherwise). */
+enum { SDD_FP64 = 0, SDD_FP32_ACC64 = 1, SDD_FP32_KAHAN = 2 };
+
+/* Monitor (mesh density) kinds, evaluated on the current physical mesh (x, y) at t^n. */
+enum {
+    SDD_MONITOR_NODAL = 0, /* values supplied with sdd_set_monitor                              */
+    SDD_MONITOR_GAUSS = 1, /* sqrt(1 + a exp(-b |x - c|^2)); params a, b, cx, cy                */
+    SDD_MONITOR_FRONT = 2, /* sqrt(1 + alpha |grad u|^2), u = tanh(R (|x - c| - r0 - v t));
+                              params alpha, R, r0, v, cx, cy (the arc-length monitor, Sec. 1)   */
+    SDD_MONITOR_BUMPS = 3  /* 1 + sum_k a_k exp(-|x - c_k|^2 / w_k^2); params (a, w, cx, cy)*   */
+};
+
+typedef struct {
+    int32_t nx, ny;          /* grid nodes per direction, >= 3; (nx-1) % px == 0, (ny-1) % py == 0  */
+    int32_t px, py;          /* subdomains per direction, >= 1 (px * py >= 2 for an interface)     */
+    int32_t periodic;        /* 0: Dirichlet, boundary mesh fixed at (Lx xi, Ly eta) (Sec. 2);
+                                1: doubly periodic, x(xi+1) = x(xi) + Lx, y(eta+1) = y(eta) + Ly    */
+    int32_t form;            /* SDD_FORM_DIV or SDD_FORM_WINSLOW                                   */
+    int32_t precision;       /* SDD_FP64, SDD_FP32_ACC64 or SDD_FP32_KAHAN                          */
+    int32_t bicubic;         /* 1: Keys bicubic of the previous mesh at the path end (Sec. 3.4);
+                                0: bilinear                                                          */
+    int32_t bb_test;         /* 1: Brownian-bridge crossing test between substeps (Sec. 3.4)       */
+    int32_t substeps;        /* K >= 1: Euler-Maruyama substeps per time step, ds = dt / K (Eq. 7) */
+    int32_t solve_max_iter;  /* PCG iteration cap per subdomain solve, >= 1                       */
+    int32_t reserved0;       /* must be 0                                                          */
+    double Lx, Ly;           /* physical rectangle [0, Lx] x [0, Ly], > 0                           */
+    double tau;              /* relaxation time of the generator, > 0                              */
+    double dt;               /* mesh time step, > 0                                                */
+    uint64_t seed;           /* Philox key                                                         */
+    int64_t paths_per_node;  /* N >= 2: paths per node (fixed mode) or first chunk (adaptive)     */
+    int64_t max_paths_per_node; /* adaptive cap, >= paths_per_node, <= 2^31                       */
+    double se_target;        /* > 0: adaptive -- draw paths until max(SE_x, SE_y) <= se_target
+                                at every node; 0: fixed N                                           */
+    double solve_rtol;       /* subdomain solves stop at ||b - A x||_2 <= solve_rtol ||b||_2, > 0   */
+    double t0;               /* time of the initial mesh                                           */
+} sdd_params;
+
+typedef struct {
+    int32_t M;                  /* interface nodes                                             */
+    int32_t step_index;         /* n: steps taken so far (fourth Philox counter word)          */
+    double t;                   /* current time t^n = t0 + n dt                                */
+    int64_t path_steps;         /* substeps actually taken by all paths of the last MC call    */
+    int64_t paths;              /* paths run by the last MC call                               */
+    int32_t mc_rounds;          /* launches of the last MC call (1 in fixed mode)              */
+    int32_t nodes_not_reached;  /* nodes above se_target after the last adaptive MC call       */
+    double max_se;              /* largest SE over nodes and components (last MC call)         */
+    int32_t solve_iters_max;    /* largest total PCG iteration count over subdomains (last solve) */
+    int32_t solve_outer_max;    /* largest refinement sweep count over subdomains (last solve)  */
+    double solve_rel_residual;  /* largest final ||b - A x|| / ||b|| over subdomains and components */
+    double mc_kernel_ms;        /* device time of the path-kernel launches of the last MC call,
+                                   CUDA events on the problem's stream                          */
+    int32_t mc_kernel_launches; /* path-kernel launches of the last MC call                     */
+    int32_t reserved1;
+    int64_t kernel_launches;    /* kernels launched by this problem since creation              */
+} sdd_stats;
+
+/* Create a problem: validates params, copies the initial mesh x0, y0 (nx*ny each, host or
+ * device), allocates all device state.  Dirichlet problems require the boundary nodes of
+ * x0, y0 to equal (Lx xi, Ly eta) to within 1e-12 (Lx + Ly).  `stream` is a cudaStream_t
+ * (NULL = legacy default stream).  Monitor defaults to SDD_MONITOR_NODAL with omega = 1.
+ * Sec. 2 (computational square, physical rectangle, fixed boundary), Sec. 3.4 (dt, K, N). */
+sdd_status sdd_create_problem(const sdd_params* params, const double* x0, const double* y0,
+                              void* stream, sdd_problem** out);
+
+/* Release every resource of the problem (NULL is ignored). */
+void sdd_destroy_problem(sdd_problem* p);
+
+/* Replace the stream all later work of the problem is ordered on. */
+sdd_status sdd_set_stream(sdd_problem* p, void* stream);
+
+/* Overwrite the current mesh x^n, y^n (nx*ny each).  Same boundary rule as at creation. */
+sdd_status sdd_set_mesh(sdd_problem* p, const double* x, const double* y);
+
+/* Copy the current mesh x^n, y^n out (nx*ny each). */
+sdd_status sdd_get_mesh(sdd_problem* p, double* x, double* y);
+
+/* Nodal monitor omega (nx*ny values, > 0), frozen until replaced (Sec. 3.2).  Periodic
+ * problems read only the nodes i < nx-1, j < ny-1 (the wrap nodes repeat node 0). */
+sdd_status sdd_set_monitor(sdd_problem* p, const double* omega);
+
+/* Analytic monitor re-evaluated on the current mesh at t^n before each MC call and step
+ * (the MP procedure: omega from u^n on x^n, Sec. 2 and Sec. 3.6).  Periodic problems use
+ * the minimum-image offset x - c.  n_params: 4 (GAUSS), 6 (FRONT), 4k with k <= 16 (BUMPS). */
+sdd_status sdd_set_monitor_analytic(sdd_problem* p, int32_t kind, const double* params,
+                                    int32_t n_params);
+
+/* Interface Monte Carlo (Sec. 3.4): for every interface node m, paths p = 0, 1, ... of
+ * Eq. (7) started at the node, each substep k drawing Philox4x32-10 with counter
+ * (k, p, m, n) and key = seed, estimate x^{n+1} and y^{n+1} by the arithmetic mean.
+ * Outputs (nullable): est_xy, se_xy: M x 2 doubles (node-major, x then y);
+ * paths_used: M int64.  Does not advance time.  Returns SDD_ERR_SE_NOT_REACHED (outputs
+ * still written) when an adaptive node hit max_paths_per_node. */
+sdd_status sdd_interface_mc(sdd_problem* p, double* est_xy, double* se_xy, int64_t* paths_used);
+
+/* Subdomain solves (Sec. 3.5): Dirichlet data = iface_xy (M x 2, nullable = the last
+ * sdd_interface_mc result) on the interfaces and the boundary mesh on the physical boundary;
+ * backward-Euler 5-point solve of every subdomain interior.  Writes the new mesh to x_out,
+ * y_out (nx*ny each, nullable).  Does not advance time. */
+sdd_status sdd_subdomain_solve(sdd_problem* p, const double* iface_xy, double* x_out, double* y_out);
+
+/* One alternating step t^n -> t^{n+1} (Sec. 3.6): monitor on x^n at t^n (analytic kinds),
+ * interface MC, subdomain solves, then x^n <- x^{n+1}, n <- n + 1.  x_out, y_out nullable. */
+sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out);
+
+/* Counters of the last calls (see sdd_stats). */
+sdd_status sdd_get_stats(const sdd_problem* p, sdd_stats* out);
+
+/* Interface nodes of the problem: ij (M x 2 int32 (i, j), nullable) and *M. */
+sdd_status sdd_get_interface_nodes(const sdd_problem* p, int32_t* ij, int32_t* M);
+
+/* Host-only (no GPU needed): interface nodes of an nx x ny grid split px x py, in the
+ * order that defines the node id m: vertical interface lines by increasing i (nodes by
+ * increasing j), then horizontal lines by increasing j (nodes by increasing i, skipping
+ * nodes already listed).  Dirichlet lines: i = I (nx-1)/px, I = 1..px-1, j = 1..ny-2;
+ * periodic lines: I = 0..px-1, j = 0..ny-2.  ij may be NULL to query *M.  Sec. 3.1, 3.5. */
+sdd_status sdd_interface_layout(int32_t nx, int32_t ny, int32_t px, int32_t py, int32_t periodic,
+                                int32_t* ij, int32_t* M);
+
+/* Host-only: adaptive path total of a node after n_done paths with standard error se
+ * (max of both components): n_done when se <= target or n_done >= max_paths, else
+ * min(max_paths, max(n_done + 1024, 1024 ceil(1.1 n_done (se/target)^2 / 1024))). */
+int64_t sdd_adaptive_next_total(int64_t n_done, double se, double target, int64_t max_paths);
+
+/* Test hook: the monitor as frozen for the next MC call (nx*ny each, FP64, nullable):
+ * omega and its finite-difference gradient (Sec. 3.4). */
+sdd_status sdd_get_monitor(sdd_problem* p, double* omega, double* w_xi, double* w_eta);
+
+/* Test hook: per-path records of paths p_begin .. p_begin + n_paths - 1 of interface node
+ * `node`, computed by the same kernel code as sdd_interface_mc: val_xy (n x 2 doubles),
+ * exit_step (substeps taken), exit_side (0: xi=0, 1: xi=1, 2: eta=0, 3: eta=1, 4: none).
+ * Any output may be NULL.  Uses the current monitor and mesh; does not change state. */
+sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_t n_paths,
+                           double* val_xy, int32_t* exit_step, int8_t* exit_side);
+
+/* Test hook: n Philox4x32-10 draws on the device (ctr n x 4, key n x 2, out n x 4 words),
+ * on the legacy default stream; returns after `out` is written. */
+sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
+
+const char* sdd_status_string(sdd_status s);
+const char* sdd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDD_H */

@@ -1,0 +1,332 @@
+"""Python binding of the GB300 SDD mesh-generator library (argument marshalling only).
+
+Every function here forwards to the C ABI of include/sdd.h in the in-tree CUDA library
+paper_1504_00084_gb300/_build/libsdd.so; every step of the method runs in its kernels.
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); torch supplies device
+memory and streams only.  There is no CPU fallback: importing this module fails loudly if
+the CUDA library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsdd.so")
+
+SDD_OK = 0
+SDD_ERR_INVALID_ARG = 1
+SDD_ERR_OOM = 2
+SDD_ERR_CUDA = 3
+SDD_ERR_NOT_CONVERGED = 4
+SDD_ERR_SE_NOT_REACHED = 5
+SDD_ERR_NO_DEVICE = 6
+
+SDD_FORM_DIV, SDD_FORM_WINSLOW = 0, 1
+SDD_FP64, SDD_FP32_ACC64, SDD_FP32_KAHAN = 0, 1, 2
+SDD_MONITOR_NODAL, SDD_MONITOR_GAUSS, SDD_MONITOR_FRONT, SDD_MONITOR_BUMPS = 0, 1, 2, 3
+
+
+class SddParams(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("px", ctypes.c_int32),
+                ("py", ctypes.c_int32), ("periodic", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("bicubic", ctypes.c_int32), ("bb_test", ctypes.c_int32),
+                ("substeps", ctypes.c_int32), ("solve_max_iter", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("tau", ctypes.c_double), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("paths_per_node", ctypes.c_int64), ("max_paths_per_node", ctypes.c_int64),
+                ("se_target", ctypes.c_double), ("solve_rtol", ctypes.c_double), ("t0", ctypes.c_double)]
+
+
+class SddStats(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int32), ("step_index", ctypes.c_int32), ("t", ctypes.c_double),
+                ("path_steps", ctypes.c_int64), ("paths", ctypes.c_int64), ("mc_rounds", ctypes.c_int32),
+                ("nodes_not_reached", ctypes.c_int32), ("max_se", ctypes.c_double),
+                ("solve_iters_max", ctypes.c_int32), ("solve_outer_max", ctypes.c_int32),
+                ("solve_rel_residual", ctypes.c_double), ("mc_kernel_ms", ctypes.c_double),
+                ("mc_kernel_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTS = [
+    "sdd_create_problem", "sdd_destroy_problem", "sdd_set_stream", "sdd_set_mesh", "sdd_get_mesh",
+    "sdd_set_monitor", "sdd_set_monitor_analytic", "sdd_interface_mc", "sdd_subdomain_solve",
+    "sdd_step", "sdd_get_stats", "sdd_get_interface_nodes", "sdd_interface_layout",
+    "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
+    "sdd_status_string", "sdd_last_error",
+]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build() "
+                          "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, F64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sdd_create_problem": ([ctypes.POINTER(SddParams), P, P, P, ctypes.POINTER(P)], I32),
+        "sdd_destroy_problem": ([P], None),
+        "sdd_set_stream": ([P, P], I32),
+        "sdd_set_mesh": ([P, P, P], I32),
+        "sdd_get_mesh": ([P, P, P], I32),
+        "sdd_set_monitor": ([P, P], I32),
+        "sdd_set_monitor_analytic": ([P, I32, P, I32], I32),
+        "sdd_interface_mc": ([P, P, P, P], I32),
+        "sdd_subdomain_solve": ([P, P, P, P], I32),
+        "sdd_step": ([P, P, P], I32),
+        "sdd_get_stats": ([P, ctypes.POINTER(SddStats)], I32),
+        "sdd_get_interface_nodes": ([P, P, ctypes.POINTER(I32)], I32),
+        "sdd_interface_layout": ([I32, I32, I32, I32, I32, P, ctypes.POINTER(I32)], I32),
+        "sdd_adaptive_next_total": ([I64, F64, F64, I64], I64),
+        "sdd_get_monitor": ([P, P, P, P], I32),
+        "sdd_debug_paths": ([P, I32, I64, I64, P, P, P], I32),
+        "sdd_debug_philox": ([P, P, I64, P], I32),
+        "sdd_status_string": ([I32], ctypes.c_char_p),
+        "sdd_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+
+
+class SddError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib.sdd_status_string(status).decode()
+        detail = lib.sdd_last_error().decode()
+        super().__init__(f"{where}: {msg} ({detail})")
+
+
+def _check(status: int, where: str, ok=(SDD_OK,)):
+    if status not in ok:
+        raise SddError(status, where)
+    return status
+
+
+def _ptr(a) -> Optional[int]:
+    """Raw address of a numpy array or torch tensor (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def params_from(prob, **overrides) -> SddParams:
+    """sdd_params from a workloads.Problem-like object (attributes of the same names)."""
+    p = SddParams()
+    for name, _ in SddParams._fields_:
+        if name == "reserved0":
+            continue
+        if hasattr(prob, name):
+            setattr(p, name, getattr(prob, name))
+    if getattr(prob, "max_paths_per_node", 0) <= 0:
+        p.max_paths_per_node = p.paths_per_node
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------------------------------
+# Same-name wrappers of the C ABI.
+# --------------------------------------------------------------------------------------
+
+def sdd_create_problem(params: SddParams, x0, y0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.sdd_create_problem(ctypes.byref(params), _ptr(x0), _ptr(y0), _stream_handle(stream),
+                                  ctypes.byref(h)), "sdd_create_problem")
+    return h.value
+
+
+def sdd_destroy_problem(h: int) -> None:
+    lib.sdd_destroy_problem(h)
+
+
+def sdd_set_stream(h: int, stream) -> None:
+    _check(lib.sdd_set_stream(h, _stream_handle(stream)), "sdd_set_stream")
+
+
+def sdd_set_mesh(h: int, x, y) -> None:
+    _check(lib.sdd_set_mesh(h, _ptr(x), _ptr(y)), "sdd_set_mesh")
+
+
+def sdd_get_mesh(h: int, x, y) -> None:
+    _check(lib.sdd_get_mesh(h, _ptr(x), _ptr(y)), "sdd_get_mesh")
+
+
+def sdd_set_monitor(h: int, omega) -> None:
+    _check(lib.sdd_set_monitor(h, _ptr(omega)), "sdd_set_monitor")
+
+
+def sdd_set_monitor_analytic(h: int, kind: int, params) -> None:
+    arr = np.ascontiguousarray(params, dtype=np.float64)
+    _check(lib.sdd_set_monitor_analytic(h, kind, arr.ctypes.data if arr.size else None, arr.size),
+           "sdd_set_monitor_analytic")
+
+
+def sdd_interface_mc(h: int, est_xy=None, se_xy=None, paths_used=None, allow_se_not_reached=True) -> int:
+    ok = (SDD_OK, SDD_ERR_SE_NOT_REACHED) if allow_se_not_reached else (SDD_OK,)
+    return _check(lib.sdd_interface_mc(h, _ptr(est_xy), _ptr(se_xy), _ptr(paths_used)),
+                  "sdd_interface_mc", ok)
+
+
+def sdd_subdomain_solve(h: int, iface_xy=None, x_out=None, y_out=None) -> int:
+    return _check(lib.sdd_subdomain_solve(h, _ptr(iface_xy), _ptr(x_out), _ptr(y_out)), "sdd_subdomain_solve")
+
+
+def sdd_step(h: int, x_out=None, y_out=None, allow_se_not_reached=True) -> int:
+    ok = (SDD_OK, SDD_ERR_SE_NOT_REACHED) if allow_se_not_reached else (SDD_OK,)
+    return _check(lib.sdd_step(h, _ptr(x_out), _ptr(y_out)), "sdd_step", ok)
+
+
+def sdd_get_stats(h: int) -> dict:
+    s = SddStats()
+    _check(lib.sdd_get_stats(h, ctypes.byref(s)), "sdd_get_stats")
+    return s.as_dict()
+
+
+def sdd_get_interface_nodes(h: int) -> np.ndarray:
+    M = ctypes.c_int32()
+    _check(lib.sdd_get_interface_nodes(h, None, ctypes.byref(M)), "sdd_get_interface_nodes")
+    ij = np.zeros((M.value, 2), dtype=np.int32)
+    _check(lib.sdd_get_interface_nodes(h, ij.ctypes.data if M.value else None, ctypes.byref(M)),
+           "sdd_get_interface_nodes")
+    return ij
+
+
+def sdd_interface_layout(nx: int, ny: int, px: int, py: int, periodic: int) -> np.ndarray:
+    M = ctypes.c_int32()
+    _check(lib.sdd_interface_layout(nx, ny, px, py, periodic, None, ctypes.byref(M)), "sdd_interface_layout")
+    ij = np.zeros((M.value, 2), dtype=np.int32)
+    if M.value:
+        _check(lib.sdd_interface_layout(nx, ny, px, py, periodic, ij.ctypes.data, ctypes.byref(M)),
+               "sdd_interface_layout")
+    return ij
+
+
+def sdd_adaptive_next_total(n_done: int, se: float, target: float, max_paths: int) -> int:
+    return int(lib.sdd_adaptive_next_total(n_done, se, target, max_paths))
+
+
+def sdd_get_monitor(h: int, omega=None, w_xi=None, w_eta=None) -> None:
+    _check(lib.sdd_get_monitor(h, _ptr(omega), _ptr(w_xi), _ptr(w_eta)), "sdd_get_monitor")
+
+
+def sdd_debug_paths(h: int, node: int, p_begin: int, n_paths: int):
+    val = np.zeros((n_paths, 2), dtype=np.float64)
+    steps = np.zeros(n_paths, dtype=np.int32)
+    side = np.zeros(n_paths, dtype=np.int8)
+    _check(lib.sdd_debug_paths(h, node, p_begin, n_paths, val.ctypes.data, steps.ctypes.data,
+                               side.ctypes.data), "sdd_debug_paths")
+    return val, steps, side
+
+
+def sdd_debug_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    key = np.ascontiguousarray(key, dtype=np.uint32).reshape(-1, 2)
+    out = np.zeros_like(ctr)
+    _check(lib.sdd_debug_philox(ctr.ctypes.data, key.ctypes.data, len(ctr), out.ctypes.data),
+           "sdd_debug_philox")
+    return out
+
+
+class SddProblem:
+    """Owning handle of one problem (context manager); methods forward to the C ABI."""
+
+    def __init__(self, params: SddParams, x0, y0, stream=None):
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        self.h = sdd_create_problem(params, np.ascontiguousarray(x0, dtype=np.float64)
+                                    if isinstance(x0, np.ndarray) else x0,
+                                    np.ascontiguousarray(y0, dtype=np.float64)
+                                    if isinstance(y0, np.ndarray) else y0, stream)
+        self.M = len(sdd_get_interface_nodes(self.h))
+
+    def close(self):
+        if self.h:
+            sdd_destroy_problem(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_monitor(self, omega):
+        sdd_set_monitor(self.h, np.ascontiguousarray(omega, dtype=np.float64)
+                        if isinstance(omega, np.ndarray) else omega)
+
+    def set_monitor_analytic(self, kind, params):
+        sdd_set_monitor_analytic(self.h, kind, params)
+
+    def interface_mc(self):
+        est = np.zeros((self.M, 2))
+        se = np.zeros((self.M, 2))
+        n = np.zeros(self.M, dtype=np.int64)
+        status = sdd_interface_mc(self.h, est, se, n)
+        return est, se, n, status
+
+    def subdomain_solve(self, iface=None):
+        x = np.zeros((self.ny, self.nx))
+        y = np.zeros((self.ny, self.nx))
+        iface = None if iface is None else np.ascontiguousarray(iface, dtype=np.float64)
+        status = sdd_subdomain_solve(self.h, iface, x, y)
+        return x, y, status
+
+    def step(self):
+        x = np.zeros((self.ny, self.nx))
+        y = np.zeros((self.ny, self.nx))
+        status = sdd_step(self.h, x, y)
+        return x, y, status
+
+    def mesh(self):
+        x = np.zeros((self.ny, self.nx))
+        y = np.zeros((self.ny, self.nx))
+        sdd_get_mesh(self.h, x, y)
+        return x, y
+
+    def monitor(self):
+        w, a, b = (np.zeros((self.ny, self.nx)) for _ in range(3))
+        sdd_get_monitor(self.h, w, a, b)
+        return w, a, b
+
+    def stats(self):
+        return sdd_get_stats(self.h)
+
+    def nodes(self):
+        return sdd_get_interface_nodes(self.h)
+
+    def debug_paths(self, node, p_begin, n_paths):
+        return sdd_debug_paths(self.h, node, p_begin, n_paths)

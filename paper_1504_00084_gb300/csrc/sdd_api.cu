@@ -1,0 +1,727 @@
+// C ABI of the SDD mesh generator (declared in include/sdd.h).
+//
+// Host-side orchestration only: validation, device state, the round loop of the interface
+// Monte Carlo, and the order of the kernels of one alternating step.  Every arithmetic step
+// of the method runs in the kernels of sdd_prep.cu, sdd_mc.cu and sdd_solve.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "sdd.h"
+#include "sdd_internal.cuh"
+
+using namespace sdd;
+
+namespace {
+
+thread_local std::string g_err;
+
+sdd_status fail(sdd_status s, const std::string& msg)
+{
+    g_err = msg;
+    return s;
+}
+
+#define SDD_CK(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA,      \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+#define SDD_TRY(call)                          \
+    do {                                       \
+        sdd_status s_ = (call);                \
+        if (s_ != SDD_OK) return s_;           \
+    } while (0)
+
+constexpr int64_t kMaxChunk = int64_t(1) << 19;  // paths per node per launch (see plan kernel)
+constexpr int kSlotsPerNode = (int)(kMaxChunk / kPathsPerTask);
+constexpr int kMaxAdaptiveRounds = 4096;
+
+void layout(int nx, int ny, int px, int py, int periodic, std::vector<int32_t>& ij)
+{
+    ij.clear();
+    const int sx = (nx - 1) / px, sy = (ny - 1) / py;
+    std::vector<int> vl, hl;
+    if (periodic) {
+        for (int I = 0; I < px; ++I) vl.push_back(I * sx);
+        for (int J = 0; J < py; ++J) hl.push_back(J * sy);
+    } else {
+        for (int I = 1; I < px; ++I) vl.push_back(I * sx);
+        for (int J = 1; J < py; ++J) hl.push_back(J * sy);
+    }
+    const int jlo = periodic ? 0 : 1, jhi = periodic ? ny - 2 : ny - 2;
+    const int ilo = periodic ? 0 : 1, ihi = periodic ? nx - 2 : nx - 2;
+    std::vector<char> on_v(nx, 0);
+    for (int i : vl) on_v[i] = 1;
+    for (int i : vl)
+        for (int j = jlo; j <= jhi; ++j) { ij.push_back(i); ij.push_back(j); }
+    for (int j : hl)
+        for (int i = ilo; i <= ihi; ++i)
+            if (!on_v[i]) { ij.push_back(i); ij.push_back(j); }
+}
+
+bool is_device_ptr(const void* ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct sdd_problem {
+    sdd_params prm{};
+    cudaStream_t stream = nullptr;
+    int M = 0;
+    std::vector<int32_t> ij;
+    int mc_grid = 1;
+    bool fp64 = true;
+    int acc_mode = kAcc64;
+    int64_t step = 0;
+    bool have_est = false;
+    // monitor
+    int mon_kind = 0;
+    int n_params = 0;
+    double mon_params[64] = {0};
+    // device: mesh and monitor
+    double *x = nullptr, *y = nullptr, *xn = nullptr, *yn = nullptr;
+    double *om64 = nullptr, *wxi64 = nullptr, *weta64 = nullptr, *omega_nodal = nullptr;
+    void *mon = nullptr, *disp = nullptr;
+    int2* nodes = nullptr;
+    double* shift = nullptr;
+    // device: interface MC
+    double* acc = nullptr;
+    int64_t *n_done = nullptr, *steps = nullptr, *paths_run = nullptr, *next_total = nullptr;
+    int32_t* node_of = nullptr;
+    int64_t *p_begin = nullptr, *p_count = nullptr, *task_off = nullptr;
+    int32_t *n_active = nullptr, *task_counter = nullptr;
+    TaskSlot* slots = nullptr;
+    int64_t slot_cap = 0;
+    double *est = nullptr, *se = nullptr;
+    // device: solves
+    double *ce64 = nullptr, *cn64 = nullptr;
+    void *ce = nullptr, *cn = nullptr, *vec = nullptr;
+    int32_t *st_iters = nullptr, *st_outer = nullptr, *st_ok = nullptr;
+    double* st_res = nullptr;
+    // host
+    int32_t* h_n_active = nullptr;  // pinned
+    sdd_stats stats{};
+    std::vector<void*> allocs;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs around path-kernel launches
+    int64_t launches = 0;         // kernels launched since creation
+
+    template <typename P>
+    cudaError_t dalloc(P** p, size_t bytes)
+    {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
+        if (e == cudaSuccess) {
+            allocs.push_back(v);
+            *p = static_cast<P*>(v);
+        }
+        return e;
+    }
+    ~sdd_problem()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (void* v : allocs) cudaFree(v);
+        if (h_n_active) cudaFreeHost(h_n_active);
+    }
+};
+
+namespace {
+
+sdd_status validate(const sdd_params* P)
+{
+    if (!P) return fail(SDD_ERR_INVALID_ARG, "params is NULL");
+    if (P->nx < 3 || P->ny < 3) return fail(SDD_ERR_INVALID_ARG, "nx, ny must be >= 3");
+    if ((int64_t)P->nx * P->ny > (int64_t)1 << 28) return fail(SDD_ERR_INVALID_ARG, "grid too large");
+    if (P->px < 1 || P->py < 1) return fail(SDD_ERR_INVALID_ARG, "px, py must be >= 1");
+    if ((P->nx - 1) % P->px || (P->ny - 1) % P->py)
+        return fail(SDD_ERR_INVALID_ARG, "(nx-1) % px and (ny-1) % py must be 0");
+    if (P->periodic != 0 && P->periodic != 1) return fail(SDD_ERR_INVALID_ARG, "periodic must be 0 or 1");
+    if (P->form != SDD_FORM_DIV && P->form != SDD_FORM_WINSLOW) return fail(SDD_ERR_INVALID_ARG, "bad form");
+    if (P->precision < SDD_FP64 || P->precision > SDD_FP32_KAHAN)
+        return fail(SDD_ERR_INVALID_ARG, "bad precision");
+    if (P->bicubic != 0 && P->bicubic != 1) return fail(SDD_ERR_INVALID_ARG, "bicubic must be 0 or 1");
+    if (P->bb_test != 0 && P->bb_test != 1) return fail(SDD_ERR_INVALID_ARG, "bb_test must be 0 or 1");
+    if (P->substeps < 1) return fail(SDD_ERR_INVALID_ARG, "substeps must be >= 1");
+    if (P->solve_max_iter < 1) return fail(SDD_ERR_INVALID_ARG, "solve_max_iter must be >= 1");
+    if (P->reserved0 != 0) return fail(SDD_ERR_INVALID_ARG, "reserved0 must be 0");
+    if (!(P->Lx > 0) || !(P->Ly > 0) || !(P->tau > 0) || !(P->dt > 0))
+        return fail(SDD_ERR_INVALID_ARG, "Lx, Ly, tau, dt must be > 0");
+    if (!isfinite(P->Lx) || !isfinite(P->Ly) || !isfinite(P->tau) || !isfinite(P->dt) || !isfinite(P->t0))
+        return fail(SDD_ERR_INVALID_ARG, "non-finite parameter");
+    if (P->paths_per_node < 2) return fail(SDD_ERR_INVALID_ARG, "paths_per_node must be >= 2");
+    if (!(P->se_target >= 0) || !isfinite(P->se_target)) return fail(SDD_ERR_INVALID_ARG, "se_target must be >= 0");
+    const int64_t cap = P->se_target > 0 ? P->max_paths_per_node : P->paths_per_node;
+    if (cap < P->paths_per_node || cap > ((int64_t)1 << 31))
+        return fail(SDD_ERR_INVALID_ARG, "max_paths_per_node must be in [paths_per_node, 2^31]");
+    if (!(P->solve_rtol > 0)) return fail(SDD_ERR_INVALID_ARG, "solve_rtol must be > 0");
+    return SDD_OK;
+}
+
+sdd_status copy_in(sdd_problem* p, void* dst, const void* src, size_t bytes)
+{
+    SDD_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, p->stream));
+    return SDD_OK;
+}
+
+// Copy to a caller buffer; return only after a host destination holds the data.
+sdd_status copy_out(sdd_problem* p, void* dst, const void* src, size_t bytes)
+{
+    if (!dst || bytes == 0) return SDD_OK;
+    SDD_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, p->stream));
+    if (!is_device_ptr(dst)) SDD_CK(cudaStreamSynchronize(p->stream));
+    return SDD_OK;
+}
+
+sdd_status check_boundary(const sdd_problem* p, const double* x, const double* y)
+{
+    if (p->prm.periodic) return SDD_OK;
+    const int nx = p->prm.nx, ny = p->prm.ny;
+    std::vector<double> hx((size_t)nx * ny), hy((size_t)nx * ny);
+    if (cudaMemcpy(hx.data(), x, hx.size() * 8, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(hy.data(), y, hy.size() * 8, cudaMemcpyDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SDD_ERR_INVALID_ARG, "mesh pointers are not readable");
+    }
+    const double tol = 1e-12 * (p->prm.Lx + p->prm.Ly);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            if (i != 0 && j != 0 && i != nx - 1 && j != ny - 1) continue;
+            const double bx = p->prm.Lx * ((double)i / (double)(nx - 1));
+            const double by = p->prm.Ly * ((double)j / (double)(ny - 1));
+            const size_t id = (size_t)j * nx + i;
+            if (!(fabs(hx[id] - bx) <= tol) || !(fabs(hy[id] - by) <= tol))
+                return fail(SDD_ERR_INVALID_ARG,
+                            "Dirichlet mesh must equal (Lx xi, Ly eta) on the boundary");
+        }
+    return SDD_OK;
+}
+
+// Monitor on the current mesh, FD gradient, packed records, estimator shifts.
+sdd_status run_prep(sdd_problem* p)
+{
+    PrepParams P{};
+    P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic;
+    P.kind = p->mon_kind; P.n_params = p->n_params; P.precision = p->prm.precision;
+    P.Lx = p->prm.Lx; P.Ly = p->prm.Ly;
+    P.t = p->prm.t0 + (double)p->step * p->prm.dt;
+    P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
+    memcpy(P.params, p->mon_params, sizeof(P.params));
+    P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64;
+    P.mon = p->mon; P.disp = p->disp;
+    SDD_CK(launch_prep(P, p->stream));
+    p->launches += 2;
+    if (p->M > 0) {
+        SDD_CK(launch_shift(p->nodes, p->M, p->prm.nx, p->x, p->y, p->shift, p->stream));
+        p->launches += 1;
+    }
+    return SDD_OK;
+}
+
+template <typename T>
+McParams<T> mc_params(const sdd_problem* p)
+{
+    McParams<T> P{};
+    P.mon = static_cast<const Mon4<T>*>(p->mon);
+    P.disp = static_cast<const Disp2<T>*>(p->disp);
+    P.nodes = p->nodes; P.shift = p->shift;
+    P.node_of = p->node_of; P.p_begin = p->p_begin; P.p_count = p->p_count;
+    P.task_off = p->task_off; P.n_active = p->n_active; P.task_counter = p->task_counter;
+    P.slots = p->slots;
+    P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic; P.form = p->prm.form;
+    P.K = p->prm.substeps; P.bicubic = p->prm.bicubic; P.bb = p->prm.bb_test;
+    const T ds = (T)p->prm.dt / (T)p->prm.substeps;
+    P.cb = ds / (T)p->prm.tau;
+    P.Lx = (T)p->prm.Lx; P.Ly = (T)p->prm.Ly;
+    P.key0 = (uint32_t)(p->prm.seed & 0xFFFFFFFFu);
+    P.key1 = (uint32_t)(p->prm.seed >> 32);
+    P.tstep = (uint32_t)p->step;
+    return P;
+}
+
+sdd_status launch_mc_round(sdd_problem* p, bool debug, double* dval, int32_t* dsteps, int8_t* dside,
+                           int64_t dp0)
+{
+    if (p->fp64) {
+        McParams<double> P = mc_params<double>(p);
+        P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0;
+        SDD_CK(launch_mc<double>(P, p->acc_mode, debug, p->mc_grid, p->stream));
+    } else {
+        McParams<float> P = mc_params<float>(p);
+        P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0;
+        SDD_CK(launch_mc<float>(P, p->acc_mode, debug, p->mc_grid, p->stream));
+    }
+    return SDD_OK;
+}
+
+// Path-kernel launch bracketed by CUDA events on the problem's stream (pair `slot`).
+sdd_status timed_mc_round(sdd_problem* p, int slot)
+{
+    while ((int)p->ev.size() < 2 * (slot + 1)) {
+        cudaEvent_t e;
+        SDD_CK(cudaEventCreate(&e));
+        p->ev.push_back(e);
+    }
+    SDD_CK(cudaEventRecord(p->ev[2 * slot], p->stream));
+    SDD_TRY(launch_mc_round(p, false, nullptr, nullptr, nullptr, 0));
+    SDD_CK(cudaEventRecord(p->ev[2 * slot + 1], p->stream));
+    return SDD_OK;
+}
+
+sdd_status run_mc(sdd_problem* p)
+{
+    const int M = p->M;
+    p->stats.mc_rounds = 0;
+    p->stats.mc_kernel_ms = 0.0;
+    p->stats.mc_kernel_launches = 0;
+    p->stats.path_steps = 0;
+    p->stats.paths = 0;
+    p->stats.nodes_not_reached = 0;
+    p->stats.max_se = 0.0;
+    if (M == 0) {
+        p->have_est = true;
+        return SDD_OK;
+    }
+    const bool adaptive = p->prm.se_target > 0;
+    const int64_t n0 = p->prm.paths_per_node;
+    const int64_t maxp = adaptive ? p->prm.max_paths_per_node : n0;
+    SDD_CK(launch_mc_init(M, n0, maxp, p->acc, p->n_done, p->steps, p->paths_run, p->next_total, p->stream));
+    p->launches += 1;
+    int n_timed = 0;
+    PlanParams PP{};
+    PP.M = M; PP.n_done = p->n_done; PP.next_total = p->next_total; PP.node_of = p->node_of;
+    PP.p_begin = p->p_begin; PP.p_count = p->p_count; PP.task_off = p->task_off;
+    PP.n_active = p->n_active; PP.task_counter = p->task_counter;
+    ReduceParams RP{};
+    RP.node_of = p->node_of; RP.p_count = p->p_count; RP.task_off = p->task_off;
+    RP.n_active = p->n_active; RP.slots = p->slots; RP.shift = p->shift; RP.acc = p->acc;
+    RP.n_done = p->n_done; RP.steps = p->steps; RP.paths_run = p->paths_run;
+    RP.next_total = p->next_total; RP.se_target = adaptive ? p->prm.se_target : 0.0;
+    RP.max_paths = maxp;
+    if (!adaptive) {
+        // fixed N: the number of launches is known, no host round trip
+        const int64_t rounds = (n0 + kMaxChunk - 1) / kMaxChunk;
+        for (int64_t r = 0; r < rounds; ++r) {
+            SDD_CK(launch_plan(PP, p->stream));
+            SDD_TRY(timed_mc_round(p, n_timed++));
+            SDD_CK(launch_reduce(RP, M, p->stream));
+            p->launches += 3;
+        }
+        p->stats.mc_rounds = (int32_t)rounds;
+    } else {
+        for (int r = 0; r < kMaxAdaptiveRounds; ++r) {
+            SDD_CK(launch_plan(PP, p->stream));
+            p->launches += 1;
+            SDD_CK(cudaMemcpyAsync(p->h_n_active, p->n_active, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                   p->stream));
+            SDD_CK(cudaStreamSynchronize(p->stream));
+            if (*p->h_n_active == 0) break;
+            SDD_TRY(timed_mc_round(p, n_timed++));
+            SDD_CK(launch_reduce(RP, M, p->stream));
+            p->launches += 2;
+            p->stats.mc_rounds = r + 1;
+        }
+    }
+    SDD_CK(launch_output(M, p->acc, p->n_done, p->shift, p->est, p->se, p->stream));
+    p->launches += 1;
+    // counters (small copies)
+    std::vector<int64_t> st(M), np(M);
+    std::vector<double> se((size_t)2 * M);
+    SDD_CK(cudaMemcpyAsync(st.data(), p->steps, 8 * (size_t)M, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(np.data(), p->paths_run, 8 * (size_t)M, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(se.data(), p->se, 16 * (size_t)M, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    p->stats.mc_kernel_ms = 0.0;
+    p->stats.mc_kernel_launches = n_timed;
+    for (int k = 0; k < n_timed; ++k) {
+        float ms = 0.f;
+        SDD_CK(cudaEventElapsedTime(&ms, p->ev[2 * k], p->ev[2 * k + 1]));
+        p->stats.mc_kernel_ms += ms;
+    }
+    for (int m = 0; m < M; ++m) {
+        p->stats.path_steps += st[m];
+        p->stats.paths += np[m];
+        const double s = se[2 * m] > se[2 * m + 1] ? se[2 * m] : se[2 * m + 1];
+        if (s > p->stats.max_se) p->stats.max_se = s;
+        if (adaptive && s > p->prm.se_target) p->stats.nodes_not_reached += 1;
+    }
+    p->have_est = true;
+    return p->stats.nodes_not_reached ? fail(SDD_ERR_SE_NOT_REACHED, "max_paths_per_node reached before se_target")
+                                      : SDD_OK;
+}
+
+sdd_status run_solve(sdd_problem* p)
+{
+    SDD_CK(launch_scatter(p->prm.nx, p->prm.ny, p->prm.periodic, p->prm.Lx, p->prm.Ly, p->nodes, p->M,
+                          p->est, p->xn, p->yn, p->stream));
+    p->launches += (p->prm.periodic ? 0 : 1) + (p->M > 0 ? 1 : 0);
+    SolveParams S{};
+    S.nx = p->prm.nx; S.ny = p->prm.ny; S.px = p->prm.px; S.py = p->prm.py; S.form = p->prm.form;
+    S.r = p->prm.dt / p->prm.tau; S.rtol = p->prm.solve_rtol; S.max_iter = p->prm.solve_max_iter;
+    S.om64 = p->om64; S.xcur = p->x; S.ycur = p->y; S.xnew = p->xn; S.ynew = p->yn;
+    S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
+    S.stat_iters = p->st_iters; S.stat_outer = p->st_outer; S.stat_ok = p->st_ok; S.stat_res = p->st_res;
+    SDD_CK(launch_solve(S, p->fp64, p->stream));
+    p->launches += 2;
+    const int ns = p->prm.px * p->prm.py;
+    std::vector<int32_t> it(ns), ou(ns), ok(ns);
+    std::vector<double> rs(ns);
+    SDD_CK(cudaMemcpyAsync(it.data(), p->st_iters, 4 * (size_t)ns, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(ou.data(), p->st_outer, 4 * (size_t)ns, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(ok.data(), p->st_ok, 4 * (size_t)ns, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(rs.data(), p->st_res, 8 * (size_t)ns, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    p->stats.solve_iters_max = 0;
+    p->stats.solve_outer_max = 0;
+    p->stats.solve_rel_residual = 0.0;
+    int bad = 0;
+    for (int s = 0; s < ns; ++s) {
+        if (it[s] > p->stats.solve_iters_max) p->stats.solve_iters_max = it[s];
+        if (ou[s] > p->stats.solve_outer_max) p->stats.solve_outer_max = ou[s];
+        if (rs[s] > p->stats.solve_rel_residual) p->stats.solve_rel_residual = rs[s];
+        bad += ok[s] ? 0 : 1;
+    }
+    return bad ? fail(SDD_ERR_NOT_CONVERGED, "a subdomain solve reached solve_max_iter") : SDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sdd_status_string(sdd_status s)
+{
+    switch (s) {
+    case SDD_OK: return "ok";
+    case SDD_ERR_INVALID_ARG: return "invalid argument";
+    case SDD_ERR_OOM: return "out of memory";
+    case SDD_ERR_CUDA: return "CUDA error";
+    case SDD_ERR_NOT_CONVERGED: return "subdomain solve not converged";
+    case SDD_ERR_SE_NOT_REACHED: return "standard-error target not reached";
+    case SDD_ERR_NO_DEVICE: return "no CUDA device";
+    }
+    return "unknown status";
+}
+
+const char* sdd_last_error(void) { return g_err.c_str(); }
+
+sdd_status sdd_interface_layout(int32_t nx, int32_t ny, int32_t px, int32_t py, int32_t periodic,
+                                int32_t* ij, int32_t* M)
+{
+    if (!M) return fail(SDD_ERR_INVALID_ARG, "M is NULL");
+    if (nx < 3 || ny < 3 || px < 1 || py < 1 || (nx - 1) % px || (ny - 1) % py || (periodic != 0 && periodic != 1))
+        return fail(SDD_ERR_INVALID_ARG, "bad grid or split");
+    std::vector<int32_t> v;
+    layout(nx, ny, px, py, periodic, v);
+    *M = (int32_t)(v.size() / 2);
+    if (ij && !v.empty()) memcpy(ij, v.data(), v.size() * sizeof(int32_t));
+    return SDD_OK;
+}
+
+int64_t sdd_adaptive_next_total(int64_t n_done, double se, double target, int64_t max_paths)
+{
+    return adaptive_next_total(n_done, se, target, max_paths);
+}
+
+sdd_status sdd_create_problem(const sdd_params* params, const double* x0, const double* y0, void* stream,
+                              sdd_problem** out)
+{
+    if (!out) return fail(SDD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    SDD_TRY(validate(params));
+    if (!x0 || !y0) return fail(SDD_ERR_INVALID_ARG, "x0, y0 must not be NULL");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(SDD_ERR_NO_DEVICE, "no CUDA device visible");
+    }
+    sdd_problem* p = new sdd_problem();
+    p->prm = *params;
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->fp64 = params->precision == SDD_FP64;
+    p->acc_mode = params->precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
+    layout(params->nx, params->ny, params->px, params->py, params->periodic, p->ij);
+    p->M = (int)(p->ij.size() / 2);
+    auto bail = [&](sdd_status s) { delete p; return s; };
+    {
+        sdd_status s = check_boundary(p, x0, y0);
+        if (s != SDD_OK) return bail(s);
+    }
+    const size_t N = (size_t)params->nx * params->ny;
+    const size_t M = (size_t)p->M;
+    const size_t rs = p->fp64 ? 8 : 4;
+    p->slot_cap = (int64_t)(M > 0 ? M : 1) * kSlotsPerNode;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) if (e == cudaSuccess) e = p->dalloc(&(ptr), (bytes))
+    ALLOC(p->x, N * 8); ALLOC(p->y, N * 8); ALLOC(p->xn, N * 8); ALLOC(p->yn, N * 8);
+    ALLOC(p->om64, N * 8); ALLOC(p->wxi64, N * 8); ALLOC(p->weta64, N * 8); ALLOC(p->omega_nodal, N * 8);
+    ALLOC(p->mon, N * 4 * rs); ALLOC(p->disp, N * 2 * rs);
+    ALLOC(p->nodes, (M + 1) * sizeof(int2)); ALLOC(p->shift, (M + 1) * 16);
+    ALLOC(p->acc, (M + 1) * 32); ALLOC(p->n_done, (M + 1) * 8); ALLOC(p->steps, (M + 1) * 8);
+    ALLOC(p->paths_run, (M + 1) * 8); ALLOC(p->next_total, (M + 1) * 8);
+    ALLOC(p->node_of, (M + 1) * 4); ALLOC(p->p_begin, (M + 1) * 8); ALLOC(p->p_count, (M + 1) * 8);
+    ALLOC(p->task_off, (M + 2) * 8); ALLOC(p->n_active, 16); ALLOC(p->task_counter, 16);
+    ALLOC(p->slots, (size_t)p->slot_cap * sizeof(TaskSlot));
+    ALLOC(p->est, (M + 1) * 16); ALLOC(p->se, (M + 1) * 16);
+    ALLOC(p->ce64, N * 8); ALLOC(p->cn64, N * 8); ALLOC(p->ce, N * rs); ALLOC(p->cn, N * rs);
+    ALLOC(p->vec, N * 4 * 2 * rs);
+    const int ns = params->px * params->py;
+    ALLOC(p->st_iters, ns * 4); ALLOC(p->st_outer, ns * 4); ALLOC(p->st_ok, ns * 4); ALLOC(p->st_res, ns * 8);
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_n_active, 16, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const std::string msg = std::string("allocation failed: ") + cudaGetErrorString(e);
+        delete p;
+        return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, msg);
+    }
+    auto ck = [&](cudaError_t c, const char* what) -> sdd_status {
+        if (c == cudaSuccess) return SDD_OK;
+        return fail(SDD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(c));
+    };
+    sdd_status s = SDD_OK;
+    if (s == SDD_OK) s = ck(cudaMemsetAsync(p->vec, 0, N * 4 * 2 * rs, p->stream), "memset");
+    if (s == SDD_OK) s = ck(cudaMemcpyAsync(p->x, x0, N * 8, cudaMemcpyDefault, p->stream), "copy x0");
+    if (s == SDD_OK) s = ck(cudaMemcpyAsync(p->y, y0, N * 8, cudaMemcpyDefault, p->stream), "copy y0");
+    if (s == SDD_OK && M > 0)
+        s = ck(cudaMemcpyAsync(p->nodes, p->ij.data(), M * sizeof(int2), cudaMemcpyHostToDevice, p->stream),
+               "copy nodes");
+    // default monitor: omega = 1 everywhere
+    if (s == SDD_OK) {
+        std::vector<double> ones(N, 1.0);
+        s = ck(cudaMemcpyAsync(p->omega_nodal, ones.data(), N * 8, cudaMemcpyHostToDevice, p->stream), "copy omega");
+        if (s == SDD_OK) s = ck(cudaStreamSynchronize(p->stream), "sync");
+    }
+    if (s != SDD_OK) return bail(s);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = p->fp64 ? mc_max_blocks_per_sm<double>(p->acc_mode, false)
+                               : mc_max_blocks_per_sm<float>(p->acc_mode, false);
+    p->mc_grid = nsm * per_sm;
+    p->stats.M = p->M;
+    p->stats.t = params->t0;
+    *out = p;
+    return SDD_OK;
+}
+
+void sdd_destroy_problem(sdd_problem* p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(p->stream);
+    delete p;
+}
+
+sdd_status sdd_set_stream(sdd_problem* p, void* stream)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    p->stream = static_cast<cudaStream_t>(stream);
+    return SDD_OK;
+}
+
+sdd_status sdd_set_mesh(sdd_problem* p, const double* x, const double* y)
+{
+    if (!p || !x || !y) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    SDD_TRY(check_boundary(p, x, y));
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_in(p, p->x, x, N * 8));
+    SDD_TRY(copy_in(p, p->y, y, N * 8));
+    p->have_est = false;
+    return SDD_OK;
+}
+
+sdd_status sdd_get_mesh(sdd_problem* p, double* x, double* y)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_out(p, x, p->x, N * 8));
+    SDD_TRY(copy_out(p, y, p->y, N * 8));
+    return SDD_OK;
+}
+
+sdd_status sdd_set_monitor(sdd_problem* p, const double* omega)
+{
+    if (!p || !omega) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_in(p, p->omega_nodal, omega, N * 8));
+    p->mon_kind = SDD_MONITOR_NODAL;
+    p->n_params = 0;
+    return SDD_OK;
+}
+
+sdd_status sdd_set_monitor_analytic(sdd_problem* p, int32_t kind, const double* params, int32_t n_params)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    if (kind == SDD_MONITOR_GAUSS && n_params != 4) return fail(SDD_ERR_INVALID_ARG, "GAUSS needs 4 params");
+    if (kind == SDD_MONITOR_FRONT && n_params != 6) return fail(SDD_ERR_INVALID_ARG, "FRONT needs 6 params");
+    if (kind == SDD_MONITOR_BUMPS && (n_params % 4 || n_params < 0 || n_params > 64))
+        return fail(SDD_ERR_INVALID_ARG, "BUMPS needs 4k params, k <= 16");
+    if (kind < SDD_MONITOR_GAUSS || kind > SDD_MONITOR_BUMPS) return fail(SDD_ERR_INVALID_ARG, "bad monitor kind");
+    if (n_params > 0 && !params) return fail(SDD_ERR_INVALID_ARG, "params is NULL");
+    p->mon_kind = kind;
+    p->n_params = n_params;
+    memset(p->mon_params, 0, sizeof(p->mon_params));
+    for (int k = 0; k < n_params; ++k) p->mon_params[k] = params[k];
+    return SDD_OK;
+}
+
+sdd_status sdd_interface_mc(sdd_problem* p, double* est_xy, double* se_xy, int64_t* paths_used)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    SDD_TRY(run_prep(p));
+    const sdd_status s = run_mc(p);
+    if (s != SDD_OK && s != SDD_ERR_SE_NOT_REACHED) return s;
+    const size_t M = (size_t)p->M;
+    SDD_TRY(copy_out(p, est_xy, p->est, M * 16));
+    SDD_TRY(copy_out(p, se_xy, p->se, M * 16));
+    SDD_TRY(copy_out(p, paths_used, p->n_done, M * 8));
+    return s;
+}
+
+sdd_status sdd_subdomain_solve(sdd_problem* p, const double* iface_xy, double* x_out, double* y_out)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    SDD_TRY(run_prep(p));
+    if (iface_xy) {
+        SDD_TRY(copy_in(p, p->est, iface_xy, (size_t)p->M * 16));
+        p->have_est = true;
+    }
+    if (!p->have_est) return fail(SDD_ERR_INVALID_ARG, "no interface data: pass iface_xy or call sdd_interface_mc");
+    const sdd_status s = run_solve(p);
+    if (s != SDD_OK && s != SDD_ERR_NOT_CONVERGED) return s;
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_out(p, x_out, p->xn, N * 8));
+    SDD_TRY(copy_out(p, y_out, p->yn, N * 8));
+    return s;
+}
+
+sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    SDD_TRY(run_prep(p));
+    const sdd_status s_mc = run_mc(p);
+    if (s_mc != SDD_OK && s_mc != SDD_ERR_SE_NOT_REACHED) return s_mc;
+    const sdd_status s_sv = run_solve(p);
+    if (s_sv != SDD_OK && s_sv != SDD_ERR_NOT_CONVERGED) return s_sv;
+    double* t;
+    t = p->x; p->x = p->xn; p->xn = t;
+    t = p->y; p->y = p->yn; p->yn = t;
+    p->step += 1;
+    p->have_est = false;
+    p->stats.step_index = (int32_t)p->step;
+    p->stats.t = p->prm.t0 + (double)p->step * p->prm.dt;
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_out(p, x_out, p->x, N * 8));
+    SDD_TRY(copy_out(p, y_out, p->y, N * 8));
+    if (s_mc != SDD_OK) return fail(s_mc, "max_paths_per_node reached before se_target");
+    return s_sv;
+}
+
+sdd_status sdd_get_stats(const sdd_problem* p, sdd_stats* out)
+{
+    if (!p || !out) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    *out = p->stats;
+    out->kernel_launches = p->launches;
+    out->M = p->M;
+    out->step_index = (int32_t)p->step;
+    out->t = p->prm.t0 + (double)p->step * p->prm.dt;
+    return SDD_OK;
+}
+
+sdd_status sdd_get_interface_nodes(const sdd_problem* p, int32_t* ij, int32_t* M)
+{
+    if (!p || !M) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    *M = p->M;
+    if (ij && p->M > 0) memcpy(ij, p->ij.data(), p->ij.size() * sizeof(int32_t));
+    return SDD_OK;
+}
+
+sdd_status sdd_get_monitor(sdd_problem* p, double* omega, double* w_xi, double* w_eta)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    SDD_TRY(run_prep(p));
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_out(p, omega, p->om64, N * 8));
+    SDD_TRY(copy_out(p, w_xi, p->wxi64, N * 8));
+    SDD_TRY(copy_out(p, w_eta, p->weta64, N * 8));
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_t n_paths, double* val_xy,
+                           int32_t* exit_step, int8_t* exit_side)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    if (node < 0 || node >= p->M) return fail(SDD_ERR_INVALID_ARG, "node out of range");
+    if (n_paths < 1 || p_begin < 0 || p_begin + n_paths > ((int64_t)1 << 32))
+        return fail(SDD_ERR_INVALID_ARG, "path range out of [0, 2^32)");
+    const int64_t tasks = (n_paths + kPathsPerTask - 1) / kPathsPerTask;
+    if (tasks > p->slot_cap) return fail(SDD_ERR_INVALID_ARG, "too many paths for one debug call");
+    SDD_TRY(run_prep(p));
+    double* dval = nullptr;
+    int32_t* dst = nullptr;
+    int8_t* dsd = nullptr;
+    SDD_CK(cudaMalloc(&dval, (size_t)n_paths * 16));
+    cudaError_t e = cudaMalloc(&dst, (size_t)n_paths * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&dsd, (size_t)n_paths);
+    sdd_status s = SDD_OK;
+    if (e != cudaSuccess) s = fail(SDD_ERR_OOM, "debug buffers");
+    // one-node plan
+    const int32_t h_node = node, h_act = 1, h_zero = 0;
+    const int64_t h_off[2] = {0, tasks};
+    auto ck = [&](cudaError_t c) {
+        if (s == SDD_OK && c != cudaSuccess) s = fail(SDD_ERR_CUDA, cudaGetErrorString(c));
+    };
+    if (s == SDD_OK) {
+        ck(cudaMemcpyAsync(p->node_of, &h_node, 4, cudaMemcpyHostToDevice, p->stream));
+        ck(cudaMemcpyAsync(p->p_begin, &p_begin, 8, cudaMemcpyHostToDevice, p->stream));
+        ck(cudaMemcpyAsync(p->p_count, &n_paths, 8, cudaMemcpyHostToDevice, p->stream));
+        ck(cudaMemcpyAsync(p->task_off, h_off, 16, cudaMemcpyHostToDevice, p->stream));
+        ck(cudaMemcpyAsync(p->n_active, &h_act, 4, cudaMemcpyHostToDevice, p->stream));
+        ck(cudaMemcpyAsync(p->task_counter, &h_zero, 4, cudaMemcpyHostToDevice, p->stream));
+    }
+    if (s == SDD_OK) s = launch_mc_round(p, true, dval, dst, dsd, p_begin);
+    if (s == SDD_OK) s = copy_out(p, val_xy, dval, (size_t)n_paths * 16);
+    if (s == SDD_OK) s = copy_out(p, exit_step, dst, (size_t)n_paths * 4);
+    if (s == SDD_OK) s = copy_out(p, exit_side, dsd, (size_t)n_paths);
+    if (s == SDD_OK) ck(cudaStreamSynchronize(p->stream));
+    cudaFree(dval);
+    if (dst) cudaFree(dst);
+    if (dsd) cudaFree(dsd);
+    return s;
+}
+
+sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out)
+{
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(SDD_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return SDD_OK;
+    uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+    SDD_CK(cudaMalloc(&dc, (size_t)n * 16));
+    cudaError_t e = cudaMalloc(&dk, (size_t)n * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)n * 16);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, (size_t)n * 16, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaMemcpy(dk, key, (size_t)n * 8, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = launch_philox(dc, dk, n, dout, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)n * 16, cudaMemcpyDefault);
+    cudaFree(dc);
+    if (dk) cudaFree(dk);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(SDD_ERR_CUDA, cudaGetErrorString(e));
+    return SDD_OK;
+}
+
+}  // extern "C"

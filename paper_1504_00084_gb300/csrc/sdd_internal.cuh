@@ -1,0 +1,207 @@
+// Internal declarations of the SDD CUDA library (sm_103a).  Not part of the ABI.
+//
+// Kernels:
+//   sdd_prep.cu   monitor on the current mesh + FD gradient + packing (A1), Dirichlet rims and
+//                 interface scatter (A10), face coefficients of the subdomain systems
+//   sdd_mc.cu     interface Monte Carlo (A3-A9): one path per lane, Philox4x32-10,
+//                 Euler-Maruyama, exit tests, terminal values, deterministic reductions
+//   sdd_solve.cu  backward-Euler subdomain solves (A11): batched PCG, FP64 refinement
+//   sdd_api.cu    the C ABI
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sdd {
+
+// ---------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+//   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)),
+// key bumped by the Weyl increments between rounds.
+// ---------------------------------------------------------------------------------------
+struct U4 {
+    uint32_t x, y, z, w;
+};
+
+__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b)
+{
+#ifdef __CUDA_ARCH__
+    return __umulhi(a, b);
+#else
+    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
+#endif
+}
+
+__host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
+{
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = mulhi32(kM0, c.x), lo0 = kM0 * c.x;
+        const uint32_t hi1 = mulhi32(kM1, c.z), lo1 = kM1 * c.z;
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += kW0;
+        k1 += kW1;
+    }
+    return c;
+}
+
+// Uniform in (0, 1) from one word without rounding: FP32 keeps the top 23 bits,
+// u = (floor(w / 2^9) + 1/2) 2^-23; FP64 u = (w + 1/2) 2^-32.
+__device__ __forceinline__ float uniform_open(uint32_t w, float)
+{
+    return (__uint2float_rn(w >> 9) + 0.5f) * 0x1p-23f;
+}
+__device__ __forceinline__ double uniform_open(uint32_t w, double)
+{
+    return (__uint2double_rn(w) + 0.5) * 0x1p-32;
+}
+
+// ---------------------------------------------------------------------------------------
+// Packed per-node data read by the path kernel.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct alignas(4 * sizeof(T)) Mon4 {
+    T w, wx, we, pad;  // omega, d omega / d xi, d omega / d eta
+};
+template <typename T> struct alignas(2 * sizeof(T)) Disp2 {
+    T X, Y;            // previous mesh minus the identity: x - Lx xi, y - Ly eta
+};
+
+// Per-task partial sums written by one warp (deterministic order).
+struct alignas(16) TaskSlot {
+    double s1x, s2x, s1y, s2y;   // shifted sums of the path values and their squares
+    unsigned long long steps;    // substeps taken
+    unsigned long long paths;    // paths completed
+};
+
+enum AccMode { kAcc64 = 0, kAccKahan32 = 1 };
+
+// Paths handed to one warp at a time (64 per lane on average).
+constexpr int kPathsPerTask = 2048;
+// Adaptive chunk totals are multiples of this many paths.
+constexpr int64_t kAdaptiveGranule = 1024;
+
+template <typename T> struct McParams {
+    const Mon4<T>* mon;        // nx*ny packed monitor
+    const Disp2<T>* disp;      // nx*ny packed displacement of the previous mesh
+    const int2* nodes;         // M interface nodes (i, j)
+    const double* shift;       // M x 2 estimator shifts (node's previous position)
+    // round plan (written by the plan kernel)
+    const int32_t* node_of;    // active node ids
+    const int64_t* p_begin;    // first path index of each active node's chunk
+    const int64_t* p_count;    // chunk length
+    const int64_t* task_off;   // exclusive prefix of tasks per active node (n_active + 1)
+    const int32_t* n_active;   // device scalar
+    int32_t* task_counter;     // dynamic task dispenser (reset by the plan kernel)
+    TaskSlot* slots;           // one per task
+    // debug records (null unless the debug variant runs)
+    double* dbg_val;
+    int32_t* dbg_steps;
+    int8_t* dbg_side;
+    int64_t dbg_p0;
+    // problem
+    int nx, ny, periodic, form, K, bicubic, bb;
+    T cb;                      // ds / tau
+    T Lx, Ly;
+    uint32_t key0, key1, tstep;
+};
+
+struct PlanParams {
+    int M;
+    int64_t* n_done;           // paths accumulated per node
+    int64_t* next_total;       // scheduled total per node
+    int32_t* node_of;
+    int64_t* p_begin;
+    int64_t* p_count;
+    int64_t* task_off;
+    int32_t* n_active;
+    int32_t* task_counter;
+    int32_t* host_n_active;    // mapped pinned host word
+};
+
+struct ReduceParams {
+    const int32_t* node_of;
+    const int64_t* p_count;
+    const int64_t* task_off;
+    const int32_t* n_active;
+    const TaskSlot* slots;
+    const double* shift;
+    double* acc;               // M x 4 cumulative shifted sums
+    int64_t* n_done;
+    int64_t* steps;
+    int64_t* paths_run;        // M: paths completed per node (check)
+    int64_t* next_total;
+    double se_target;          // 0: fixed N
+    int64_t max_paths;
+};
+
+struct PrepParams {
+    int nx, ny, periodic, kind, n_params, precision;
+    double Lx, Ly, t;
+    const double* x;           // current mesh
+    const double* y;
+    const double* omega_in;    // nodal monitor (kind == NODAL)
+    double params[64];
+    double* om64;              // out: omega at the nodes (FP64)
+    double* wxi64;             // out: FD gradient (FP64)
+    double* weta64;
+    void* mon;                 // out: Mon4<T>
+    void* disp;                // out: Disp2<T>
+};
+
+struct SolveParams {
+    int nx, ny, px, py, form;
+    double r;                  // dt / tau
+    double rtol;
+    int max_iter;
+    const double* om64;        // omega at the nodes
+    const double* xcur;        // previous mesh (right-hand side)
+    const double* ycur;
+    double* xnew;              // new mesh: rims in, interiors out
+    double* ynew;
+    double* ce64;              // east-face coefficients r w_{i+1/2,j} / h_xi^2   (nx*ny)
+    double* cn64;              // north-face coefficients r w_{i,j+1/2} / h_eta^2 (nx*ny)
+    void* ce;                  // the same in the inner precision
+    void* cn;
+    void* vec;                 // inner vectors: 4 x nx*ny pairs (e, r, p, q), rims zero
+    int32_t* stat_iters;       // per subdomain: PCG iterations, refinement sweeps, converged
+    int32_t* stat_outer;
+    int32_t* stat_ok;
+    double* stat_res;          // per subdomain: final relative residual (max of x, y)
+};
+
+// Launchers (return cudaGetLastError of the launch).
+cudaError_t launch_prep(const PrepParams& P, cudaStream_t s);
+cudaError_t launch_shift(const int2* nodes, int M, int nx, const double* x, const double* y,
+                         double* shift, cudaStream_t s);
+cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, const int2* nodes,
+                           int M, const double* est, double* xnew, double* ynew, cudaStream_t s);
+cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
+                           int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s);
+cudaError_t launch_plan(const PlanParams& P, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, int grid, cudaStream_t s);
+template <typename T> int mc_max_blocks_per_sm(int acc_mode, bool debug);
+cudaError_t launch_reduce(const ReduceParams& P, int M, cudaStream_t s);
+cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const double* shift,
+                          double* est, double* se, cudaStream_t s);
+cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                          cudaStream_t s);
+
+// Host/device shared scheduling rule of the adaptive estimator.
+__host__ __device__ inline int64_t adaptive_next_total(int64_t n_done, double se, double target,
+                                                       int64_t max_paths)
+{
+    if (se <= target || n_done >= max_paths) return n_done;
+    const double r = se / target;
+    const double want = ((double)n_done * (r * r)) * 1.1;
+    double total = ceil(want / (double)kAdaptiveGranule) * (double)kAdaptiveGranule;
+    const double floor_total = (double)(n_done + kAdaptiveGranule);
+    if (total < floor_total) total = floor_total;
+    if (total > (double)max_paths) total = (double)max_paths;
+    return (int64_t)total;
+}
+
+}  // namespace sdd

@@ -1,0 +1,672 @@
+// Interface Monte Carlo of the SDD mesh generator (Sec. 3.4), sm_103a.
+//
+// Work decomposition.  A round gives every active interface node a chunk of consecutive
+// path indices; chunks are cut into tasks of kPathsPerTask paths.  A persistent grid of warps
+// pulls tasks from an atomic counter.  Inside a task each lane runs one path at a time and,
+// when its path ends (exit or K substeps), immediately takes the next unused path index of
+// the task (ballot + popc), so the 32 lanes stay busy through paths of very different
+// lengths.  The assignment of path indices to lanes depends only on the paths' own lengths,
+// so a task's partial sums are a deterministic function of (node, path range) and are
+// independent of scheduling and of which other problems or nodes share the launch.
+//
+// Per substep and lane: one Philox4x32-10 call keyed by the seed with counter
+// (k, p, m, n) -> Box-Muller normals (words 0, 1) and the bridge uniform (word 2); bilinear
+// gather of {omega, omega_xi, omega_eta} from the packed monitor (read-only cache; the
+// record of a node is one 16-byte (FP32) or 32-byte (FP64) load); Euler-Maruyama update
+// (Eq. 7); endpoint and Brownian-bridge exit tests.  Terminal values: the boundary mesh at
+// the exit point, or the Keys-bicubic previous mesh at the final point (Eq. 5a, Eq. 6).
+//
+// Reductions: per-lane sums of the shifted values (FP64, or Kahan-compensated FP32), a
+// fixed xor-shuffle tree per task, one slot per task, then one warp per node adds its slots
+// in task order.  No floating-point atomics: results are bitwise reproducible.
+#include <math.h>
+
+#include "sdd_internal.cuh"
+
+namespace sdd {
+
+namespace {
+
+constexpr int kMcThreads = 256;
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float dlog(float x) { return logf(x); }
+__device__ __forceinline__ double dlog(double x) { return log(x); }
+__device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float dexp(float x) { return expf(x); }
+__device__ __forceinline__ double dexp(double x) { return exp(x); }
+__device__ __forceinline__ float dfloor(float x) { return floorf(x); }
+__device__ __forceinline__ double dfloor(double x) { return floor(x); }
+__device__ __forceinline__ float dabs(float x) { return fabsf(x); }
+__device__ __forceinline__ double dabs(double x) { return fabs(x); }
+__device__ __forceinline__ void dsincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void dsincos(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename T> struct Consts;
+template <> struct Consts<float> {
+    static constexpr float two_pi = 6.28318530717958647692f;
+    // exp(-a) below this argument's reach leaves 1 - exp(-a) == 1 exactly (and cannot be the
+    // largest crossing probability of an exiting path), so the exponential is skipped.
+    static constexpr float bridge_skip = 20.0f;
+};
+template <> struct Consts<double> {
+    static constexpr double two_pi = 6.28318530717958647692;
+    static constexpr double bridge_skip = 40.0;
+};
+
+__device__ __forceinline__ Mon4<float> load_mon(const Mon4<float>* p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return Mon4<float>{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Mon4<double> load_mon(const Mon4<double>* p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    return Mon4<double>{a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ Disp2<float> load_disp(const Disp2<float>* p)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return Disp2<float>{v.x, v.y};
+}
+__device__ __forceinline__ Disp2<double> load_disp(const Disp2<double>* p)
+{
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return Disp2<double>{v.x, v.y};
+}
+
+// Cell and in-cell offset of coordinate s on an n-node line over [0, 1]; periodic lines repeat
+// with period 1 over n - 1 distinct nodes.
+template <typename T>
+__device__ __forceinline__ void locate(int n, int periodic, T s, int& cell, T& frac)
+{
+    const T u = s * (T)(n - 1);
+    const T fl = dfloor(u);
+    int c = (int)fl;
+    if (periodic) {
+        const int m = n - 1;
+        c %= m;
+        if (c < 0) c += m;
+        frac = u - fl;
+    } else {
+        c = c < 0 ? 0 : (c > n - 2 ? n - 2 : c);
+        frac = u - (T)c;
+    }
+    cell = c;
+}
+
+// Bilinear interpolation of the packed monitor at (xi, eta) (Sec. 3.4).
+template <typename T>
+__device__ __forceinline__ void monitor_at(const McParams<T>& P, T xi, T eta, T& w, T& wx, T& we)
+{
+    int i, j;
+    T fx, fy;
+    locate(P.nx, P.periodic, xi, i, fx);
+    locate(P.ny, P.periodic, eta, j, fy);
+    const Mon4<T>* r0 = P.mon + (long)j * P.nx + i;
+    const Mon4<T> a = load_mon(r0), b = load_mon(r0 + 1);
+    const Mon4<T> c = load_mon(r0 + P.nx), d = load_mon(r0 + P.nx + 1);
+    const T gx = 1 - fx, gy = 1 - fy;
+    const T w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
+    w = w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w;
+    wx = w00 * a.wx + w10 * b.wx + w01 * c.wx + w11 * d.wx;
+    we = w00 * a.we + w10 * b.we + w01 * c.we + w11 * d.we;
+}
+
+// Keys (1981) cubic-convolution kernel, a = -1/2.
+template <typename T>
+__device__ __forceinline__ T keys_kernel(T s)
+{
+    const T a = (T)-0.5;
+    s = dabs(s);
+    if (s <= 1) return (a + 2) * s * s * s - (a + 3) * s * s + 1;
+    if (s < 2) return a * s * s * s - 5 * a * s * s + 8 * a * s - 4 * a;
+    return 0;
+}
+
+template <typename T>
+__device__ __forceinline__ T keys_combine(const T g[4], const T k[4])
+{
+    return g[0] * k[0] + g[1] * k[1] + g[2] * k[2] + g[3] * k[3];
+}
+
+// Previous mesh displacement (X, Y) at (xi, eta): Keys bicubic with Keys' boundary
+// extrapolation f(-1) = 3 f(0) - 3 f(1) + f(2) on Dirichlet grids, wrapped on periodic
+// grids; or bilinear.
+template <typename T>
+__device__ void mesh_at(const McParams<T>& P, T xi, T eta, T& ix, T& iy)
+{
+    int i, j;
+    T tx, ty;
+    locate(P.nx, P.periodic, xi, i, tx);
+    locate(P.ny, P.periodic, eta, j, ty);
+    const int nx = P.nx, ny = P.ny;
+    if (!P.bicubic) {
+        const Disp2<T>* r0 = P.disp + (long)j * nx + i;
+        const Disp2<T> a = load_disp(r0), b = load_disp(r0 + 1);
+        const Disp2<T> c = load_disp(r0 + nx), d = load_disp(r0 + nx + 1);
+        const T gx = 1 - tx, gy = 1 - ty;
+        ix = gx * gy * a.X + tx * gy * b.X + gx * ty * c.X + tx * ty * d.X;
+        iy = gx * gy * a.Y + tx * gy * b.Y + gx * ty * c.Y + tx * ty * d.Y;
+        return;
+    }
+    const T kx[4] = {keys_kernel<T>(1 + tx), keys_kernel<T>(tx), keys_kernel<T>(1 - tx),
+                     keys_kernel<T>(2 - tx)};
+    const T ky[4] = {keys_kernel<T>(1 + ty), keys_kernel<T>(ty), keys_kernel<T>(1 - ty),
+                     keys_kernel<T>(2 - ty)};
+    T gX[4] = {0, 0, 0, 0}, gY[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        int r = j - 1 + b;
+        if (P.periodic) {
+            const int m = ny - 1;
+            r = ((r % m) + m) % m;
+        } else if (r < 0 || r > ny - 1) {
+            continue;
+        }
+        const Disp2<T>* row = P.disp + (long)r * nx;
+        T cX[4], cY[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            int c = i - 1 + a;
+            if (P.periodic) {
+                const int m = nx - 1;
+                c = ((c % m) + m) % m;
+                const Disp2<T> v = load_disp(row + c);
+                cX[a] = v.X;
+                cY[a] = v.Y;
+            } else if (c < 0) {
+                const Disp2<T> v0 = load_disp(row), v1 = load_disp(row + 1), v2 = load_disp(row + 2);
+                cX[a] = 3 * v0.X - 3 * v1.X + v2.X;
+                cY[a] = 3 * v0.Y - 3 * v1.Y + v2.Y;
+            } else if (c > nx - 1) {
+                const Disp2<T> v0 = load_disp(row + nx - 1), v1 = load_disp(row + nx - 2),
+                               v2 = load_disp(row + nx - 3);
+                cX[a] = 3 * v0.X - 3 * v1.X + v2.X;
+                cY[a] = 3 * v0.Y - 3 * v1.Y + v2.Y;
+            } else {
+                const Disp2<T> v = load_disp(row + c);
+                cX[a] = v.X;
+                cY[a] = v.Y;
+            }
+        }
+        gX[b] = keys_combine(cX, kx);
+        gY[b] = keys_combine(cY, kx);
+    }
+    if (!P.periodic) {
+        if (j - 1 < 0) {
+            gX[0] = 3 * gX[1] - 3 * gX[2] + gX[3];
+            gY[0] = 3 * gY[1] - 3 * gY[2] + gY[3];
+        }
+        if (j + 2 > ny - 1) {
+            gX[3] = 3 * gX[2] - 3 * gX[1] + gX[0];
+            gY[3] = 3 * gY[2] - 3 * gY[1] + gY[0];
+        }
+    }
+    ix = keys_combine(gX, ky);
+    iy = keys_combine(gY, ky);
+}
+
+template <typename T>
+__device__ __forceinline__ T clamp01(T v) { return v < 0 ? (T)0 : (v > 1 ? (T)1 : v); }
+
+// One substep k of path p at node m.  Returns true when the path ends at this substep
+// (exit, or k == K - 1); then (vx, vy) is its value and side its exit side (4: none).
+template <typename T>
+__device__ __forceinline__ bool path_substep(const McParams<T>& P, uint32_t m, uint32_t p, int k,
+                                             T& xi, T& eta, T& vx, T& vy, int& side)
+{
+    const U4 w = philox4x32_10(U4{(uint32_t)k, p, m, P.tstep}, P.key0, P.key1);
+    const T u1 = uniform_open(w.x, T()), u2 = uniform_open(w.y, T()), ub = uniform_open(w.z, T());
+    const T r = dsqrt((T)-2 * dlog(u1));
+    T sn, cs;
+    dsincos(Consts<T>::two_pi * u2, &sn, &cs);
+    const T z1 = r * cs, z2 = r * sn;
+
+    T wv, wx, we;
+    monitor_at(P, xi, eta, wv, wx, we);
+    T q, bx, by;  // q = D ds, (bx, by) = drift * ds
+    if (P.form == 0) {
+        q = wv * P.cb;
+        bx = wx * P.cb;
+        by = we * P.cb;
+    } else {
+        q = P.cb;
+        bx = wx / wv * P.cb;
+        by = we / wv * P.cb;
+    }
+    const T sd = dsqrt(2 * q);
+    const T xn = xi + bx + sd * z1;
+    const T en = eta + by + sd * z2;
+
+    if (!P.periodic) {
+        const T viol[4] = {-xn, xn - 1, -en, en - 1};
+        int s = 0;
+#pragma unroll
+        for (int t = 1; t < 4; ++t)
+            if (viol[t] > viol[s]) s = t;
+        bool exited = viol[s] > 0;
+        if (!exited && P.bb) {
+            const T d0[4] = {xi, 1 - xi, eta, 1 - eta};
+            const T d1[4] = {xn, 1 - xn, en, 1 - en};
+            T pr[4];
+            T surv = 1;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const T a = d0[t] * d1[t];
+                pr[t] = (a > Consts<T>::bridge_skip * q) ? (T)0 : dexp(-a / q);
+                surv *= (1 - pr[t]);
+            }
+            if (ub > surv) {
+                exited = true;
+                s = 0;
+#pragma unroll
+                for (int t = 1; t < 4; ++t)
+                    if (pr[t] > pr[s]) s = t;
+            }
+        }
+        if (exited) {
+            T xe = clamp01(xn), ee = clamp01(en);
+            if (s == 0) xe = 0;
+            if (s == 1) xe = 1;
+            if (s == 2) ee = 0;
+            if (s == 3) ee = 1;
+            vx = P.Lx * xe;
+            vy = P.Ly * ee;
+            side = s;
+            return true;
+        }
+    }
+    xi = xn;
+    eta = en;
+    if (k + 1 == P.K) {
+        T ix, iy;
+        mesh_at(P, xi, eta, ix, iy);
+        vx = P.Lx * xi + ix;
+        vy = P.Ly * eta + iy;
+        side = 4;
+        return true;
+    }
+    return false;
+}
+
+// Per-lane estimator sums.
+template <typename T, int ACC> struct LaneAcc;
+template <typename T> struct LaneAcc<T, kAcc64> {
+    double s1x = 0, s2x = 0, s1y = 0, s2y = 0;
+    __device__ __forceinline__ void add(T vx, T vy, double sx, double sy)
+    {
+        const double dx = (double)vx - sx, dy = (double)vy - sy;
+        s1x += dx;
+        s2x += dx * dx;
+        s1y += dy;
+        s2y += dy * dy;
+    }
+    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, double, double,
+                                           unsigned long long) const
+    {
+        a = s1x; b = s2x; c = s1y; d = s2y;
+    }
+};
+// Kahan-compensated FP32 sums of v - fl(shift); converted to the exact shift at the end.
+template <typename T> struct LaneAcc<T, kAccKahan32> {
+    float s1x = 0, c1x = 0, s2x = 0, c2x = 0, s1y = 0, c1y = 0, s2y = 0, c2y = 0;
+    __device__ __forceinline__ static void kahan(float& s, float& c, float v)
+    {
+        const float y = __fsub_rn(v, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ void add(T vx, T vy, double sx, double sy)
+    {
+        const float dx = __fsub_rn((float)vx, (float)sx), dy = __fsub_rn((float)vy, (float)sy);
+        kahan(s1x, c1x, dx);
+        kahan(s2x, c2x, __fmul_rn(dx, dx));
+        kahan(s1y, c1y, dy);
+        kahan(s2y, c2y, __fmul_rn(dy, dy));
+    }
+    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, double sx,
+                                           double sy, unsigned long long n) const
+    {
+        // sums of (v - fl(s)) -> sums of (v - s) with delta = s - fl(s)
+        const double ex = sx - (double)(float)sx, ey = sy - (double)(float)sy;
+        const double S1x = (double)s1x - (double)c1x, S2x = (double)s2x - (double)c2x;
+        const double S1y = (double)s1y - (double)c1y, S2y = (double)s2y - (double)c2y;
+        const double nn = (double)n;
+        a = S1x - nn * ex;
+        b = S2x - 2.0 * ex * S1x + nn * ex * ex;
+        c = S1y - nn * ey;
+        d = S2y - 2.0 * ey * S1y + nn * ey * ey;
+    }
+};
+
+template <typename T, int ACC, bool DEBUG>
+__global__ void __launch_bounds__(kMcThreads) mc_kernel(const __grid_constant__ McParams<T> P)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int n_active = *P.n_active;
+    const int64_t n_tasks = P.task_off[n_active];
+    for (;;) {
+        int task = 0;
+        if (lane == 0) task = atomicAdd(P.task_counter, 1);
+        task = __shfl_sync(kFull, task, 0);
+        if ((int64_t)task >= n_tasks) break;
+        int lo = 0, hi = n_active - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.task_off[mid] <= task) lo = mid; else hi = mid - 1;
+        }
+        const int m = P.node_of[lo];
+        const int64_t chunk_end = P.p_begin[lo] + P.p_count[lo];
+        const int64_t pb = P.p_begin[lo] + ((int64_t)task - P.task_off[lo]) * kPathsPerTask;
+        const int64_t pe = pb + kPathsPerTask < chunk_end ? pb + kPathsPerTask : chunk_end;
+        const int2 ij = P.nodes[m];
+        const T xi0 = (T)ij.x / (T)(P.nx - 1);
+        const T eta0 = (T)ij.y / (T)(P.ny - 1);
+        const double sx = P.shift[2 * m], sy = P.shift[2 * m + 1];
+
+        LaneAcc<T, ACC> acc;
+        unsigned long long steps = 0, paths = 0;
+        int64_t path = pb + lane;
+        bool live = path < pe;
+        int64_t next = pb + 32;
+        T xi = xi0, eta = eta0;
+        int k = 0;
+        while (__any_sync(kFull, live)) {
+            bool done = false;
+            if (live) {
+                T vx, vy;
+                int side;
+                done = path_substep<T>(P, (uint32_t)m, (uint32_t)path, k, xi, eta, vx, vy, side);
+                ++k;
+                if (done) {
+                    acc.add(vx, vy, sx, sy);
+                    steps += (unsigned long long)k;
+                    paths += 1;
+                    if (DEBUG) {
+                        const int64_t qd = path - P.dbg_p0;
+                        P.dbg_val[2 * qd] = (double)vx;
+                        P.dbg_val[2 * qd + 1] = (double)vy;
+                        P.dbg_steps[qd] = k;
+                        P.dbg_side[qd] = (int8_t)side;
+                    }
+                }
+            }
+            const unsigned dm = __ballot_sync(kFull, done);
+            if (done) {
+                path = next + __popc(dm & lt);
+                live = path < pe;
+                xi = xi0;
+                eta = eta0;
+                k = 0;
+            }
+            next += __popc(dm);
+        }
+        double a, b, c, d;
+        acc.finish(a, b, c, d, sx, sy, paths);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            a += __shfl_xor_sync(kFull, a, off);
+            b += __shfl_xor_sync(kFull, b, off);
+            c += __shfl_xor_sync(kFull, c, off);
+            d += __shfl_xor_sync(kFull, d, off);
+            steps += __shfl_xor_sync(kFull, steps, off);
+            paths += __shfl_xor_sync(kFull, paths, off);
+        }
+        if (lane == 0) P.slots[task] = TaskSlot{a, b, c, d, steps, paths};
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Round plan: compact the nodes that still need paths, cut their chunks into tasks.
+// One block; node order is preserved so the plan is deterministic.
+// ---------------------------------------------------------------------------------------
+constexpr int kPlanThreads = 1024;
+constexpr int64_t kMaxChunkPerRound = int64_t(1) << 19;
+
+template <typename V>
+__device__ V block_exclusive_scan(V v, V* warp_tot, V& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    V incl = v;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const V o = __shfl_up_sync(kFull, incl, off);
+        if (lane >= off) incl += o;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        V t = lane < nw ? warp_tot[lane] : (V)0;
+        V ti = t;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const V o = __shfl_up_sync(kFull, ti, off);
+            if (lane >= off) ti += o;
+        }
+        if (lane < nw) warp_tot[lane] = ti - t;   // exclusive prefix of warp totals
+        if (lane == nw - 1) warp_tot[32] = ti;    // block total
+    }
+    __syncthreads();
+    const V res = warp_tot[wid] + incl - v;
+    total = warp_tot[32];
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
+{
+    __shared__ int64_t s_tasks[33];
+    __shared__ int s_act[33];
+    int64_t task_base = 0;
+    int act_base = 0;
+    for (int base = 0; base < P.M; base += kPlanThreads) {
+        const int m = base + threadIdx.x;
+        int64_t cnt = 0;
+        if (m < P.M) {
+            cnt = P.next_total[m] - P.n_done[m];
+            if (cnt > kMaxChunkPerRound) cnt = kMaxChunkPerRound;
+            if (cnt < 0) cnt = 0;
+        }
+        const int act = cnt > 0 ? 1 : 0;
+        const int64_t tasks = act ? (cnt + kPathsPerTask - 1) / kPathsPerTask : 0;
+        int act_tot;
+        int64_t task_tot;
+        const int a_ex = block_exclusive_scan<int>(act, s_act, act_tot);
+        const int64_t t_ex = block_exclusive_scan<int64_t>(tasks, s_tasks, task_tot);
+        if (act) {
+            const int a = act_base + a_ex;
+            P.node_of[a] = m;
+            P.p_begin[a] = P.n_done[m];
+            P.p_count[a] = cnt;
+            P.task_off[a] = task_base + t_ex;
+        }
+        act_base += act_tot;
+        task_base += task_tot;
+    }
+    if (threadIdx.x == 0) {
+        P.task_off[act_base] = task_base;
+        *P.n_active = act_base;
+        *P.task_counter = 0;
+    }
+}
+
+__global__ void mc_init_kernel(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
+                               int64_t* steps, int64_t* paths_run, int64_t* next_total)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    acc[4 * m] = acc[4 * m + 1] = acc[4 * m + 2] = acc[4 * m + 3] = 0.0;
+    n_done[m] = 0;
+    steps[m] = 0;
+    paths_run[m] = 0;
+    next_total[m] = n0 < max_paths ? n0 : max_paths;
+}
+
+__device__ __forceinline__ void node_estimate(const double* s, double n, double sx, double sy,
+                                              double& mx, double& my, double& ex, double& ey)
+{
+    mx = sx + s[0] / n;
+    my = sy + s[2] / n;
+    double vx = (s[1] - s[0] * s[0] / n) / (n - 1.0);
+    double vy = (s[3] - s[2] * s[2] / n) / (n - 1.0);
+    vx = vx > 0 ? vx : 0.0;
+    vy = vy > 0 ? vy : 0.0;
+    ex = sqrt(vx / n);
+    ey = sqrt(vy / n);
+}
+
+// One warp per active node: add its task slots in task order to the node's sums, then
+// schedule its next total (adaptive mode).
+__global__ void reduce_kernel(const ReduceParams P)
+{
+    const int lane = threadIdx.x & 31;
+    const int a = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (a >= *P.n_active) return;
+    const int m = P.node_of[a];
+    const int64_t t0 = P.task_off[a], t1 = P.task_off[a + 1];
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    unsigned long long st = 0, np = 0;
+    for (int64_t t = t0 + lane; t < t1; t += 32) {
+        const TaskSlot v = P.slots[t];
+        s0 += v.s1x; s1 += v.s2x; s2 += v.s1y; s3 += v.s2y;
+        st += v.steps; np += v.paths;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        s0 += __shfl_xor_sync(kFull, s0, off);
+        s1 += __shfl_xor_sync(kFull, s1, off);
+        s2 += __shfl_xor_sync(kFull, s2, off);
+        s3 += __shfl_xor_sync(kFull, s3, off);
+        st += __shfl_xor_sync(kFull, st, off);
+        np += __shfl_xor_sync(kFull, np, off);
+    }
+    if (lane != 0) return;
+    double* s = P.acc + 4 * m;
+    s[0] += s0; s[1] += s1; s[2] += s2; s[3] += s3;
+    P.steps[m] += (int64_t)st;
+    P.paths_run[m] += (int64_t)np;
+    const int64_t n = P.n_done[m] + P.p_count[a];
+    P.n_done[m] = n;
+    if (n < P.next_total[m]) return;  // chunk capped by the round size: keep the schedule
+    if (P.se_target > 0) {
+        double mx, my, ex, ey;
+        node_estimate(s, (double)n, P.shift[2 * m], P.shift[2 * m + 1], mx, my, ex, ey);
+        P.next_total[m] = adaptive_next_total(n, ex > ey ? ex : ey, P.se_target, P.max_paths);
+    } else {
+        P.next_total[m] = n;
+    }
+}
+
+__global__ void output_kernel(int M, const double* acc, const int64_t* n_done, const double* shift,
+                              double* est, double* se)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double mx, my, ex, ey;
+    node_estimate(acc + 4 * m, (double)n_done[m], shift[2 * m], shift[2 * m + 1], mx, my, ex, ey);
+    est[2 * m] = mx;
+    est[2 * m + 1] = my;
+    se[2 * m] = ex;
+    se[2 * m + 1] = ey;
+}
+
+__global__ void philox_kernel(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const U4 r = philox4x32_10(U4{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]},
+                               key[2 * i], key[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+}
+
+template <typename T, int ACC, bool DEBUG>
+const void* mc_kernel_ptr()
+{
+    return reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG>);
+}
+
+template <typename T>
+const void* select_mc(int acc_mode, bool debug)
+{
+    if (debug) return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, true>()
+                                              : mc_kernel_ptr<T, kAcc64, true>();
+    return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false>()
+                                   : mc_kernel_ptr<T, kAcc64, false>();
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, int grid, cudaStream_t s)
+{
+    if (debug) {
+        if (acc_mode == kAccKahan32) mc_kernel<T, kAccKahan32, true><<<grid, kMcThreads, 0, s>>>(P);
+        else mc_kernel<T, kAcc64, true><<<grid, kMcThreads, 0, s>>>(P);
+    } else {
+        if (acc_mode == kAccKahan32) mc_kernel<T, kAccKahan32, false><<<grid, kMcThreads, 0, s>>>(P);
+        else mc_kernel<T, kAcc64, false><<<grid, kMcThreads, 0, s>>>(P);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+int mc_max_blocks_per_sm(int acc_mode, bool debug)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_mc<T>(acc_mode, debug), kMcThreads,
+                                                      0) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
+
+template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, int, cudaStream_t);
+template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, int, cudaStream_t);
+template int mc_max_blocks_per_sm<float>(int, bool);
+template int mc_max_blocks_per_sm<double>(int, bool);
+
+cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
+                           int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s)
+{
+    mc_init_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, n0, max_paths, acc, n_done, steps, paths_run,
+                                                   next_total);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plan(const PlanParams& P, cudaStream_t s)
+{
+    plan_kernel<<<1, kPlanThreads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const ReduceParams& P, int M, cudaStream_t s)
+{
+    const int threads = 256;
+    const long warps = M;
+    reduce_kernel<<<(int)((warps * 32 + threads - 1) / threads), threads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const double* shift,
+                          double* est, double* se, cudaStream_t s)
+{
+    output_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, acc, n_done, shift, est, se);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
+                          cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    philox_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(ctr, key, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace sdd

@@ -1,0 +1,203 @@
+// Monitor preparation and Dirichlet-data scatter (grid-sized, HBM/L2-bound, negligible next
+// to the path kernel).
+//
+//   prep_omega_kernel : omega at every node on the current mesh at t^n (Sec. 2, Sec. 3.2),
+//                       FP64; periodic wrap nodes evaluate their canonical node so they
+//                       repeat it bit for bit.
+//   prep_pack_kernel  : finite-difference gradient of omega in the computational
+//                       coordinates (Sec. 3.4), the packed {omega, omega_xi, omega_eta}
+//                       record of every node in the path precision, and the previous mesh
+//                       as a displacement from the identity.
+//   scatter kernels   : the new mesh's Dirichlet data -- physical boundary (identity) and
+//                       interface estimates with periodic offsets (Sec. 3.5).
+//   face kernel       : face coefficients of the backward-Euler subdomain systems.
+//
+// The prep arithmetic uses explicit round-to-nearest intrinsics (no fused multiply-add), so
+// the FP64 monitor record is reproducible independently of compiler contraction choices.
+#include <math.h>
+
+#include "sdd_internal.cuh"
+
+namespace sdd {
+
+namespace {
+
+constexpr int kMonGauss = 1, kMonFront = 2;  // otherwise bumps (3) or nodal (0)
+
+__device__ __forceinline__ double min_image(double d, double L, int periodic)
+{
+    return periodic ? d - L * floor(d / L + 0.5) : d;
+}
+
+__device__ double monitor_value(const PrepParams& P, double x, double y)
+{
+    const double* q = P.params;
+    if (P.kind == kMonGauss) {
+        const double dx = min_image(x - q[2], P.Lx, P.periodic);
+        const double dy = min_image(y - q[3], P.Ly, P.periodic);
+        return sqrt(1.0 + q[0] * exp(-q[1] * (dx * dx + dy * dy)));
+    }
+    if (P.kind == kMonFront) {
+        const double dx = min_image(x - q[4], P.Lx, P.periodic);
+        const double dy = min_image(y - q[5], P.Ly, P.periodic);
+        const double r = sqrt(dx * dx + dy * dy);
+        const double u = tanh(q[1] * (r - q[2] - q[3] * P.t));
+        const double g = q[1] * (1.0 - u * u);      // |grad u|
+        return sqrt(1.0 + q[0] * g * g);
+    }
+    double w = 1.0;                                  // bumps
+    for (int b = 0; b + 3 < P.n_params; b += 4) {
+        const double dx = min_image(x - q[b + 2], P.Lx, P.periodic);
+        const double dy = min_image(y - q[b + 3], P.Ly, P.periodic);
+        w += q[b] * exp(-(dx * dx + dy * dy) / (q[b + 1] * q[b + 1]));
+    }
+    return w;
+}
+
+__global__ void prep_omega_kernel(const PrepParams P)
+{
+    const int n = P.nx * P.ny;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+        const int i = id % P.nx, j = id / P.nx;
+        const int ci = P.periodic ? i % (P.nx - 1) : i;
+        const int cj = P.periodic ? j % (P.ny - 1) : j;
+        const int c = cj * P.nx + ci;
+        P.om64[id] = P.kind == 0 ? P.omega_in[c] : monitor_value(P, P.x[c], P.y[c]);
+    }
+}
+
+// d f / d s along one grid line at index i of n nodes: central differences in the interior,
+// one-sided second order at Dirichlet ends, wrapped when periodic; factor c = (n - 1) / 2.
+__device__ __forceinline__ double fd_line(const double* f, long stride, int i, int n, int periodic)
+{
+    const double c = 0.5 * (double)(n - 1);
+    if (periodic) {
+        const int m = n - 1;
+        const int ii = i % m;
+        const int ip = (ii + 1) % m, im = (ii + m - 1) % m;
+        return __dmul_rn(__dsub_rn(f[ip * stride], f[im * stride]), c);
+    }
+    if (i == 0)
+        return __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn(-3.0, f[0]), __dmul_rn(4.0, f[stride])),
+                                   f[2 * stride]), c);
+    if (i == n - 1)
+        return __dmul_rn(__dsub_rn(__dadd_rn(__dmul_rn(3.0, f[(long)(n - 1) * stride]),
+                                             __dmul_rn(-4.0, f[(long)(n - 2) * stride])),
+                                   -f[(long)(n - 3) * stride]), c);
+    return __dmul_rn(__dsub_rn(f[(long)(i + 1) * stride], f[(long)(i - 1) * stride]), c);
+}
+
+template <typename T>
+__global__ void prep_pack_kernel(const PrepParams P)
+{
+    const int n = P.nx * P.ny;
+    Mon4<T>* mon = static_cast<Mon4<T>*>(P.mon);
+    Disp2<T>* disp = static_cast<Disp2<T>*>(P.disp);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+        const int i = id % P.nx, j = id / P.nx;
+        const double w = P.om64[id];
+        const double wx = fd_line(P.om64 + (long)j * P.nx, 1, i, P.nx, P.periodic);
+        const double we = fd_line(P.om64 + i, P.nx, j, P.ny, P.periodic);
+        P.wxi64[id] = wx;
+        P.weta64[id] = we;
+        mon[id] = Mon4<T>{(T)w, (T)wx, (T)we, (T)0};
+        const int ci = P.periodic ? i % (P.nx - 1) : i;
+        const int cj = P.periodic ? j % (P.ny - 1) : j;
+        const int c = cj * P.nx + ci;
+        const double xi = (double)ci / (double)(P.nx - 1);
+        const double eta = (double)cj / (double)(P.ny - 1);
+        const double X = __dsub_rn(P.x[c], __dmul_rn(P.Lx, xi));
+        const double Y = __dsub_rn(P.y[c], __dmul_rn(P.Ly, eta));
+        disp[id] = Disp2<T>{(T)X, (T)Y};
+    }
+}
+
+__global__ void shift_kernel(const int2* nodes, int M, int nx, const double* x, const double* y,
+                             double* shift)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int2 ij = nodes[m];
+    shift[2 * m] = x[(long)ij.y * nx + ij.x];
+    shift[2 * m + 1] = y[(long)ij.y * nx + ij.x];
+}
+
+__global__ void scatter_boundary_kernel(int nx, int ny, double Lx, double Ly, double* xnew,
+                                        double* ynew)
+{
+    const int n = nx * ny;
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+        const int i = id % nx, j = id / nx;
+        if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
+            xnew[id] = Lx * ((double)i / (double)(nx - 1));
+            ynew[id] = Ly * ((double)j / (double)(ny - 1));
+        }
+    }
+}
+
+__global__ void scatter_iface_kernel(int nx, int ny, int periodic, double Lx, double Ly,
+                                     const int2* nodes, int M, const double* est, double* xnew,
+                                     double* ynew)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int2 ij = nodes[m];
+    const double vx = est[2 * m], vy = est[2 * m + 1];
+    const long id = (long)ij.y * nx + ij.x;
+    xnew[id] = vx;
+    ynew[id] = vy;
+    if (periodic) {
+        if (ij.x == 0) {
+            xnew[id + nx - 1] = vx + Lx;
+            ynew[id + nx - 1] = vy;
+        }
+        if (ij.y == 0) {
+            const long w = (long)(ny - 1) * nx + ij.x;
+            xnew[w] = vx;
+            ynew[w] = vy + Ly;
+        }
+        if (ij.x == 0 && ij.y == 0) {
+            const long w = (long)(ny - 1) * nx + nx - 1;
+            xnew[w] = vx + Lx;
+            ynew[w] = vy + Ly;
+        }
+    }
+}
+
+inline int blocks_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_prep(const PrepParams& P, cudaStream_t s)
+{
+    const long n = (long)P.nx * P.ny;
+    const int threads = 256;
+    const int blocks = blocks_for(n, threads);
+    prep_omega_kernel<<<blocks, threads, 0, s>>>(P);
+    if (P.precision == 0)
+        prep_pack_kernel<double><<<blocks, threads, 0, s>>>(P);
+    else
+        prep_pack_kernel<float><<<blocks, threads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift(const int2* nodes, int M, int nx, const double* x, const double* y,
+                         double* shift, cudaStream_t s)
+{
+    shift_kernel<<<blocks_for(M, 256), 256, 0, s>>>(nodes, M, nx, x, y, shift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, const int2* nodes,
+                           int M, const double* est, double* xnew, double* ynew, cudaStream_t s)
+{
+    if (!periodic)
+        scatter_boundary_kernel<<<blocks_for((long)nx * ny, 256), 256, 0, s>>>(nx, ny, Lx, Ly, xnew,
+                                                                               ynew);
+    if (M > 0)
+        scatter_iface_kernel<<<blocks_for(M, 256), 256, 0, s>>>(nx, ny, periodic, Lx, Ly, nodes, M, est,
+                                                                xnew, ynew);
+    return cudaGetLastError();
+}
+
+}  // namespace sdd

@@ -1,0 +1,268 @@
+// Backward-Euler subdomain solves of the SDD mesh generator (Sec. 3.5), sm_103a.
+//
+// Every subdomain is an independent Dirichlet problem (interface estimates and physical
+// boundary on its rim).  For interior node P with neighbours E, W, N, S the step solves
+//   d_P x_P + sum_nb c_nb (x_P - x_nb) = d_P x^n_P,
+//   c_E = (dt/tau) (omega_P + omega_E)/2 / h_xi^2  (likewise W, N, S with h_eta),
+//   d_P = 1 (tau x_t = div(omega grad x))  or  omega_P (the paper's Eq. 4 form),
+// a symmetric positive-definite system, for both mesh components at once.
+//
+// One CTA per subdomain.  Outer loop in FP64: residual b - A x of the current iterate (rims
+// included), stop when ||r||_2 <= rtol ||b||_2 for both components.  Inner solve A e = r by
+// Jacobi-preconditioned CG in the inner precision (FP32 for the FP32 modes, FP64 otherwise),
+// then x += e (iterative refinement).  Inner vectors live in full-grid arrays whose rim
+// entries stay zero, so A p needs no rim special cases.  All reductions are fixed-order
+// block trees: the solve is deterministic.
+#include <math.h>
+
+#include "sdd_internal.cuh"
+
+namespace sdd {
+
+namespace {
+
+constexpr int kSolveThreads = 512;
+constexpr int kMaxOuter = 12;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename TI> struct Pair {
+    TI x, y;
+};
+
+// Sum of NV doubles over the block; every thread receives the totals.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[k] += __shfl_xor_sync(kFull, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = v[k];
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = lane < nw ? sh[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(kFull, t, off);
+            if (lane == 0) sh[k * 32 + 32 * NV] = t;  // slot after the per-warp table
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = sh[k * 32 + 32 * NV];
+    __syncthreads();
+}
+
+__global__ void faces_kernel(const SolveParams P, int inner_fp64)
+{
+    const int nx = P.nx, ny = P.ny;
+    const double hx2 = (double)(nx - 1) * (double)(nx - 1);
+    const double hy2 = (double)(ny - 1) * (double)(ny - 1);
+    const long n = (long)nx * ny;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < n; id += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(id % nx), j = (int)(id / nx);
+        const double w = P.om64[id];
+        double e = 0.0, no = 0.0;
+        if (i < nx - 1) e = __dmul_rn(P.r, __dmul_rn(__dmul_rn(0.5, __dadd_rn(w, P.om64[id + 1])), hx2));
+        if (j < ny - 1) no = __dmul_rn(P.r, __dmul_rn(__dmul_rn(0.5, __dadd_rn(w, P.om64[id + nx])), hy2));
+        P.ce64[id] = e;
+        P.cn64[id] = no;
+        if (inner_fp64) {
+            static_cast<double*>(P.ce)[id] = e;
+            static_cast<double*>(P.cn)[id] = no;
+        } else {
+            static_cast<float*>(P.ce)[id] = (float)e;
+            static_cast<float*>(P.cn)[id] = (float)no;
+        }
+    }
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_constant__ SolveParams P)
+{
+    __shared__ double sh[32 * 8 + 8];
+    const int nx = P.nx, ny = P.ny;
+    const int sx = (nx - 1) / P.px, sy = (ny - 1) / P.py;
+    const int I = blockIdx.x % P.px, J = blockIdx.x / P.px;
+    const int i0 = I * sx, j0 = J * sy;
+    const int ni = sx - 1, nj = sy - 1;
+    const int nint = ni * nj;
+    const long N = (long)nx * ny;
+    Pair<TI>* e = static_cast<Pair<TI>*>(P.vec);
+    Pair<TI>* r = e + N;
+    Pair<TI>* p = e + 2 * N;
+    Pair<TI>* q = e + 3 * N;
+    const TI* ce = static_cast<const TI*>(P.ce);
+    const TI* cn = static_cast<const TI*>(P.cn);
+
+    auto node = [&](int t) -> long { return (long)(j0 + 1 + t / ni) * nx + (i0 + 1 + t % ni); };
+    auto dP = [&](long id) -> double { return P.form == 0 ? 1.0 : P.om64[id]; };
+
+    // initial guess: the previous mesh
+    for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+        const long id = node(t);
+        P.xnew[id] = P.xcur[id];
+        P.ynew[id] = P.ycur[id];
+    }
+    // ||b||: b = d x^n + rim terms
+    double bn[2] = {0.0, 0.0};
+    for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+        const long id = node(t);
+        const int i = (int)(id % nx), j = (int)(id / nx);
+        const double d = dP(id);
+        double bx = d * P.xcur[id], by = d * P.ycur[id];
+        if (i - 1 == i0) { bx += P.ce64[id - 1] * P.xnew[id - 1]; by += P.ce64[id - 1] * P.ynew[id - 1]; }
+        if (i + 1 == i0 + sx) { bx += P.ce64[id] * P.xnew[id + 1]; by += P.ce64[id] * P.ynew[id + 1]; }
+        if (j - 1 == j0) { bx += P.cn64[id - nx] * P.xnew[id - nx]; by += P.cn64[id - nx] * P.ynew[id - nx]; }
+        if (j + 1 == j0 + sy) { bx += P.cn64[id] * P.xnew[id + nx]; by += P.cn64[id] * P.ynew[id + nx]; }
+        bn[0] += bx * bx;
+        bn[1] += by * by;
+    }
+    __syncthreads();
+    block_sum<2>(bn, sh);
+
+    const bool fp64_inner = sizeof(TI) == 8;
+    int iters = 0, outer = 0, ok = 0;
+    double rel = 0.0;
+    for (outer = 0; outer < kMaxOuter; ++outer) {
+        // FP64 residual of the current iterate
+        double rn[2] = {0.0, 0.0};
+        for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+            const long id = node(t);
+            const double cE = P.ce64[id], cW = P.ce64[id - 1], cN = P.cn64[id], cS = P.cn64[id - nx];
+            const double d = dP(id);
+            const double diag = d + cE + cW + cN + cS;
+            const double ax = diag * P.xnew[id] - cE * P.xnew[id + 1] - cW * P.xnew[id - 1] -
+                              cN * P.xnew[id + nx] - cS * P.xnew[id - nx];
+            const double ay = diag * P.ynew[id] - cE * P.ynew[id + 1] - cW * P.ynew[id - 1] -
+                              cN * P.ynew[id + nx] - cS * P.ynew[id - nx];
+            const double rx = d * P.xcur[id] - ax, ry = d * P.ycur[id] - ay;
+            r[id] = Pair<TI>{(TI)rx, (TI)ry};
+            rn[0] += rx * rx;
+            rn[1] += ry * ry;
+        }
+        __syncthreads();
+        block_sum<2>(rn, sh);
+        const double relx = bn[0] > 0 ? sqrt(rn[0] / bn[0]) : sqrt(rn[0]);
+        const double rely = bn[1] > 0 ? sqrt(rn[1] / bn[1]) : sqrt(rn[1]);
+        rel = relx > rely ? relx : rely;
+        if (rel <= P.rtol) {
+            ok = 1;
+            break;
+        }
+        if (iters >= P.max_iter) break;
+        // inner relative tolerance: straight to the target in FP64, 1e-4 per sweep in FP32
+        double tol_rel[2];
+        for (int c = 0; c < 2; ++c) {
+            const double cur = c == 0 ? relx : rely;
+            double t = fp64_inner ? 0.5 * P.rtol / (cur > 0 ? cur : 1.0) : 1e-4;
+            if (fp64_inner && t < 1e-14) t = 1e-14;
+            if (t > 0.5) t = 0.5;
+            tol_rel[c] = t;
+        }
+        // CG start: e = 0, p = z = r / diag
+        double rz[2] = {0.0, 0.0}, rr0[2] = {0.0, 0.0};
+        for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+            const long id = node(t);
+            const TI diag = (TI)dP(id) + ce[id] + ce[id - 1] + cn[id] + cn[id - nx];
+            const Pair<TI> rv = r[id];
+            const Pair<TI> z = Pair<TI>{rv.x / diag, rv.y / diag};
+            e[id] = Pair<TI>{(TI)0, (TI)0};
+            p[id] = z;
+            rz[0] += (double)rv.x * (double)z.x;
+            rz[1] += (double)rv.y * (double)z.y;
+            rr0[0] += (double)rv.x * (double)rv.x;
+            rr0[1] += (double)rv.y * (double)rv.y;
+        }
+        __syncthreads();
+        {
+            double v[4] = {rz[0], rz[1], rr0[0], rr0[1]};
+            block_sum<4>(v, sh);
+            rz[0] = v[0]; rz[1] = v[1]; rr0[0] = v[2]; rr0[1] = v[3];
+        }
+        bool done_c[2] = {rr0[0] == 0.0, rr0[1] == 0.0};
+        while (iters < P.max_iter && !(done_c[0] && done_c[1])) {
+            ++iters;
+            double pq[2] = {0.0, 0.0};
+            for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+                const long id = node(t);
+                const TI cE = ce[id], cW = ce[id - 1], cN = cn[id], cS = cn[id - nx];
+                const TI diag = (TI)dP(id) + cE + cW + cN + cS;
+                const Pair<TI> pc = p[id], pe = p[id + 1], pw = p[id - 1], pn = p[id + nx], ps = p[id - nx];
+                const Pair<TI> qv = Pair<TI>{diag * pc.x - cE * pe.x - cW * pw.x - cN * pn.x - cS * ps.x,
+                                             diag * pc.y - cE * pe.y - cW * pw.y - cN * pn.y - cS * ps.y};
+                q[id] = qv;
+                pq[0] += (double)pc.x * (double)qv.x;
+                pq[1] += (double)pc.y * (double)qv.y;
+            }
+            __syncthreads();
+            block_sum<2>(pq, sh);
+            const TI ax = (!done_c[0] && pq[0] > 0) ? (TI)(rz[0] / pq[0]) : (TI)0;
+            const TI ay = (!done_c[1] && pq[1] > 0) ? (TI)(rz[1] / pq[1]) : (TI)0;
+            double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z (x, y), r.r (x, y)
+            for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+                const long id = node(t);
+                const TI diag = (TI)dP(id) + ce[id] + ce[id - 1] + cn[id] + cn[id - nx];
+                const Pair<TI> pc = p[id], qv = q[id];
+                Pair<TI> ev = e[id], rv = r[id];
+                ev.x += ax * pc.x; ev.y += ay * pc.y;
+                rv.x -= ax * qv.x; rv.y -= ay * qv.y;
+                e[id] = ev;
+                r[id] = rv;
+                v[0] += (double)rv.x * (double)(rv.x / diag);
+                v[1] += (double)rv.y * (double)(rv.y / diag);
+                v[2] += (double)rv.x * (double)rv.x;
+                v[3] += (double)rv.y * (double)rv.y;
+            }
+            __syncthreads();
+            block_sum<4>(v, sh);
+            for (int c = 0; c < 2; ++c)
+                if (!done_c[c] && v[2 + c] <= tol_rel[c] * tol_rel[c] * rr0[c]) done_c[c] = true;
+            const TI bx = (!done_c[0] && rz[0] > 0) ? (TI)(v[0] / rz[0]) : (TI)0;
+            const TI by = (!done_c[1] && rz[1] > 0) ? (TI)(v[1] / rz[1]) : (TI)0;
+            rz[0] = v[0];
+            rz[1] = v[1];
+            for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+                const long id = node(t);
+                const TI diag = (TI)dP(id) + ce[id] + ce[id - 1] + cn[id] + cn[id - nx];
+                const Pair<TI> rv = r[id], pc = p[id];
+                p[id] = Pair<TI>{rv.x / diag + bx * pc.x, rv.y / diag + by * pc.y};
+            }
+            __syncthreads();
+        }
+        // x += e
+        for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+            const long id = node(t);
+            const Pair<TI> ev = e[id];
+            P.xnew[id] += (double)ev.x;
+            P.ynew[id] += (double)ev.y;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        P.stat_iters[blockIdx.x] = iters;
+        P.stat_outer[blockIdx.x] = outer;
+        P.stat_ok[blockIdx.x] = ok;
+        P.stat_res[blockIdx.x] = rel;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s)
+{
+    const long n = (long)P.nx * P.ny;
+    faces_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(P, fp64_inner ? 1 : 0);
+    const int nsub = P.px * P.py;
+    if (fp64_inner)
+        solve_kernel<double><<<nsub, kSolveThreads, 0, s>>>(P);
+    else
+        solve_kernel<float><<<nsub, kSolveThreads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace sdd

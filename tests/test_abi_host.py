@@ -1,0 +1,93 @@
+"""The C-ABI library loads, exports every symbol include/sdd.h declares, and its host-only
+logic (interface layout, adaptive schedule, argument validation) matches the oracle.
+No compute call needs a GPU here."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sdd():
+    from paper_1504_00084_gb300 import build as B
+    B.build()
+    import paper_1504_00084_gb300 as S
+    return S
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "sdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdd_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(sdd):
+    names = declared_functions()
+    assert len(names) >= 19
+    lib = ctypes.CDLL(sdd.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(sdd.EXPORTS)
+
+
+@pytest.mark.parametrize("nx,ny,px,py,per", [(33, 33, 2, 2, 0), (257, 257, 4, 4, 0), (257, 257, 4, 4, 1),
+                                             (65, 129, 8, 2, 0), (9, 9, 1, 1, 0), (9, 9, 1, 1, 1),
+                                             (3, 3, 2, 2, 0), (17, 33, 4, 2, 1)])
+def test_interface_layout_matches_oracle(sdd, nx, ny, px, py, per):
+    from oracle.layout import interface_nodes
+    got = sdd.sdd_interface_layout(nx, ny, px, py, per)
+    want = interface_nodes(nx, ny, px, py, per)
+    assert np.array_equal(got, want)
+
+
+def test_adaptive_schedule_matches_oracle(sdd):
+    from oracle.mc import next_total
+    rng = np.random.default_rng(0)
+    cases = [(4096, 1e-4, 1e-4, 10 ** 7), (4096, 2e-4, 1e-4, 10 ** 7), (4096, 1.01e-4, 1e-4, 10 ** 7),
+             (4096, 1.0, 1e-4, 50000), (50000, 1.0, 1e-4, 50000), (1000, 0.0, 1e-4, 10 ** 6)]
+    for _ in range(500):
+        n = int(rng.integers(2, 10 ** 7))
+        t = float(10 ** rng.uniform(-6, -2))
+        cases.append((n, float(t * 10 ** rng.uniform(-1, 2)), t, int(n + rng.integers(0, 10 ** 8))))
+    for n, se, t, mx in cases:
+        assert sdd.sdd_adaptive_next_total(n, se, t, mx) == next_total(n, se, t, mx), (n, se, t, mx)
+
+
+def base_params(sdd, **kw):
+    import workloads as W
+    return sdd.params_from(W.c0_small_fp64(), **kw)
+
+
+@pytest.mark.parametrize("field,value", [("nx", 2), ("px", 3), ("py", 0), ("substeps", 0),
+                                         ("paths_per_node", 1), ("reserved0", 1), ("tau", 0.0),
+                                         ("precision", 7), ("form", 2), ("solve_rtol", 0.0),
+                                         ("periodic", 2), ("se_target", -1.0)])
+def test_invalid_params_rejected_before_any_device_work(sdd, field, value):
+    import workloads as W
+    p = base_params(sdd)
+    setattr(p, field, value)
+    x, y = W.identity_mesh(W.c0_small_fp64())
+    h = ctypes.c_void_p()
+    st = sdd.lib.sdd_create_problem(ctypes.byref(p), x.ctypes.data, y.ctypes.data, None, ctypes.byref(h))
+    assert st == sdd.SDD_ERR_INVALID_ARG
+    assert h.value is None
+    assert len(sdd.lib.sdd_last_error()) > 0
+
+
+def test_adaptive_cap_validated(sdd):
+    import workloads as W
+    p = base_params(sdd, se_target=1e-3, max_paths_per_node=10)
+    x, y = W.identity_mesh(W.c0_small_fp64())
+    h = ctypes.c_void_p()
+    assert sdd.lib.sdd_create_problem(ctypes.byref(p), x.ctypes.data, y.ctypes.data, None,
+                                      ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
+
+
+def test_status_strings(sdd):
+    for s in range(7):
+        assert len(sdd.lib.sdd_status_string(s)) > 0

@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs
+and Philox streams.  Tolerances: per-path values 1e-12 (FP64) / 1e-5 (FP32); exit steps and
+sides bit-exact wherever the oracle's decision margins clear the precision's noise floor;
+node estimates 1e-10 (FP64); meshes within the interface tolerance plus the solver's
+residual bound (see test docstrings)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_helpers import compare_paths, gpu_problem, oracle_inputs, real_of
+from oracle import mc, step as ostep
+from oracle.solve import box_system
+from oracle.layout import subdomains
+
+pytestmark = pytest.mark.gpu
+
+FP64_MARGIN, FP64_VAL = 1e-9, 1e-12
+FP32_MARGIN, FP32_VAL = 1e-4, 1e-5
+
+
+@pytest.fixture(scope="module")
+def S():
+    import paper_1504_00084_gb300 as S
+    return S
+
+
+def test_philox_bit_exact(S):
+    from test_oracle_philox import philox
+    rng = np.random.default_rng(7)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, size=(4096, 2), dtype=np.uint64).astype(np.uint32)
+    assert np.array_equal(S.sdd_debug_philox(ctr, key), philox(ctr, key))
+
+
+@pytest.mark.parametrize("prob", [
+    W.c0_small_fp64(),
+    W.c1_front(W.PREC_FP64).replace(nx=65, ny=65),
+    W.c1_front(W.PREC_FP64, periodic=1).replace(nx=65, ny=65),
+    W.c3_mix(4)[1].replace(precision=W.PREC_FP64),
+], ids=["gauss", "front", "front_periodic", "bumps"])
+def test_monitor_and_gradient(S, prob):
+    x, y = W.sine_mode_mesh(prob, amp=0.01, periodic_mode=bool(prob.periodic))
+    h = gpu_problem(prob, x, y)
+    w, wx, we = h.monitor()
+    from oracle.monitor import fd_gradient
+    om = ostep.monitor_on_mesh(prob, x, y, prob.t0)
+    gx, gy = fd_gradient(om, prob.periodic)
+    scale = np.abs(om).max()
+    assert np.abs(w - om).max() <= 1e-14 * scale
+    gscale = max(np.abs(gx).max(), np.abs(gy).max(), 1.0)
+    assert np.abs(wx - gx).max() <= 1e-13 * gscale * prob.nx
+    assert np.abs(we - gy).max() <= 1e-13 * gscale * prob.ny
+    h.close()
+
+
+def _paths_case(S, prob, nodes_to_check, n, mesh=None):
+    x, y = mesh if mesh is not None else W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    om, inp, nodes = oracle_inputs(prob, x, y, prob.t0, 0)
+    fp64 = prob.precision == W.PREC_FP64
+    res = []
+    for m in nodes_to_check:
+        gv, gs, gd = h.debug_paths(m, 0, n)
+        ov, os_, od, mg = mc.paths(inp, m, int(nodes[m, 0]), int(nodes[m, 1]), 0, n)
+        res.append(compare_paths(gv, gs, gd, ov, os_, od, mg,
+                                 FP64_MARGIN if fp64 else FP32_MARGIN, FP64_VAL if fp64 else FP32_VAL))
+    h.close()
+    return res
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_ACC64])
+def test_paths_c0(S, precision):
+    prob = W.c0_small_fp64().replace(precision=precision)
+    res = _paths_case(S, prob, [0, 15, 30, 45, 60], 1000)
+    for robust, mism in res:
+        assert robust > (0.999 if precision == W.PREC_FP64 else 0.95)
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_ACC64])
+@pytest.mark.parametrize("variant", ["periodic", "winslow", "bilinear_nobridge", "sine_mesh"])
+def test_paths_variants(S, precision, variant):
+    prob = W.c0_small_fp64().replace(precision=precision, nx=17, ny=17, substeps=40)
+    mesh = None
+    if variant == "periodic":
+        prob = prob.replace(periodic=1, Lx=2.0, Ly=1.5)
+        mesh = W.sine_mode_mesh(prob, amp=0.03, periodic_mode=True)
+    elif variant == "winslow":
+        prob = prob.replace(form=W.FORM_WINSLOW, tau=1.0, dt=1e-2)
+    elif variant == "bilinear_nobridge":
+        prob = prob.replace(bicubic=0, bb_test=0)
+        mesh = W.sine_mode_mesh(prob, amp=0.04)
+    else:
+        mesh = W.sine_mode_mesh(prob, amp=0.04)
+    res = _paths_case(S, prob, [0, 7, 20], 700, mesh)
+    for robust, mism in res:
+        assert robust > (0.999 if precision == W.PREC_FP64 else 0.9)
+
+
+def test_node_estimates_c0_fp64(S):
+    prob = W.c0_small_fp64()
+    x, y = W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    est, se, n, _ = h.interface_mc()
+    om, inp, nodes = oracle_inputs(prob, x, y, prob.t0, 0)
+    oest, ose, on, osteps = mc.interface_mc(prob, x, y, om, nodes, 0, np.float64)
+    assert np.array_equal(n, on)
+    assert np.abs(est - oest).max() <= 1e-10
+    assert np.abs(se - ose).max() <= 1e-10
+    st = h.stats()
+    assert st["path_steps"] == int(osteps.sum())
+    assert st["paths"] == prob.paths_per_node * len(nodes)
+    h.close()
+
+
+def test_node_estimates_deterministic(S):
+    prob = W.c0_small_fp64().replace(precision=W.PREC_FP32_ACC64, paths_per_node=20000)
+    h = gpu_problem(prob)
+    a = h.interface_mc()[0]
+    b = h.interface_mc()[0]
+    assert np.array_equal(a, b)
+    h.close()
+
+
+def test_adaptive_matches_oracle(S):
+    prob = W.c0_small_fp64().replace(paths_per_node=2048, se_target=4e-3, max_paths_per_node=200000)
+    x, y = W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    est, se, n, status = h.interface_mc()
+    om, inp, nodes = oracle_inputs(prob, x, y, prob.t0, 0)
+    oest, ose, on, _ = mc.interface_mc(prob, x, y, om, nodes, 0, np.float64)
+    assert np.array_equal(n, on)
+    assert np.abs(est - oest).max() <= 1e-10
+    assert se.max() <= prob.se_target
+    assert h.stats()["mc_rounds"] >= 2
+    h.close()
+
+
+def _mesh_tolerance(prob, om, rims_x, rims_y, xn, yn, est_tol):
+    """Interface tolerance (max principle carries it into the interiors) plus the solver's
+    bound ||x - x*||_2 <= ||A^-1|| rtol ||b||_2 with ||A^-1|| <= 1 / lambda_min, lambda_min >= 1
+    (form 0) or >= min omega (form 1)."""
+    lam = 1.0 if prob.form == W.FORM_DIV else float(om.min())
+    worst = 0.0
+    for (i0, i1, j0, j1) in subdomains(prob.nx, prob.ny, prob.px, prob.py):
+        if i1 - i0 < 2 or j1 - j0 < 2:
+            continue
+        A, rhs, _ = box_system(om, None, i0, i1, j0, j1, prob.dt, prob.tau, prob.form)
+        bx = np.linalg.norm(rhs(rims_x, xn))
+        by = np.linalg.norm(rhs(rims_y, yn))
+        worst = max(worst, prob.solve_rtol * max(bx, by) / lam)
+    return est_tol + worst + 1e-12
+
+
+@pytest.mark.parametrize("variant", ["c0", "periodic", "winslow"])
+def test_full_step_fp64(S, variant):
+    prob = W.c0_small_fp64()
+    if variant == "periodic":
+        prob = prob.replace(periodic=1, monitor_params=[6.0, 40.0, 0.3, 0.6])
+    elif variant == "winslow":
+        prob = prob.replace(form=W.FORM_WINSLOW, tau=1.0)
+    x, y = W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    gx, gy, status = h.step()
+    r = ostep.step(prob, x, y, prob.t0, 0)
+    bx, by = ostep.scatter(prob, r["nodes"], r["est"])
+    tol = _mesh_tolerance(prob, r["omega"], bx, by, x, y, 1e-10)
+    assert np.abs(gx - r["x"]).max() <= tol
+    assert np.abs(gy - r["y"]).max() <= tol
+    st = h.stats()
+    assert st["step_index"] == 1 and st["solve_rel_residual"] <= prob.solve_rtol
+    h.close()
+
+
+def test_subdomain_solve_fp32_refinement_matches_oracle(S):
+    """FP32 PCG + FP64 refinement reaches the FP64 target: same interface data on both sides."""
+    prob = W.c0_small_fp64().replace(precision=W.PREC_FP32_ACC64, solve_rtol=1e-11)
+    x, y = W.sine_mode_mesh(prob, amp=0.02)
+    h = gpu_problem(prob, x, y)
+    nodes = h.nodes()
+    iface = np.stack([x[nodes[:, 1], nodes[:, 0]], y[nodes[:, 1], nodes[:, 0]]], 1) + 0.003
+    gx, gy, status = h.subdomain_solve(iface)
+    om = ostep.monitor_on_mesh(prob, x, y, prob.t0)
+    bx, by = ostep.scatter(prob, nodes, iface)
+    ox, oy = ostep.subdomain_solves(prob, om, bx, by, x, y)
+    tol = _mesh_tolerance(prob, om, bx, by, x, y, 0.0)
+    assert np.abs(gx - ox).max() <= tol and np.abs(gy - oy).max() <= tol
+    assert h.stats()["solve_outer_max"] >= 2
+    h.close()
+
+
+def test_single_domain_split_has_no_interface(S):
+    """px = py = 1 (Dirichlet): no interface nodes; the step is the single-domain solve."""
+    prob = W.c0_small_fp64().replace(px=1, py=1, nx=17, ny=17)
+    x, y = W.sine_mode_mesh(prob, amp=0.03)
+    h = gpu_problem(prob, x, y)
+    assert h.M == 0
+    gx, gy, _ = h.step()
+    from oracle.solve import single_domain_step
+    om = ostep.monitor_on_mesh(prob, x, y, prob.t0)
+    ox, oy = single_domain_step(om, x, y, prob.dt, prob.tau, prob.form)
+    assert np.abs(gx - ox).max() <= 1e-9 and np.abs(gy - oy).max() <= 1e-9
+    h.close()
+
+
+def test_tiny_grid_without_subdomain_interiors(S):
+    prob = W.c0_small_fp64().replace(nx=3, ny=3, px=2, py=2, paths_per_node=3000)
+    h = gpu_problem(prob)
+    assert h.M == 1
+    gx, gy, _ = h.step()
+    r = ostep.step(prob, *W.identity_mesh(prob), prob.t0, 0)
+    assert np.abs(gx - r["x"]).max() <= 1e-10 and np.abs(gy - r["y"]).max() <= 1e-10
+    h.close()
+
+
+def test_kahan_accumulation_close_to_fp64(S):
+    base = W.c0_small_fp64().replace(paths_per_node=100000)
+    a = gpu_problem(base.replace(precision=W.PREC_FP32_ACC64))
+    b = gpu_problem(base.replace(precision=W.PREC_FP32_KAHAN))
+    ea, sa, _, _ = a.interface_mc()
+    eb, sb, _, _ = b.interface_mc()
+    # same FP32 paths; only the summation differs: Kahan error ~ 2 eps32 sum|d| / N
+    assert np.abs(ea - eb).max() <= 1e-6
+    assert np.abs(sa - sb).max() <= 1e-6
+    a.close(); b.close()
+
+
+def test_sine_mode_closed_form_on_gpu(S):
+    """omega = 1: the estimates follow xi + A exp(-2 pi^2 dt / tau) sin sin within 4 SE."""
+    prob = W.c2_sine(W.PREC_FP32_ACC64, paths=200000).replace(nx=65, ny=65, px=4, py=4,
+                                                              tau=1.0, dt=0.01)
+    x, y = W.sine_mode_mesh(prob, amp=0.05)
+    h = gpu_problem(prob, x, y)
+    est, se, _, _ = h.interface_mc()
+    nodes = h.nodes()
+    xi = nodes[:, 0] / (prob.nx - 1)
+    eta = nodes[:, 1] / (prob.ny - 1)
+    mode = 0.05 * np.sin(np.pi * xi) * np.sin(np.pi * eta) * math.exp(-2 * math.pi ** 2 * prob.dt / prob.tau)
+    dev = np.abs(est - np.stack([xi + mode, eta + mode], 1))
+    assert np.mean(dev <= 4 * se + 1e-6) > 0.995
+    h.close()
