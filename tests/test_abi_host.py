@@ -14,8 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 @pytest.fixture(scope="module")
 def sdd():
-    from paper_1504_00084_gb300 import build as B
-    B.build()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1504_00084_gb300 as S
     return S
 
