@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--mc-only", type=int, default=0,
+                    help="profiling case: run `steps` interface-MC calls at this fixed N per node and "
+                         "print the library's counters (not a benchmark line)")
     return ap.parse_args()
 
 
@@ -317,8 +320,30 @@ def run_ours(args):
     return 0
 
 
+def run_mc_only(args):
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    prob = workload(args).replace(se_target=0.0, paths_per_node=args.mc_only, max_paths_per_node=args.mc_only)
+    x0, y0 = W.identity_mesh(prob)
+    with S.SddProblem(S.params_from(prob), x0, y0, stream=torch.cuda.current_stream()) as h:
+        h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
+        for _ in range(args.warmup + args.steps):
+            h.interface_mc()
+            st = h.stats()
+            print(json.dumps({"mc_only": args.mc_only, "path_steps": st["path_steps"], "paths": st["paths"],
+                              "mc_kernel_ms": st["mc_kernel_ms"],
+                              "path_steps_per_s": st["path_steps"] / (st["mc_kernel_ms"] / 1e3)}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.mc_only > 0:
+        return run_mc_only(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

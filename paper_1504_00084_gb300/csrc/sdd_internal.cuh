@@ -23,24 +23,16 @@ struct U4 {
     uint32_t x, y, z, w;
 };
 
-__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b)
-{
-#ifdef __CUDA_ARCH__
-    return __umulhi(a, b);
-#else
-    return (uint32_t)(((uint64_t)a * (uint64_t)b) >> 32);
-#endif
-}
-
 __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
 {
     constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
     constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = mulhi32(kM0, c.x), lo0 = kM0 * c.x;
-        const uint32_t hi1 = mulhi32(kM1, c.z), lo1 = kM1 * c.z;
-        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        const uint64_t p0 = (uint64_t)kM0 * c.x;   // one 32x32 -> 64 multiply each
+        const uint64_t p1 = (uint64_t)kM1 * c.z;
+        c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
+               (uint32_t)p0};
         k0 += kW0;
         k1 += kW1;
     }
@@ -48,14 +40,16 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t
 }
 
 // Uniform in (0, 1) from one word without rounding: FP32 keeps the top 23 bits,
-// u = (floor(w / 2^9) + 1/2) 2^-23; FP64 u = (w + 1/2) 2^-32.
+// u = (floor(w / 2^9) + 1/2) 2^-23; FP64 u = (w + 1/2) 2^-32.  Built from the exponent bits
+// of [1, 2): 1 + k 2^-23 (resp. 1 + w 2^-32) minus (1 - 2^-24) (resp. 1 - 2^-33); the
+// difference is representable, so the subtraction is exact.
 __device__ __forceinline__ float uniform_open(uint32_t w, float)
 {
-    return (__uint2float_rn(w >> 9) + 0.5f) * 0x1p-23f;
+    return __int_as_float(0x3F800000 | (w >> 9)) - 0x1.fffffep-1f;
 }
 __device__ __forceinline__ double uniform_open(uint32_t w, double)
 {
-    return (__uint2double_rn(w) + 0.5) * 0x1p-32;
+    return __hiloint2double((int)(0x3FF00000u | (w >> 12)), (int)(w << 20)) - 0x1.ffffffffp-1;
 }
 
 // ---------------------------------------------------------------------------------------

@@ -212,6 +212,16 @@ __device__ void mesh_at(const McParams<T>& P, T xi, T eta, T& ix, T& iy)
 template <typename T>
 __device__ __forceinline__ T clamp01(T v) { return v < 0 ? (T)0 : (v > 1 ? (T)1 : v); }
 
+// Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; zero
+// where the exponential is too small to change 1 - p (and then cannot be the largest p of an
+// exiting path).
+template <typename T>
+__device__ __forceinline__ T bridge_p(T d0, T d1, T q)
+{
+    const T a = d0 * d1;
+    return (a > Consts<T>::bridge_skip * q) ? (T)0 : dexp(-a / q);
+}
+
 // One substep k of path p at node m.  Returns true when the path ends at this substep
 // (exit, or k == K - 1); then (vx, vy) is its value and side its exit side (4: none).
 template <typename T>
@@ -242,29 +252,28 @@ __device__ __forceinline__ bool path_substep(const McParams<T>& P, uint32_t m, u
     const T en = eta + by + sd * z2;
 
     if (!P.periodic) {
-        const T viol[4] = {-xn, xn - 1, -en, en - 1};
+        // deepest violation of the unit square; ties keep the lower side index
+        T vmax = -xn;
         int s = 0;
-#pragma unroll
-        for (int t = 1; t < 4; ++t)
-            if (viol[t] > viol[s]) s = t;
-        bool exited = viol[s] > 0;
+        if (xn - 1 > vmax) { vmax = xn - 1; s = 1; }
+        if (-en > vmax) { vmax = -en; s = 2; }
+        if (en - 1 > vmax) { vmax = en - 1; s = 3; }
+        bool exited = vmax > 0;
         if (!exited && P.bb) {
-            const T d0[4] = {xi, 1 - xi, eta, 1 - eta};
-            const T d1[4] = {xn, 1 - xn, en, 1 - en};
-            T pr[4];
+            const T p0 = bridge_p(xi, xn, q), p1 = bridge_p(1 - xi, 1 - xn, q);
+            const T p2 = bridge_p(eta, en, q), p3 = bridge_p(1 - eta, 1 - en, q);
             T surv = 1;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const T a = d0[t] * d1[t];
-                pr[t] = (a > Consts<T>::bridge_skip * q) ? (T)0 : dexp(-a / q);
-                surv *= (1 - pr[t]);
-            }
+            surv *= (1 - p0);
+            surv *= (1 - p1);
+            surv *= (1 - p2);
+            surv *= (1 - p3);
             if (ub > surv) {
                 exited = true;
+                T pm = p0;
                 s = 0;
-#pragma unroll
-                for (int t = 1; t < 4; ++t)
-                    if (pr[t] > pr[s]) s = t;
+                if (p1 > pm) { pm = p1; s = 1; }
+                if (p2 > pm) { pm = p2; s = 2; }
+                if (p3 > pm) { pm = p3; s = 3; }
             }
         }
         if (exited) {
