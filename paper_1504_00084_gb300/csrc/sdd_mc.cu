@@ -29,6 +29,9 @@ namespace {
 
 constexpr int kMcThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
+#ifndef SDD_MC_MIN_BLOCKS
+#define SDD_MC_MIN_BLOCKS 4   // resident blocks per SM asked of the register allocator (64 registers)
+#endif
 
 __device__ __forceinline__ float dlog(float x) { return logf(x); }
 __device__ __forceinline__ double dlog(double x) { return log(x); }
@@ -301,11 +304,13 @@ __device__ __forceinline__ bool path_substep(const McParams<T>& P, uint32_t m, u
     return false;
 }
 
-// Per-lane estimator sums.
+// Per-lane estimator sums of the shifted path values (shift = the node's previous position).
 template <typename T, int ACC> struct LaneAcc;
 template <typename T> struct LaneAcc<T, kAcc64> {
+    double sx, sy;
     double s1x = 0, s2x = 0, s1y = 0, s2y = 0;
-    __device__ __forceinline__ void add(T vx, T vy, double sx, double sy)
+    __device__ __forceinline__ LaneAcc(double sx_, double sy_) : sx(sx_), sy(sy_) {}
+    __device__ __forceinline__ void add(T vx, T vy)
     {
         const double dx = (double)vx - sx, dy = (double)vy - sy;
         s1x += dx;
@@ -313,15 +318,19 @@ template <typename T> struct LaneAcc<T, kAcc64> {
         s1y += dy;
         s2y += dy * dy;
     }
-    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, double, double,
-                                           unsigned long long) const
+    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long) const
     {
         a = s1x; b = s2x; c = s1y; d = s2y;
     }
 };
-// Kahan-compensated FP32 sums of v - fl(shift); converted to the exact shift at the end.
+// Kahan-compensated FP32 sums of v - fl(shift): no FP64 work per path; converted to sums of
+// v - shift (exact shift) once per task.
 template <typename T> struct LaneAcc<T, kAccKahan32> {
+    float sxf, syf;
+    double ex, ey;  // shift - fl(shift)
     float s1x = 0, c1x = 0, s2x = 0, c2x = 0, s1y = 0, c1y = 0, s2y = 0, c2y = 0;
+    __device__ __forceinline__ LaneAcc(double sx, double sy)
+        : sxf((float)sx), syf((float)sy), ex(sx - (double)(float)sx), ey(sy - (double)(float)sy) {}
     __device__ __forceinline__ static void kahan(float& s, float& c, float v)
     {
         const float y = __fsub_rn(v, c);
@@ -329,19 +338,16 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
-    __device__ __forceinline__ void add(T vx, T vy, double sx, double sy)
+    __device__ __forceinline__ void add(T vx, T vy)
     {
-        const float dx = __fsub_rn((float)vx, (float)sx), dy = __fsub_rn((float)vy, (float)sy);
+        const float dx = __fsub_rn((float)vx, sxf), dy = __fsub_rn((float)vy, syf);
         kahan(s1x, c1x, dx);
         kahan(s2x, c2x, __fmul_rn(dx, dx));
         kahan(s1y, c1y, dy);
         kahan(s2y, c2y, __fmul_rn(dy, dy));
     }
-    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, double sx,
-                                           double sy, unsigned long long n) const
+    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long n) const
     {
-        // sums of (v - fl(s)) -> sums of (v - s) with delta = s - fl(s)
-        const double ex = sx - (double)(float)sx, ey = sy - (double)(float)sy;
         const double S1x = (double)s1x - (double)c1x, S2x = (double)s2x - (double)c2x;
         const double S1y = (double)s1y - (double)c1y, S2y = (double)s2y - (double)c2y;
         const double nn = (double)n;
@@ -353,7 +359,7 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
 };
 
 template <typename T, int ACC, bool DEBUG>
-__global__ void __launch_bounds__(kMcThreads) mc_kernel(const __grid_constant__ McParams<T> P)
+__global__ void __launch_bounds__(kMcThreads, SDD_MC_MIN_BLOCKS) mc_kernel(const __grid_constant__ McParams<T> P)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(kMcThreads) mc_kernel(const __grid_constant__ 
         const T eta0 = (T)ij.y / (T)(P.ny - 1);
         const double sx = P.shift[2 * m], sy = P.shift[2 * m + 1];
 
-        LaneAcc<T, ACC> acc;
+        LaneAcc<T, ACC> acc(sx, sy);
         unsigned long long steps = 0, paths = 0;
         int64_t path = pb + lane;
         bool live = path < pe;
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(kMcThreads) mc_kernel(const __grid_constant__ 
                 done = path_substep<T>(P, (uint32_t)m, (uint32_t)path, k, xi, eta, vx, vy, side);
                 ++k;
                 if (done) {
-                    acc.add(vx, vy, sx, sy);
+                    acc.add(vx, vy);
                     steps += (unsigned long long)k;
                     paths += 1;
                     if (DEBUG) {
@@ -416,7 +422,7 @@ __global__ void __launch_bounds__(kMcThreads) mc_kernel(const __grid_constant__ 
             next += __popc(dm);
         }
         double a, b, c, d;
-        acc.finish(a, b, c, d, sx, sy, paths);
+        acc.finish(a, b, c, d, paths);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             a += __shfl_xor_sync(kFull, a, off);
