@@ -193,6 +193,32 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
  * on the legacy default stream; returns after `out` is written. */
 sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 
+/* Allocation-free interface Monte Carlo.  The paper has no counterpart: this entry point
+ * serves callers that cannot call cudaMalloc -- for instance a host framework whose caching
+ * allocator owns the device memory budget and forbids allocations outside it, or a
+ * latency-critical loop that cannot afford a device allocation.  It runs the same kernels as
+ * sdd_interface_mc in fixed-N mode (same Philox streams, same node ids, same estimates) for
+ * the nodal monitor `omega` on the mesh (x, y) at time-step index `step_index`, and allocates
+ * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
+ *   params : as for sdd_create_problem, with se_target == 0 (fixed paths_per_node).
+ *   x, y, omega : nx*ny doubles in DEVICE memory (read); est_xy, se_xy : M x 2 doubles in
+ *            DEVICE memory (written, same layout as sdd_interface_mc).
+ *   stream : cudaStream_t for all work (NULL = legacy default stream); the call returns
+ *            without waiting for the GPU.
+ * Intermediates live in one 16 MiB device array inside the library, held by every GPU that
+ * loads it until the process exits.  Requests needing more are rejected with
+ * SDD_ERR_INVALID_ARG: the requirement is about 72 B per grid node (FP32; 120 B in FP64),
+ * 200 B per interface node and 48 B per task of min(N, 2^19)/2048 paths per node -- e.g. a
+ * 257x257 grid with 1521 interface nodes fits for N <= 2.6e5.  Host pointers are rejected.
+ * The first call on a device (with that device current) resolves the array's device address
+ * with cudaGetSymbolAddress; make that first call before any stream capture.  Every call
+ * shares the array and leaves its contents behind; each call re-initialises what it reads,
+ * and calls that overlap on the GPU race.  Errors are reported by the status only
+ * (sdd_last_error is not updated by this call). */
+sdd_status sdd_interface_mc_noalloc(const sdd_params* params, const double* x, const double* y,
+                                    const double* omega, int32_t step_index, double* est_xy,
+                                    double* se_xy, void* stream);
+
 const char* sdd_status_string(sdd_status s);
 const char* sdd_last_error(void);
 

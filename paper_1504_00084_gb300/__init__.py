@@ -59,7 +59,7 @@ EXPORTS = [
     "sdd_set_monitor", "sdd_set_monitor_analytic", "sdd_interface_mc", "sdd_subdomain_solve",
     "sdd_step", "sdd_get_stats", "sdd_get_interface_nodes", "sdd_interface_layout",
     "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
-    "sdd_status_string", "sdd_last_error",
+    "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
 ]
 
 
@@ -87,6 +87,7 @@ def _load():
         "sdd_get_monitor": ([P, P, P, P], I32),
         "sdd_debug_paths": ([P, I32, I64, I64, P, P, P], I32),
         "sdd_debug_philox": ([P, P, I64, P], I32),
+        "sdd_interface_mc_noalloc": ([ctypes.POINTER(SddParams), P, P, P, I32, P, P, P], I32),
         "sdd_status_string": ([I32], ctypes.c_char_p),
         "sdd_last_error": ([], ctypes.c_char_p),
     }
