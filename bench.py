@@ -3,7 +3,7 @@
 
 Workload (default): the 257x257 grid split 4x4 (1521 interface nodes), moving-front monitor
 u = tanh(50 (r - 0.25 - 0.1 t)), omega = sqrt(1 + 50 |grad u|^2), tau = 1e-2, dt = 1e-3,
-K = 100 substeps, paths stepped in FP32 with FP64 estimator sums, every interface node
+K = 100 substeps, paths stepped in FP32 with Kahan-compensated sums, every interface node
 estimated to SE <= 1e-4 (adaptive: first chunk 1e5 paths), then the 16 backward-Euler
 subdomain solves.  One benchmark step = one alternating time step (sdd_step): monitor on
 the mesh, interface Monte Carlo, subdomain solves, new mesh.  Synthetic inputs only.
@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "kahan"])
+    ap.add_argument("--precision", default="kahan", choices=["fp32", "fp64", "kahan"])
     ap.add_argument("--se-target", type=float, default=1e-4)
     ap.add_argument("--paths", type=int, default=100000)
     ap.add_argument("--max-paths", type=int, default=1 << 25)
@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", default="front", choices=["front", "mix"],
+                    help="front: the 257x257 / 4x4 moving-front problem (the benchmark line); "
+                         "mix: the batch of 64 uneven problems, batched vs one at a time")
+    ap.add_argument("--mix-n", type=int, default=64)
     ap.add_argument("--mc-only", type=int, default=0,
                     help="profiling case: run `steps` interface-MC calls at this fixed N per node and "
                          "print the library's counters (not a benchmark line)")
@@ -76,6 +80,18 @@ def config_of(p, M):
             "max_paths_per_node": p.max_paths_per_node, "substeps": p.substeps, "tau": p.tau, "dt": p.dt,
             "path_precision": {0: "fp64", 1: "fp32 (fp64 sums)", 2: "fp32 (kahan fp32 sums)"}[p.precision],
             "l2": "256 MiB buffer written between timed steps (inputs are ~1 MB)"}
+
+
+def reduce_over_ranks(dist, T, path_steps, estimates, device):
+    """Whole-job numbers of a weak-scaling run: the slowest rank's time, the work of all ranks."""
+    if dist is None:
+        return float(T), float(path_steps), float(estimates)
+    import torch
+    t = torch.tensor([float(T)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(path_steps), float(estimates)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(w[0]), float(w[1])
 
 
 class ClockSampler:
@@ -217,15 +233,43 @@ def run_ours(args):
     prob = workload(args, rank)
     x0, y0 = W.identity_mesh(prob)
     stream = torch.cuda.current_stream()
-    h = S.SddProblem(S.params_from(prob), x0, y0, stream=stream)
-    h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
+
+    def fresh_problem():
+        h = S.SddProblem(S.params_from(prob), x0, y0, stream=stream)
+        h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
+        for _ in range(args.warmup):
+            S.sdd_step(h.h)
+        torch.cuda.synchronize()
+        return h
+
+    # End to end through the C ABI with host buffers: every step uploads its mesh from pinned
+    # host memory and reads the new mesh back.  Run on its own problem over the same trajectory
+    # steps as the device-timed run below (results are deterministic, so the work is identical).
+    e2e = None
+    if not args.no_e2e:
+        h = fresh_problem()
+        hx = torch.from_numpy(np.ascontiguousarray(h.mesh()[0])).pin_memory()
+        hy = torch.from_numpy(np.ascontiguousarray(h.mesh()[1])).pin_memory()
+        ox, oy = torch.empty_like(hx).pin_memory(), torch.empty_like(hy).pin_memory()
+        barrier()
+        torch.cuda.synchronize()
+        te = time.perf_counter()
+        for _ in range(args.steps):
+            S.sdd_set_mesh(h.h, hx, hy)
+            S.sdd_step(h.h, ox, oy)
+            hx, ox = ox, hx
+            hy, oy = oy, hy
+        torch.cuda.synchronize()
+        barrier()
+        Te, _, _ = reduce_over_ranks(dist, time.perf_counter() - te, 0, 0, "cuda")
+        nb = 2 * prob.nx * prob.ny * 8
+        e2e = {"value": h.M * args.steps * world / Te, "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb}
+        h.close()
+
+    h = fresh_problem()
     M = h.M
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-
-    for _ in range(args.warmup):
-        S.sdd_step(h.h)
-    torch.cuda.synchronize()
-
     launches0 = h.stats()["kernel_launches"]
     path_steps, mc_ms, mc_launches, paths = 0, 0.0, 0, 0
     max_se, not_reached = 0.0, 0
@@ -253,39 +297,7 @@ def run_ours(args):
     dev_s = ev0.elapsed_time(ev1) / 1e3
     T = max(dev_s, 1e-9)
     launches = h.stats()["kernel_launches"] - launches0
-    if dist is not None:
-        t = torch.tensor([T, float(path_steps), float(M * args.steps)], device="cuda", dtype=torch.float64)
-        tm = t.clone()
-        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        T_all, ps_all, est_all = float(tm[0]), float(t[1]), float(t[2])
-    else:
-        T_all, ps_all, est_all = T, float(path_steps), float(M * args.steps)
-
-    # end to end through the C ABI with host buffers: H2D of the step's mesh, D2H of the result
-    e2e = None
-    if not args.no_e2e:
-        hx = torch.from_numpy(np.ascontiguousarray(h.mesh()[0])).pin_memory()
-        hy = torch.from_numpy(np.ascontiguousarray(h.mesh()[1])).pin_memory()
-        ox, oy = torch.empty_like(hx).pin_memory(), torch.empty_like(hy).pin_memory()
-        barrier()
-        torch.cuda.synchronize()
-        te = time.perf_counter()
-        for _ in range(args.steps):
-            S.sdd_set_mesh(h.h, hx, hy)
-            S.sdd_step(h.h, ox, oy)
-            hx, ox = ox, hx
-            hy, oy = oy, hy
-        torch.cuda.synchronize()
-        barrier()
-        Te = time.perf_counter() - te
-        if dist is not None:
-            t = torch.tensor([Te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            Te = float(t[0])
-        nb = 2 * prob.nx * prob.ny * 8
-        e2e = {"value": est_all / Te, "unit": UNIT, "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
-
+    T_all, ps_all, est_all = reduce_over_ranks(dist, T, path_steps, M * args.steps, "cuda")
     h.close()
     if rank != 0:
         if dist is not None:
@@ -340,10 +352,86 @@ def run_mc_only(args):
     return 0
 
 
+def run_mix(args):
+    """The batched mix: 64 independent problems (grids 65..513, splits 2x2..8x8, bump monitors,
+    1e4 paths per node) stepped as one batch in a CUDA graph, against the same problems stepped
+    one at a time with sdd_step -- in FP32 and in plain FP64 at the same path count (the same
+    standard error)."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    mix = W.c3_mix(args.mix_n, paths=args.paths if args.paths != 100000 else 10000)
+    prec = W.PREC_FP32_KAHAN
+    stream = torch.cuda.Stream()
+
+    def make(precision):
+        hs = []
+        for p in mix:
+            q = p.replace(precision=precision)
+            x0, y0 = W.identity_mesh(q)
+            h = S.SddProblem(S.params_from(q), x0, y0)
+            h.set_monitor_analytic(q.monitor_kind, q.monitor_params)
+            hs.append(h)
+        return hs
+
+    hs = make(prec)
+    M = sum(h.M for h in hs)
+    b = S.SddBatch(hs, stream=stream, use_graph=True)
+    for _ in range(args.warmup):
+        b.step()
+    stream.synchronize()
+    l0 = b.stats()["kernel_launches"]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ps = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        b.step()
+    e1.record(stream)
+    stream.synchronize()
+    st = b.stats()
+    T = e0.elapsed_time(e1) / 1e3
+    batch = {"s_per_step": T / args.steps, "interface_node_estimates_per_s": M * args.steps / T,
+             "path_steps_last_step": st["path_steps"], "launches_per_step": (st["kernel_launches"] - l0) / args.steps}
+    b.close()
+
+    def one_at_a_time(handles, steps):
+        for h in handles:
+            S.sdd_step(h.h)  # warm
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(steps):
+            for h in handles:
+                S.sdd_step(h.h)
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t) / steps
+
+    t32 = one_at_a_time(hs, 1)
+    for h in hs:
+        h.close()
+    h64 = make(W.PREC_FP64)
+    t64 = one_at_a_time(h64, 1)
+    for h in h64:
+        h.close()
+    out = {"metric": "interface-node estimates/s, batched mix vs one problem at a time",
+           "workload": f"{args.mix_n} problems, grids 65..513, splits 2x2..8x8, bump monitors, "
+                       f"{mix[0].paths_per_node} paths per node, K = 100",
+           "interface_nodes": M, "batched_fp32_graph": batch,
+           "one_at_a_time_fp32_s_per_step": t32, "one_at_a_time_fp64_s_per_step": t64,
+           "speedup_vs_one_at_a_time_fp32": t32 / batch["s_per_step"],
+           "speedup_vs_one_at_a_time_fp64": t64 / batch["s_per_step"]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.mc_only > 0:
         return run_mc_only(args)
+    if args.workload == "mix":
+        return run_mix(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -77,7 +77,7 @@ typedef struct {
     int32_t bicubic;         /* 1: Keys bicubic of the previous mesh at the path end (Sec. 3.4);
                                 0: bilinear                                                          */
     int32_t bb_test;         /* 1: Brownian-bridge crossing test between substeps (Sec. 3.4)       */
-    int32_t substeps;        /* K >= 1: Euler-Maruyama substeps per time step, ds = dt / K (Eq. 7) */
+    int32_t substeps;        /* K in [1, 2^20]: Euler-Maruyama substeps per step, ds = dt / K (Eq. 7) */
     int32_t solve_max_iter;  /* PCG iteration cap per subdomain solve, >= 1                       */
     int32_t reserved0;       /* must be 0                                                          */
     double Lx, Ly;           /* physical rectangle [0, Lx] x [0, Ly], > 0                           */
@@ -192,6 +192,35 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
 /* Test hook: n Philox4x32-10 draws on the device (ctr n x 4, key n x 2, out n x 4 words),
  * on the legacy default stream; returns after `out` is written. */
 sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
+
+/* ---- Batches of independent problems ------------------------------------------------------
+ * Many problems of uneven grid and subdomain counts advance one alternating step together
+ * (Sec. 3.6 for each): per problem the monitor preparation and the scatter of Dirichlet data;
+ * ONE persistent path-kernel launch per round for the interface nodes of all problems, and
+ * ONE launch for all subdomain solves (one CTA per (problem, subdomain)).  Each problem's
+ * results are bitwise those of sdd_step on it alone (own seed, local node ids in the Philox
+ * counter, per-node path schedule, fixed-order reductions).  All problems must share
+ * precision, se_target and paths_per_node (and max_paths_per_node when adaptive); the batch
+ * keeps pointers to them (they must outlive it) and orders its work on `stream`.
+ * use_graph = 1 (fixed N only, stream not NULL): the first step records its launches in a CUDA
+ * graph that later steps replay (re-recorded if a problem's mesh buffers change). */
+typedef struct sdd_batch sdd_batch;
+
+sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* stream, int32_t use_graph,
+                            sdd_batch** out);
+
+/* One alternating step of every problem of the batch (x^n <- x^{n+1}, n <- n + 1 for each).
+ * Returns after queueing the work on the batch's stream. */
+sdd_status sdd_batch_step(sdd_batch* b);
+
+/* Counters of the last batch step over all problems: M, path_steps, paths, mc_rounds,
+ * nodes_not_reached, max_se, solve maxima, kernel_launches (since creation), and in
+ * mc_kernel_ms the device time of the whole last step (CUDA events on the batch's stream).
+ * Waits for the batch's stream. */
+sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out);
+
+/* Release the batch (not its problems). */
+void sdd_batch_destroy(sdd_batch* b);
 
 /* Allocation-free interface Monte Carlo.  The paper has no counterpart: this entry point
  * serves callers that cannot call cudaMalloc -- for instance a host framework whose caching

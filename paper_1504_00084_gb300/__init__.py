@@ -60,6 +60,7 @@ EXPORTS = [
     "sdd_step", "sdd_get_stats", "sdd_get_interface_nodes", "sdd_interface_layout",
     "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
     "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
+    "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy",
 ]
 
 
@@ -88,6 +89,10 @@ def _load():
         "sdd_debug_paths": ([P, I32, I64, I64, P, P, P], I32),
         "sdd_debug_philox": ([P, P, I64, P], I32),
         "sdd_interface_mc_noalloc": ([ctypes.POINTER(SddParams), P, P, P, I32, P, P, P], I32),
+        "sdd_batch_create": ([P, I32, P, I32, ctypes.POINTER(P)], I32),
+        "sdd_batch_step": ([P], I32),
+        "sdd_batch_get_stats": ([P, ctypes.POINTER(SddStats)], I32),
+        "sdd_batch_destroy": ([P], None),
         "sdd_status_string": ([I32], ctypes.c_char_p),
         "sdd_last_error": ([], ctypes.c_char_p),
     }
@@ -331,3 +336,57 @@ class SddProblem:
 
     def debug_paths(self, node, p_begin, n_paths):
         return sdd_debug_paths(self.h, node, p_begin, n_paths)
+
+
+def sdd_batch_create(problems, stream=None, use_graph=False) -> int:
+    handles = [p.h if isinstance(p, SddProblem) else p for p in problems]
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    h = ctypes.c_void_p()
+    _check(lib.sdd_batch_create(arr, len(handles), _stream_handle(stream), 1 if use_graph else 0,
+                                ctypes.byref(h)), "sdd_batch_create")
+    return h.value
+
+
+def sdd_batch_step(b: int) -> None:
+    _check(lib.sdd_batch_step(b), "sdd_batch_step")
+
+
+def sdd_batch_get_stats(b: int) -> dict:
+    s = SddStats()
+    _check(lib.sdd_batch_get_stats(b, ctypes.byref(s)), "sdd_batch_get_stats")
+    return s.as_dict()
+
+
+def sdd_batch_destroy(b: int) -> None:
+    lib.sdd_batch_destroy(b)
+
+
+class SddBatch:
+    """Owning handle of a batch (its problems stay owned by the caller)."""
+
+    def __init__(self, problems, stream=None, use_graph=False):
+        self.problems = list(problems)
+        self.h = sdd_batch_create(self.problems, stream, use_graph)
+
+    def step(self):
+        sdd_batch_step(self.h)
+
+    def stats(self):
+        return sdd_batch_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            sdd_batch_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

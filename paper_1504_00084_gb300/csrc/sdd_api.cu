@@ -14,6 +14,7 @@
 
 #include "sdd.h"
 #include "sdd_internal.cuh"
+#include "sdd_problem.cuh"
 
 using namespace sdd;
 
@@ -26,6 +27,12 @@ sdd_status fail(sdd_status s, const std::string& msg)
     g_err = msg;
     return s;
 }
+
+}  // namespace
+
+sdd_status sdd_fail(sdd_status s, const char* msg) { return fail(s, msg); }
+
+namespace {
 
 #define SDD_CK(call)                                                                       \
     do {                                                                                   \
@@ -80,66 +87,6 @@ bool is_device_ptr(const void* ptr)
 
 }  // namespace
 
-struct sdd_problem {
-    sdd_params prm{};
-    cudaStream_t stream = nullptr;
-    int M = 0;
-    std::vector<int32_t> ij;
-    int mc_grid = 1;
-    bool fp64 = true;
-    int acc_mode = kAcc64;
-    int64_t step = 0;
-    bool have_est = false;
-    // monitor
-    int mon_kind = 0;
-    int n_params = 0;
-    double mon_params[64] = {0};
-    // device: mesh and monitor
-    double *x = nullptr, *y = nullptr, *xn = nullptr, *yn = nullptr;
-    double *om64 = nullptr, *wxi64 = nullptr, *weta64 = nullptr, *omega_nodal = nullptr;
-    void *mon = nullptr, *disp = nullptr;
-    int2* nodes = nullptr;
-    double* shift = nullptr;
-    // device: interface MC
-    double* acc = nullptr;
-    int64_t *n_done = nullptr, *steps = nullptr, *paths_run = nullptr, *next_total = nullptr;
-    int32_t* node_of = nullptr;
-    int64_t *p_begin = nullptr, *p_count = nullptr, *task_off = nullptr;
-    int32_t *n_active = nullptr, *task_counter = nullptr;
-    TaskSlot* slots = nullptr;
-    int64_t slot_cap = 0;
-    double *est = nullptr, *se = nullptr;
-    // device: solves
-    double *ce64 = nullptr, *cn64 = nullptr;
-    void *ce = nullptr, *cn = nullptr, *vec = nullptr;
-    int32_t *st_iters = nullptr, *st_outer = nullptr, *st_ok = nullptr;
-    double* st_res = nullptr;
-    // host
-    int32_t* h_n_active = nullptr;  // pinned
-    sdd_stats stats{};
-    std::vector<void*> allocs;
-    std::vector<cudaEvent_t> ev;  // start/stop pairs around path-kernel launches
-    int64_t launches = 0;         // kernels launched since creation
-
-    template <typename P>
-    cudaError_t dalloc(P** p, size_t bytes)
-    {
-        void* v = nullptr;
-        cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
-        if (e == cudaSuccess) {
-            allocs.push_back(v);
-            *p = static_cast<P*>(v);
-        }
-        return e;
-    }
-    ~sdd_problem()
-    {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        for (void* v : allocs) cudaFree(v);
-        if (h_n_active) cudaFreeHost(h_n_active);
-    }
-};
-
 namespace {
 
 sdd_status validate(const sdd_params* P)
@@ -156,7 +103,7 @@ sdd_status validate(const sdd_params* P)
         return fail(SDD_ERR_INVALID_ARG, "bad precision");
     if (P->bicubic != 0 && P->bicubic != 1) return fail(SDD_ERR_INVALID_ARG, "bicubic must be 0 or 1");
     if (P->bb_test != 0 && P->bb_test != 1) return fail(SDD_ERR_INVALID_ARG, "bb_test must be 0 or 1");
-    if (P->substeps < 1) return fail(SDD_ERR_INVALID_ARG, "substeps must be >= 1");
+    if (P->substeps < 1 || P->substeps > (1 << 20)) return fail(SDD_ERR_INVALID_ARG, "substeps must be in [1, 2^20]");
     if (P->solve_max_iter < 1) return fail(SDD_ERR_INVALID_ARG, "solve_max_iter must be >= 1");
     if (P->reserved0 != 0) return fail(SDD_ERR_INVALID_ARG, "reserved0 must be 0");
     if (!(P->Lx > 0) || !(P->Ly > 0) || !(P->tau > 0) || !(P->dt > 0))
@@ -236,20 +183,11 @@ template <typename T>
 McParams<T> mc_params(const sdd_problem* p)
 {
     McParams<T> P{};
-    P.mon = static_cast<const Mon4<T>*>(p->mon);
-    P.disp = static_cast<const Disp2<T>*>(p->disp);
-    P.nodes = p->nodes; P.shift = p->shift;
+    P.prob = mc_problem<T>(p);
+    P.shift = p->shift;
     P.node_of = p->node_of; P.p_begin = p->p_begin; P.p_count = p->p_count;
     P.task_off = p->task_off; P.n_active = p->n_active; P.task_counter = p->task_counter;
     P.slots = p->slots;
-    P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic; P.form = p->prm.form;
-    P.K = p->prm.substeps; P.bicubic = p->prm.bicubic; P.bb = p->prm.bb_test;
-    const T ds = (T)p->prm.dt / (T)p->prm.substeps;
-    P.cb = ds / (T)p->prm.tau;
-    P.Lx = (T)p->prm.Lx; P.Ly = (T)p->prm.Ly;
-    P.key0 = (uint32_t)(p->prm.seed & 0xFFFFFFFFu);
-    P.key1 = (uint32_t)(p->prm.seed >> 32);
-    P.tstep = (uint32_t)p->step;
     return P;
 }
 
@@ -259,11 +197,11 @@ sdd_status launch_mc_round(sdd_problem* p, bool debug, double* dval, int32_t* ds
     if (p->fp64) {
         McParams<double> P = mc_params<double>(p);
         P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0;
-        SDD_CK(launch_mc<double>(P, p->acc_mode, debug, p->mc_grid, p->stream));
+        SDD_CK(launch_mc<double>(P, p->acc_mode, debug, false, p->mc_grid, p->stream));
     } else {
         McParams<float> P = mc_params<float>(p);
         P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0;
-        SDD_CK(launch_mc<float>(P, p->acc_mode, debug, p->mc_grid, p->stream));
+        SDD_CK(launch_mc<float>(P, p->acc_mode, debug, false, p->mc_grid, p->stream));
     }
     return SDD_OK;
 }
@@ -509,8 +447,8 @@ sdd_status sdd_create_problem(const sdd_params* params, const double* x0, const 
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = p->fp64 ? mc_max_blocks_per_sm<double>(p->acc_mode, false)
-                               : mc_max_blocks_per_sm<float>(p->acc_mode, false);
+    const int per_sm = p->fp64 ? mc_max_blocks_per_sm<double>(p->acc_mode, false, false)
+                               : mc_max_blocks_per_sm<float>(p->acc_mode, false, false);
     p->mc_grid = nsm * per_sm;
     p->stats.M = p->M;
     p->stats.t = params->t0;

@@ -1,0 +1,432 @@
+// Batched stepping of independent SDD problems (sdd_batch_*, declared in include/sdd.h).
+//
+// Many mesh problems of uneven grid and subdomain counts advance one alternating step
+// together: per problem, the monitor preparation and the Dirichlet-data scatter; then ONE
+// persistent path-kernel launch per round serves the interface nodes of every problem (the
+// round plan runs over the concatenated node list, every task carries its problem), and ONE
+// launch solves every subdomain of every problem (one CTA per (problem, subdomain)).
+//
+// A problem's results do not depend on its batch: its paths use its own seed and local node
+// ids in the Philox counter, its nodes follow their own chunk schedule, and every sum is a
+// fixed-order reduction over its own tasks -- the meshes are bitwise those of stepping each
+// problem alone.
+//
+// Per-step inputs that change between steps (time-step index, time) are read from device
+// records refreshed from pinned host memory at the start of each step, and the new mesh is
+// copied into the current one instead of swapping pointers, so a fixed-N step is one fixed
+// launch sequence: with use_graph it is captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "sdd.h"
+#include "sdd_internal.cuh"
+#include "sdd_problem.cuh"
+
+using namespace sdd;
+
+namespace {
+
+constexpr int64_t kMaxChunk = int64_t(1) << 19;           // paths per node per round (plan kernel)
+constexpr int kSlotsPerNode = (int)(kMaxChunk / kPathsPerTask);
+constexpr int kMaxRounds = 4096;
+
+}  // namespace
+
+struct sdd_batch {
+    std::vector<sdd_problem*> probs;
+    cudaStream_t stream = nullptr;
+    bool fp64 = false;
+    int acc_mode = kAcc64;
+    bool use_graph = false;
+    int n = 0;
+    int M = 0;                       // interface nodes of all problems
+    int total_subs = 0;
+    std::vector<int32_t> node_off, sub_off;
+    int mc_grid = 1;
+    // device: concatenated node arrays and round plan
+    int32_t* node_prob = nullptr;
+    double *shift = nullptr, *acc = nullptr, *est = nullptr, *se = nullptr;
+    int64_t *n_done = nullptr, *steps = nullptr, *paths_run = nullptr, *next_total = nullptr;
+    int64_t *p_begin = nullptr, *p_count = nullptr, *task_off = nullptr;
+    int32_t *node_of = nullptr, *n_active = nullptr, *task_counter = nullptr;
+    TaskSlot* slots = nullptr;
+    // device records refreshed every step, and their pinned host sources
+    void* mcprob_dev = nullptr;
+    void* mcprob_host = nullptr;
+    SolveParams* solve_dev = nullptr;
+    SolveParams* solve_host = nullptr;
+    double* t_dev = nullptr;
+    double* t_host = nullptr;
+    int32_t* sub_off_dev = nullptr;
+    int32_t* h_n_active = nullptr;
+    // graph
+    cudaGraphExec_t graph = nullptr;
+    std::vector<const double*> graph_x;  // mesh pointers the graph was recorded with
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int64_t launches = 0;
+    int64_t launches_per_step = 0;
+    int32_t rounds_last = 0;
+    double step_ms_last = 0.0;
+    std::vector<void*> allocs;
+    std::vector<void*> host_allocs;
+
+    template <typename P>
+    cudaError_t dalloc(P** p, size_t bytes)
+    {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
+        if (e == cudaSuccess) {
+            allocs.push_back(v);
+            *p = static_cast<P*>(v);
+        }
+        return e;
+    }
+    template <typename P>
+    cudaError_t halloc(P** p, size_t bytes)
+    {
+        void* v = nullptr;
+        cudaError_t e = cudaHostAlloc(&v, bytes < 16 ? 16 : bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) {
+            host_allocs.push_back(v);
+            *p = static_cast<P*>(v);
+        }
+        return e;
+    }
+    ~sdd_batch()
+    {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        for (void* v : allocs) cudaFree(v);
+        for (void* v : host_allocs) cudaFreeHost(v);
+    }
+};
+
+namespace {
+
+#define B_CK(call)                                                                         \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            const std::string m_ = std::string(#call) + ": " + cudaGetErrorString(e_);     \
+            return sdd_fail(e_ == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA,  \
+                            m_.c_str());                                                   \
+        }                                                                                  \
+    } while (0)
+
+SolveParams solve_params(const sdd_problem* p)
+{
+    SolveParams S{};
+    S.nx = p->prm.nx; S.ny = p->prm.ny; S.px = p->prm.px; S.py = p->prm.py; S.form = p->prm.form;
+    S.r = p->prm.dt / p->prm.tau; S.rtol = p->prm.solve_rtol; S.max_iter = p->prm.solve_max_iter;
+    S.om64 = p->om64; S.xcur = p->x; S.ycur = p->y; S.xnew = p->xn; S.ynew = p->yn;
+    S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
+    S.stat_iters = p->st_iters; S.stat_outer = p->st_outer; S.stat_ok = p->st_ok; S.stat_res = p->st_res;
+    return S;
+}
+
+// Host copies of the per-step records (call with no step of this batch in flight).
+void refresh_records(sdd_batch* b)
+{
+    for (int i = 0; i < b->n; ++i) {
+        const sdd_problem* p = b->probs[i];
+        if (b->fp64) {
+            McProblem<double> R = mc_problem<double>(p);
+            R.node_offset = b->node_off[i];
+            static_cast<McProblem<double>*>(b->mcprob_host)[i] = R;
+        } else {
+            McProblem<float> R = mc_problem<float>(p);
+            R.node_offset = b->node_off[i];
+            static_cast<McProblem<float>*>(b->mcprob_host)[i] = R;
+        }
+        b->solve_host[i] = solve_params(p);
+        b->t_host[i] = p->prm.t0 + (double)p->step * p->prm.dt;
+    }
+}
+
+template <typename T>
+sdd_status launch_batch_mc(sdd_batch* b)
+{
+    McParams<T> P{};
+    P.probs = static_cast<const McProblem<T>*>(b->mcprob_dev);
+    P.node_prob = b->node_prob;
+    P.shift = b->shift;
+    P.node_of = b->node_of; P.p_begin = b->p_begin; P.p_count = b->p_count; P.task_off = b->task_off;
+    P.n_active = b->n_active; P.task_counter = b->task_counter; P.slots = b->slots;
+    B_CK(launch_mc<T>(P, b->acc_mode, false, true, b->mc_grid, b->stream));
+    return SDD_OK;
+}
+
+// The launches of one step.  `capturing`: only fixed-N work (no host round trip).
+sdd_status record_step(sdd_batch* b)
+{
+    const size_t rec = b->fp64 ? sizeof(McProblem<double>) : sizeof(McProblem<float>);
+    int64_t launches = 0;
+    B_CK(cudaMemcpyAsync(b->mcprob_dev, b->mcprob_host, rec * b->n, cudaMemcpyHostToDevice, b->stream));
+    B_CK(cudaMemcpyAsync(b->solve_dev, b->solve_host, sizeof(SolveParams) * b->n, cudaMemcpyHostToDevice,
+                         b->stream));
+    B_CK(cudaMemcpyAsync(b->t_dev, b->t_host, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream));
+    for (int i = 0; i < b->n; ++i) {
+        sdd_problem* p = b->probs[i];
+        PrepParams P{};
+        P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic;
+        P.kind = p->mon_kind; P.n_params = p->n_params; P.precision = p->prm.precision;
+        P.Lx = p->prm.Lx; P.Ly = p->prm.Ly; P.t = 0.0; P.t_dev = b->t_dev + i;
+        P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
+        memcpy(P.params, p->mon_params, sizeof(P.params));
+        P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
+        B_CK(launch_prep(P, b->stream));
+        launches += 2;
+        if (p->M > 0) {
+            B_CK(launch_shift(p->nodes, p->M, p->prm.nx, p->x, p->y, b->shift + 2 * (size_t)b->node_off[i],
+                              b->stream));
+            launches += 1;
+        }
+    }
+    if (b->M > 0) {
+        const sdd_params& q = b->probs[0]->prm;
+        const bool adaptive = q.se_target > 0;
+        const int64_t n0 = q.paths_per_node;
+        const int64_t maxp = adaptive ? q.max_paths_per_node : n0;
+        B_CK(launch_mc_init(b->M, n0, maxp, b->acc, b->n_done, b->steps, b->paths_run, b->next_total,
+                            b->stream));
+        launches += 1;
+        PlanParams PP{};
+        PP.M = b->M; PP.n_done = b->n_done; PP.next_total = b->next_total; PP.node_of = b->node_of;
+        PP.p_begin = b->p_begin; PP.p_count = b->p_count; PP.task_off = b->task_off;
+        PP.n_active = b->n_active; PP.task_counter = b->task_counter;
+        ReduceParams RP{};
+        RP.node_of = b->node_of; RP.p_count = b->p_count; RP.task_off = b->task_off; RP.n_active = b->n_active;
+        RP.slots = b->slots; RP.shift = b->shift; RP.acc = b->acc; RP.n_done = b->n_done; RP.steps = b->steps;
+        RP.paths_run = b->paths_run; RP.next_total = b->next_total;
+        RP.se_target = adaptive ? q.se_target : 0.0; RP.max_paths = maxp;
+        int32_t rounds = 0;
+        if (!adaptive) {
+            const int64_t nr = (n0 + kMaxChunk - 1) / kMaxChunk;
+            for (int64_t r = 0; r < nr; ++r) {
+                B_CK(launch_plan(PP, b->stream));
+                const sdd_status s = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
+                if (s != SDD_OK) return s;
+                B_CK(launch_reduce(RP, b->M, b->stream));
+                launches += 3;
+                rounds += 1;
+            }
+        } else {
+            for (int r = 0; r < kMaxRounds; ++r) {
+                B_CK(launch_plan(PP, b->stream));
+                launches += 1;
+                B_CK(cudaMemcpyAsync(b->h_n_active, b->n_active, 4, cudaMemcpyDeviceToHost, b->stream));
+                B_CK(cudaStreamSynchronize(b->stream));
+                if (*b->h_n_active == 0) break;
+                const sdd_status s = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
+                if (s != SDD_OK) return s;
+                B_CK(launch_reduce(RP, b->M, b->stream));
+                launches += 2;
+                rounds += 1;
+            }
+        }
+        b->rounds_last = rounds;
+        B_CK(launch_output(b->M, b->acc, b->n_done, b->shift, b->est, b->se, b->stream));
+        launches += 1;
+    }
+    const bool fp64_inner = b->fp64;
+    for (int i = 0; i < b->n; ++i) {
+        sdd_problem* p = b->probs[i];
+        B_CK(launch_scatter(p->prm.nx, p->prm.ny, p->prm.periodic, p->prm.Lx, p->prm.Ly, p->nodes, p->M,
+                            b->est + 2 * (size_t)b->node_off[i], p->xn, p->yn, b->stream));
+        launches += (p->prm.periodic ? 0 : 1) + (p->M > 0 ? 1 : 0);
+        B_CK(launch_faces(b->solve_host[i], fp64_inner, b->stream));
+        launches += 1;
+    }
+    B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream));
+    launches += 1;
+    for (int i = 0; i < b->n; ++i) {
+        sdd_problem* p = b->probs[i];
+        const size_t bytes = (size_t)p->prm.nx * p->prm.ny * 8;
+        B_CK(cudaMemcpyAsync(p->x, p->xn, bytes, cudaMemcpyDeviceToDevice, b->stream));
+        B_CK(cudaMemcpyAsync(p->y, p->yn, bytes, cudaMemcpyDeviceToDevice, b->stream));
+    }
+    b->launches_per_step = launches;
+    return SDD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* stream, int32_t use_graph,
+                            sdd_batch** out)
+{
+    if (!out) return sdd_fail(SDD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!problems || n < 1) return sdd_fail(SDD_ERR_INVALID_ARG, "need at least one problem");
+    if (use_graph != 0 && use_graph != 1) return sdd_fail(SDD_ERR_INVALID_ARG, "use_graph must be 0 or 1");
+    for (int i = 0; i < n; ++i)
+        if (!problems[i]) return sdd_fail(SDD_ERR_INVALID_ARG, "NULL problem");
+    const sdd_params& q = problems[0]->prm;
+    for (int i = 1; i < n; ++i) {
+        const sdd_params& r = problems[i]->prm;
+        if (r.precision != q.precision || r.se_target != q.se_target || r.paths_per_node != q.paths_per_node ||
+            (q.se_target > 0 && r.max_paths_per_node != q.max_paths_per_node))
+            return sdd_fail(SDD_ERR_INVALID_ARG,
+                            "batched problems must share precision, se_target and path counts");
+        for (int k = 0; k < i; ++k)
+            if (problems[k] == problems[i]) return sdd_fail(SDD_ERR_INVALID_ARG, "a problem appears twice");
+    }
+    if (use_graph && (q.se_target > 0 || !stream))
+        return sdd_fail(SDD_ERR_INVALID_ARG, "graph mode needs fixed N and a non-NULL stream");
+    sdd_batch* b = new sdd_batch();
+    b->probs.assign(problems, problems + n);
+    b->n = n;
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->fp64 = q.precision == SDD_FP64;
+    b->acc_mode = q.precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
+    b->use_graph = use_graph != 0;
+    std::vector<int32_t> node_prob;
+    b->sub_off.push_back(0);
+    for (int i = 0; i < n; ++i) {
+        b->node_off.push_back(b->M);
+        b->M += problems[i]->M;
+        node_prob.insert(node_prob.end(), problems[i]->M, i);
+        b->total_subs += problems[i]->prm.px * problems[i]->prm.py;
+        b->sub_off.push_back(b->total_subs);
+    }
+    const size_t M = (size_t)b->M + 1;
+    const size_t rec = b->fp64 ? sizeof(McProblem<double>) : sizeof(McProblem<float>);
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes) if (e == cudaSuccess) e = b->dalloc(&(ptr), (bytes))
+#define HALLOC(ptr, bytes) if (e == cudaSuccess) e = b->halloc(&(ptr), (bytes))
+    ALLOC(b->node_prob, M * 4); ALLOC(b->shift, M * 16); ALLOC(b->acc, M * 32); ALLOC(b->est, M * 16);
+    ALLOC(b->se, M * 16); ALLOC(b->n_done, M * 8); ALLOC(b->steps, M * 8); ALLOC(b->paths_run, M * 8);
+    ALLOC(b->next_total, M * 8); ALLOC(b->p_begin, M * 8); ALLOC(b->p_count, M * 8);
+    ALLOC(b->task_off, (M + 1) * 8); ALLOC(b->node_of, M * 4); ALLOC(b->n_active, 16);
+    ALLOC(b->task_counter, 16); ALLOC(b->slots, M * kSlotsPerNode * sizeof(TaskSlot));
+    ALLOC(b->mcprob_dev, rec * n); ALLOC(b->solve_dev, sizeof(SolveParams) * n); ALLOC(b->t_dev, 8 * n);
+    ALLOC(b->sub_off_dev, 4 * (n + 1));
+    HALLOC(b->mcprob_host, rec * n); HALLOC(b->solve_host, sizeof(SolveParams) * n); HALLOC(b->t_host, 8 * n);
+    HALLOC(b->h_n_active, 16);
+#undef ALLOC
+#undef HALLOC
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess && b->M > 0)
+        e = cudaMemcpy(b->node_prob, node_prob.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->sub_off_dev, b->sub_off.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const std::string m = std::string("batch allocation failed: ") + cudaGetErrorString(e);
+        delete b;
+        return sdd_fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, m.c_str());
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    b->mc_grid = nsm * (b->fp64 ? mc_max_blocks_per_sm<double>(b->acc_mode, false, true)
+                                : mc_max_blocks_per_sm<float>(b->acc_mode, false, true));
+    *out = b;
+    return SDD_OK;
+}
+
+void sdd_batch_destroy(sdd_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    delete b;
+}
+
+sdd_status sdd_batch_step(sdd_batch* b)
+{
+    if (!b) return sdd_fail(SDD_ERR_INVALID_ARG, "batch is NULL");
+    for (sdd_problem* p : b->probs) B_CK(cudaStreamSynchronize(p->stream));
+    B_CK(cudaStreamSynchronize(b->stream));  // no step of this batch in flight: safe to refresh records
+    refresh_records(b);
+    B_CK(cudaEventRecord(b->ev0, b->stream));
+    if (b->use_graph) {
+        bool stale = !b->graph || b->graph_x.size() != b->probs.size();
+        for (size_t i = 0; !stale && i < b->probs.size(); ++i) stale = b->graph_x[i] != b->probs[i]->x;
+        if (stale) {
+            if (b->graph) {
+                cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            B_CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            const sdd_status s = record_step(b);
+            const cudaError_t ce = cudaStreamEndCapture(b->stream, &g);
+            if (s != SDD_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            if (ce != cudaSuccess) return sdd_fail(SDD_ERR_CUDA, cudaGetErrorString(ce));
+            const cudaError_t ie = cudaGraphInstantiate(&b->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) return sdd_fail(SDD_ERR_CUDA, cudaGetErrorString(ie));
+            b->graph_x.clear();
+            for (sdd_problem* p : b->probs) b->graph_x.push_back(p->x);
+        }
+        B_CK(cudaGraphLaunch(b->graph, b->stream));
+    } else {
+        const sdd_status s = record_step(b);
+        if (s != SDD_OK) return s;
+    }
+    B_CK(cudaEventRecord(b->ev1, b->stream));
+    b->launches += b->launches_per_step;
+    for (sdd_problem* p : b->probs) {
+        p->step += 1;
+        p->have_est = false;
+        p->stats.step_index = (int32_t)p->step;
+        p->stats.t = p->prm.t0 + (double)p->step * p->prm.dt;
+    }
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out)
+{
+    if (!b || !out) return sdd_fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    B_CK(cudaStreamSynchronize(b->stream));
+    sdd_stats s{};
+    s.M = b->M;
+    s.step_index = b->probs[0]->stats.step_index;
+    s.t = b->probs[0]->stats.t;
+    s.mc_rounds = b->rounds_last;
+    s.kernel_launches = b->launches;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) s.mc_kernel_ms = ms;  // whole last step
+    cudaGetLastError();
+    if (b->M > 0) {
+        std::vector<int64_t> st(b->M), np(b->M);
+        std::vector<double> se((size_t)2 * b->M);
+        B_CK(cudaMemcpy(st.data(), b->steps, 8 * (size_t)b->M, cudaMemcpyDeviceToHost));
+        B_CK(cudaMemcpy(np.data(), b->paths_run, 8 * (size_t)b->M, cudaMemcpyDeviceToHost));
+        B_CK(cudaMemcpy(se.data(), b->se, 16 * (size_t)b->M, cudaMemcpyDeviceToHost));
+        const double target = b->probs[0]->prm.se_target;
+        for (int m = 0; m < b->M; ++m) {
+            s.path_steps += st[m];
+            s.paths += np[m];
+            const double v = se[2 * m] > se[2 * m + 1] ? se[2 * m] : se[2 * m + 1];
+            if (v > s.max_se) s.max_se = v;
+            if (target > 0 && v > target) s.nodes_not_reached += 1;
+        }
+    }
+    for (sdd_problem* p : b->probs) {
+        const int ns = p->prm.px * p->prm.py;
+        std::vector<int32_t> it(ns), ou(ns);
+        std::vector<double> rs(ns);
+        B_CK(cudaMemcpy(it.data(), p->st_iters, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+        B_CK(cudaMemcpy(ou.data(), p->st_outer, 4 * (size_t)ns, cudaMemcpyDeviceToHost));
+        B_CK(cudaMemcpy(rs.data(), p->st_res, 8 * (size_t)ns, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < ns; ++k) {
+            if (it[k] > s.solve_iters_max) s.solve_iters_max = it[k];
+            if (ou[k] > s.solve_outer_max) s.solve_outer_max = ou[k];
+            if (rs[k] > s.solve_rel_residual) s.solve_rel_residual = rs[k];
+        }
+    }
+    *out = s;
+    return SDD_OK;
+}
+
+}  // extern "C"

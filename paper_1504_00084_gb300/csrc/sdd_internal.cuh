@@ -29,7 +29,7 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t
     constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)kM0 * c.x;   // one 32x32 -> 64 multiply each
+        const uint64_t p0 = (uint64_t)kM0 * c.x;   // 32 x 32 -> 64-bit products
         const uint64_t p1 = (uint64_t)kM1 * c.z;
         c = U4{(uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1,
                (uint32_t)p0};
@@ -76,12 +76,24 @@ constexpr int kPathsPerTask = 2048;
 // Adaptive chunk totals are multiples of this many paths.
 constexpr int64_t kAdaptiveGranule = 1024;
 
-template <typename T> struct McParams {
+// Per-problem inputs of the path kernel.
+template <typename T> struct McProblem {
     const Mon4<T>* mon;        // nx*ny packed monitor
     const Disp2<T>* disp;      // nx*ny packed displacement of the previous mesh
-    const int2* nodes;         // M interface nodes (i, j)
-    const double* shift;       // M x 2 estimator shifts (node's previous position)
-    // round plan (written by the plan kernel)
+    const int2* nodes;         // the problem's interface nodes (i, j), by local node id
+    int nx, ny, periodic, form, K, bicubic, bb;
+    T cb;                      // ds / tau
+    T Lx, Ly;
+    uint32_t key0, key1, tstep;
+    int32_t node_offset;       // global index of the problem's node 0 in the launch's node arrays
+};
+
+template <typename T> struct McParams {
+    McProblem<T> prob;         // single-problem launches
+    const McProblem<T>* probs; // batched launches: one record per problem (device memory)
+    const int32_t* node_prob;  // batched launches: problem of each global node
+    const double* shift;       // global nodes x 2: estimator shifts (node's previous position)
+    // round plan (written by the plan kernel), over global node indices
     const int32_t* node_of;    // active node ids
     const int64_t* p_begin;    // first path index of each active node's chunk
     const int64_t* p_count;    // chunk length
@@ -89,16 +101,11 @@ template <typename T> struct McParams {
     const int32_t* n_active;   // device scalar
     int32_t* task_counter;     // dynamic task dispenser (reset by the plan kernel)
     TaskSlot* slots;           // one per task
-    // debug records (null unless the debug variant runs)
+    // debug records (null unless the debug variant runs; single-problem launches only)
     double* dbg_val;
     int32_t* dbg_steps;
     int8_t* dbg_side;
     int64_t dbg_p0;
-    // problem
-    int nx, ny, periodic, form, K, bicubic, bb;
-    T cb;                      // ds / tau
-    T Lx, Ly;
-    uint32_t key0, key1, tstep;
 };
 
 struct PlanParams {
@@ -133,6 +140,7 @@ struct ReduceParams {
 struct PrepParams {
     int nx, ny, periodic, kind, n_params, precision;
     double Lx, Ly, t;
+    const double* t_dev;       // if set, the time is read from device memory (graph replays)
     const double* x;           // current mesh
     const double* y;
     const double* omega_in;    // nodal monitor (kind == NODAL)
@@ -175,12 +183,15 @@ cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, in
                            int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& P, cudaStream_t s);
 template <typename T>
-cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, int grid, cudaStream_t s);
-template <typename T> int mc_max_blocks_per_sm(int acc_mode, bool debug);
+cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s);
+template <typename T> int mc_max_blocks_per_sm(int acc_mode, bool debug, bool batch);
 cudaError_t launch_reduce(const ReduceParams& P, int M, cudaStream_t s);
 cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const double* shift,
                           double* est, double* se, cudaStream_t s);
 cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s);
+cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s);
+cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
+                               bool fp64_inner, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                           cudaStream_t s);
 

@@ -5,12 +5,16 @@
 // pulls tasks from an atomic counter.  Inside a task each lane runs one path at a time and,
 // when its path ends (exit or K substeps), immediately takes the next unused path index of
 // the task (ballot + popc), so the 32 lanes stay busy through paths of very different
-// lengths.  The assignment of path indices to lanes depends only on the paths' own lengths,
+// lengths.  A path that completes its K substeps parks its final point in a per-warp
+// shared-memory queue; the warp evaluates the bicubic terminal values 32 at a time, one per
+// lane, instead of stalling on that long branch whenever any single lane finishes.  The
+// assignment of path indices to lanes depends only on the paths' own lengths,
 // so a task's partial sums are a deterministic function of (node, path range) and are
 // independent of scheduling and of which other problems or nodes share the launch.
 //
 // Per substep and lane: one Philox4x32-10 call keyed by the seed with counter
-// (k, p, m, n) -> Box-Muller normals (words 0, 1) and the bridge uniform (word 2); bilinear
+// (k, p, m, n) -> Box-Muller normals (words 0, 1; FP32 angle through sincos_2pi) and the
+// bridge uniform (word 2); bilinear
 // gather of {omega, omega_xi, omega_eta} from the packed monitor (read-only cache; the
 // record of a node is one 16-byte (FP32) or 32-byte (FP64) load); Euler-Maruyama update
 // (Eq. 7); endpoint and Brownian-bridge exit tests.  Terminal values: the boundary mesh at
@@ -30,25 +34,56 @@ namespace {
 constexpr int kMcThreads = 256;
 constexpr unsigned kFull = 0xffffffffu;
 #ifndef SDD_MC_MIN_BLOCKS
-#define SDD_MC_MIN_BLOCKS 4   // resident blocks per SM asked of the register allocator (64 registers)
+#define SDD_MC_MIN_BLOCKS 4   // FP32: resident blocks per SM asked of the register allocator (64 registers)
 #endif
+// FP64 paths need more registers; two resident blocks keep them out of local memory.
+template <typename T> constexpr int mc_min_blocks() { return sizeof(T) == 8 ? 2 : SDD_MC_MIN_BLOCKS; }
 
 __device__ __forceinline__ float dlog(float x) { return logf(x); }
 __device__ __forceinline__ double dlog(double x) { return log(x); }
 __device__ __forceinline__ float dsqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double dsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float dexp(float x) { return expf(x); }
 __device__ __forceinline__ double dexp(double x) { return exp(x); }
 __device__ __forceinline__ float dfloor(float x) { return floorf(x); }
 __device__ __forceinline__ double dfloor(double x) { return floor(x); }
 __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double dabs(double x) { return fabs(x); }
-__device__ __forceinline__ void dsincos(float x, float* s, float* c) { sincosf(x, s, c); }
-__device__ __forceinline__ void dsincos(double x, double* s, double* c) { sincos(x, s, c); }
+
+// sin(2 pi u), cos(2 pi u) for u in (0, 1).  t = 4u is exact; with q = rint(t) and r = t - q
+// (exact, |r| <= 1/2) the angle is (pi/2)(q + r), so q mod 4 permutes and signs the sine and
+// cosine of (pi/2) r, taken from their Taylor series: coefficients (pi/2)^n / n! rounded to
+// FP32, truncated after r^9 (sine) and r^10 (cosine), where the remainders are below 2e-9 at
+// |r| = 1/2.  Measured error of the FP32 evaluation: below 0.75 ulp of 1 over the whole range.
+__device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs)
+{
+    const float t = 4.0f * u;
+    const float q = rintf(t);
+    const int qint = (int)q;
+    const float r = t - q;
+    const float r2 = r * r;
+    float ps = 0x1.507834p-13f;                 // (pi/2)^9 / 9!
+    ps = fmaf(ps, r2, -0x1.32d2ccp-8f);         // -(pi/2)^7 / 7!
+    ps = fmaf(ps, r2, 0x1.466bc6p-4f);          // (pi/2)^5 / 5!
+    ps = fmaf(ps, r2, -0x1.4abbcep-1f);         // -(pi/2)^3 / 3!
+    ps = fmaf(ps, r2, 0x1.921fb6p+0f);          // pi/2
+    ps *= r;
+    float pc = -0x1.a6d1f2p-16f;                // -(pi/2)^10 / 10!
+    pc = fmaf(pc, r2, 0x1.e1f506p-11f);         // (pi/2)^8 / 8!
+    pc = fmaf(pc, r2, -0x1.55d3c8p-6f);         // -(pi/2)^6 / 6!
+    pc = fmaf(pc, r2, 0x1.03c1f0p-2f);          // (pi/2)^4 / 4!
+    pc = fmaf(pc, r2, -0x1.3bd3ccp+0f);         // -(pi/2)^2 / 2!
+    pc = fmaf(pc, r2, 1.0f);
+    const int qi = qint & 3;
+    float s_ = (qi & 1) ? pc : ps;
+    float c_ = (qi & 1) ? ps : pc;
+    if (qi & 2) s_ = -s_;           // quadrants 2, 3
+    if ((qi + 1) & 2) c_ = -c_;     // quadrants 1, 2
+    *sn = s_;
+    *cs = c_;
+}
 
 template <typename T> struct Consts;
 template <> struct Consts<float> {
-    static constexpr float two_pi = 6.28318530717958647692f;
     // exp(-a) below this argument's reach leaves 1 - exp(-a) == 1 exactly (and cannot be the
     // largest crossing probability of an exiting path), so the exponential is skipped.
     static constexpr float bridge_skip = 20.0f;
@@ -102,7 +137,7 @@ __device__ __forceinline__ void locate(int n, int periodic, T s, int& cell, T& f
 
 // Bilinear interpolation of the packed monitor at (xi, eta) (Sec. 3.4).
 template <typename T>
-__device__ __forceinline__ void monitor_at(const McParams<T>& P, T xi, T eta, T& w, T& wx, T& we)
+__device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T& w, T& wx, T& we)
 {
     int i, j;
     T fx, fy;
@@ -139,7 +174,7 @@ __device__ __forceinline__ T keys_combine(const T g[4], const T k[4])
 // extrapolation f(-1) = 3 f(0) - 3 f(1) + f(2) on Dirichlet grids, wrapped on periodic
 // grids; or bilinear.
 template <typename T>
-__device__ void mesh_at(const McParams<T>& P, T xi, T eta, T& ix, T& iy)
+__device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
 {
     int i, j;
     T tx, ty;
@@ -224,18 +259,31 @@ __device__ __forceinline__ T bridge_p(T d0, T d1, T q)
     const T a = d0 * d1;
     return (a > Consts<T>::bridge_skip * q) ? (T)0 : dexp(-a / q);
 }
+// FP32: the probability is only compared with a uniform deviate, so the hardware exponential
+// and divide (a few ulp) serve; the skip rule is unchanged.
+template <>
+__device__ __forceinline__ float bridge_p<float>(float d0, float d1, float q)
+{
+    const float a = d0 * d1;
+    return (a > Consts<float>::bridge_skip * q) ? 0.0f : __expf(-__fdividef(a, q));
+}
 
-// One substep k of path p at node m.  Returns true when the path ends at this substep
-// (exit, or k == K - 1); then (vx, vy) is its value and side its exit side (4: none).
+// One substep k of path p at node m.  Returns 0 while the path goes on; 1 when it exits
+// at this substep ((vx, vy) = boundary mesh at the exit point, side = exit side); 2 when it
+// completes its K-th substep ((xi, eta) = final point; its value, the previous mesh there,
+// is evaluated later for 32 such paths at once).
 template <typename T>
-__device__ __forceinline__ bool path_substep(const McParams<T>& P, uint32_t m, uint32_t p, int k,
+__device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, uint32_t p, int k,
                                              T& xi, T& eta, T& vx, T& vy, int& side)
 {
     const U4 w = philox4x32_10(U4{(uint32_t)k, p, m, P.tstep}, P.key0, P.key1);
     const T u1 = uniform_open(w.x, T()), u2 = uniform_open(w.y, T()), ub = uniform_open(w.z, T());
     const T r = dsqrt((T)-2 * dlog(u1));
     T sn, cs;
-    dsincos(Consts<T>::two_pi * u2, &sn, &cs);
+    if constexpr (sizeof(T) == 4)
+        sincos_2pi(u2, &sn, &cs);  // FP32: polynomial form (below 0.75 ulp)
+    else
+        sincos(Consts<T>::two_pi * u2, &sn, &cs);
     const T z1 = r * cs, z2 = r * sn;
 
     T wv, wx, we;
@@ -288,20 +336,12 @@ __device__ __forceinline__ bool path_substep(const McParams<T>& P, uint32_t m, u
             vx = P.Lx * xe;
             vy = P.Ly * ee;
             side = s;
-            return true;
+            return 1;
         }
     }
     xi = xn;
     eta = en;
-    if (k + 1 == P.K) {
-        T ix, iy;
-        mesh_at(P, xi, eta, ix, iy);
-        vx = P.Lx * xi + ix;
-        vy = P.Ly * eta + iy;
-        side = 4;
-        return true;
-    }
-    return false;
+    return k + 1 == P.K ? 2 : 0;
 }
 
 // Per-lane estimator sums of the shifted path values (shift = the node's previous position).
@@ -358,11 +398,115 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
     }
 };
 
+// Paths pb .. pe-1 of local node m of problem R (global node g): one warp, one task.
 template <typename T, int ACC, bool DEBUG>
-__global__ void __launch_bounds__(kMcThreads, SDD_MC_MIN_BLOCKS) mc_kernel(const __grid_constant__ McParams<T> P)
+__device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T>& R, int m, int g,
+                                         int task, int64_t pb, int64_t pe, T* q_xi, T* q_eta,
+                                         uint32_t* q_path)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    const int2 ij = R.nodes[m];
+    const T xi0 = (T)ij.x / (T)(R.nx - 1);
+    const T eta0 = (T)ij.y / (T)(R.ny - 1);
+    const double sx = P.shift[2 * g], sy = P.shift[2 * g + 1];
+
+    LaneAcc<T, ACC> acc(sx, sy);
+    uint32_t steps = 0, paths = 0;          // per lane and task: far below 2^32
+    uint32_t path = (uint32_t)pb + lane;    // path indices are below 2^32
+    const uint32_t pend = (uint32_t)pe;
+    bool live = path < pend;
+    uint32_t next = (uint32_t)pb + 32;
+    T xi = xi0, eta = eta0;
+    int k = 0;
+    int qn = 0;  // completed paths waiting for their terminal value (warp-uniform)
+    // terminal values of `count` queued paths at once, one per lane
+    auto drain = [&](int count) {
+        __syncwarp();
+        if (lane < count) {
+            const int pos = qn - count + lane;
+            const T fx = q_xi[pos], fy = q_eta[pos];
+            T ix, iy;
+            mesh_at(R, fx, fy, ix, iy);
+            const T vx = R.Lx * fx + ix, vy = R.Ly * fy + iy;
+            acc.add(vx, vy);
+            if (DEBUG) {
+                const int64_t qd = (int64_t)q_path[pos] - P.dbg_p0;  // debug only
+                P.dbg_val[2 * qd] = (double)vx;
+                P.dbg_val[2 * qd + 1] = (double)vy;
+                P.dbg_steps[qd] = R.K;
+                P.dbg_side[qd] = (int8_t)4;
+            }
+        }
+        qn -= count;
+        __syncwarp();
+    };
+    while (__any_sync(kFull, live)) {
+        int st = 0;
+        if (live) {
+            T vx, vy;
+            int side;
+            st = path_substep<T>(R, (uint32_t)m, path, k, xi, eta, vx, vy, side);
+            ++k;
+            if (st != 0) {
+                steps += (uint32_t)k;
+                paths += 1;
+            }
+            if (st == 1) {
+                acc.add(vx, vy);
+                if (DEBUG) {
+                    const int64_t qd = (int64_t)path - P.dbg_p0;
+                    P.dbg_val[2 * qd] = (double)vx;
+                    P.dbg_val[2 * qd + 1] = (double)vy;
+                    P.dbg_steps[qd] = k;
+                    P.dbg_side[qd] = (int8_t)side;
+                }
+            }
+        }
+        const unsigned sm = __ballot_sync(kFull, st == 2);
+        if (st == 2) {
+            const int pos = qn + __popc(sm & lt);
+            q_xi[pos] = xi;
+            q_eta[pos] = eta;
+            q_path[pos] = path;
+        }
+        qn += __popc(sm);
+        const unsigned dm = __ballot_sync(kFull, st != 0);
+        if (st != 0) {
+            path = next + __popc(dm & lt);
+            live = path < pend;
+            xi = xi0;
+            eta = eta0;
+            k = 0;
+        }
+        next += __popc(dm);
+        if (qn >= 32) drain(32);
+    }
+    if (qn > 0) drain(qn);
+    double a, b, c, d;
+    acc.finish(a, b, c, d, paths);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(kFull, a, off);
+        b += __shfl_xor_sync(kFull, b, off);
+        c += __shfl_xor_sync(kFull, c, off);
+        d += __shfl_xor_sync(kFull, d, off);
+        steps += __shfl_xor_sync(kFull, steps, off);
+        paths += __shfl_xor_sync(kFull, paths, off);
+    }
+    if (lane == 0) P.slots[task] = TaskSlot{a, b, c, d, steps, paths};
+}
+
+// Persistent path kernel.  BATCH: tasks of several problems share the launch; each task reads
+// its problem's record (the Philox counter uses the problem-local node id, so a problem's
+// results do not depend on what else shares the launch).
+template <typename T, int ACC, bool DEBUG, bool BATCH>
+__global__ void __launch_bounds__(kMcThreads, mc_min_blocks<T>()) mc_kernel(const __grid_constant__ McParams<T> P)
+{
+    constexpr int kWarps = kMcThreads / 32;
+    __shared__ T q_xi[kWarps][64], q_eta[kWarps][64];
+    __shared__ uint32_t q_path[kWarps][64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_active = *P.n_active;
     const int64_t n_tasks = P.task_off[n_active];
     for (;;) {
@@ -375,64 +519,17 @@ __global__ void __launch_bounds__(kMcThreads, SDD_MC_MIN_BLOCKS) mc_kernel(const
             const int mid = (lo + hi + 1) >> 1;
             if (P.task_off[mid] <= task) lo = mid; else hi = mid - 1;
         }
-        const int m = P.node_of[lo];
+        const int g = P.node_of[lo];
         const int64_t chunk_end = P.p_begin[lo] + P.p_count[lo];
         const int64_t pb = P.p_begin[lo] + ((int64_t)task - P.task_off[lo]) * kPathsPerTask;
         const int64_t pe = pb + kPathsPerTask < chunk_end ? pb + kPathsPerTask : chunk_end;
-        const int2 ij = P.nodes[m];
-        const T xi0 = (T)ij.x / (T)(P.nx - 1);
-        const T eta0 = (T)ij.y / (T)(P.ny - 1);
-        const double sx = P.shift[2 * m], sy = P.shift[2 * m + 1];
-
-        LaneAcc<T, ACC> acc(sx, sy);
-        unsigned long long steps = 0, paths = 0;
-        int64_t path = pb + lane;
-        bool live = path < pe;
-        int64_t next = pb + 32;
-        T xi = xi0, eta = eta0;
-        int k = 0;
-        while (__any_sync(kFull, live)) {
-            bool done = false;
-            if (live) {
-                T vx, vy;
-                int side;
-                done = path_substep<T>(P, (uint32_t)m, (uint32_t)path, k, xi, eta, vx, vy, side);
-                ++k;
-                if (done) {
-                    acc.add(vx, vy);
-                    steps += (unsigned long long)k;
-                    paths += 1;
-                    if (DEBUG) {
-                        const int64_t qd = path - P.dbg_p0;
-                        P.dbg_val[2 * qd] = (double)vx;
-                        P.dbg_val[2 * qd + 1] = (double)vy;
-                        P.dbg_steps[qd] = k;
-                        P.dbg_side[qd] = (int8_t)side;
-                    }
-                }
-            }
-            const unsigned dm = __ballot_sync(kFull, done);
-            if (done) {
-                path = next + __popc(dm & lt);
-                live = path < pe;
-                xi = xi0;
-                eta = eta0;
-                k = 0;
-            }
-            next += __popc(dm);
+        if constexpr (BATCH) {
+            const McProblem<T> R = P.probs[P.node_prob[g]];
+            run_task<T, ACC, DEBUG>(P, R, g - R.node_offset, g, task, pb, pe, q_xi[warp], q_eta[warp],
+                                    q_path[warp]);
+        } else {
+            run_task<T, ACC, DEBUG>(P, P.prob, g, g, task, pb, pe, q_xi[warp], q_eta[warp], q_path[warp]);
         }
-        double a, b, c, d;
-        acc.finish(a, b, c, d, paths);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            a += __shfl_xor_sync(kFull, a, off);
-            b += __shfl_xor_sync(kFull, b, off);
-            c += __shfl_xor_sync(kFull, c, off);
-            d += __shfl_xor_sync(kFull, d, off);
-            steps += __shfl_xor_sync(kFull, steps, off);
-            paths += __shfl_xor_sync(kFull, paths, off);
-        }
-        if (lane == 0) P.slots[task] = TaskSlot{a, b, c, d, steps, paths};
     }
 }
 
@@ -602,50 +699,56 @@ __global__ void philox_kernel(const uint32_t* ctr, const uint32_t* key, int64_t 
     out[4 * i + 3] = r.w;
 }
 
-template <typename T, int ACC, bool DEBUG>
+template <typename T, int ACC, bool DEBUG, bool BATCH>
 const void* mc_kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG>);
+    return reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG, BATCH>);
 }
 
 template <typename T>
-const void* select_mc(int acc_mode, bool debug)
+const void* select_mc(int acc_mode, bool debug, bool batch)
 {
-    if (debug) return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, true>()
-                                              : mc_kernel_ptr<T, kAcc64, true>();
-    return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false>()
-                                   : mc_kernel_ptr<T, kAcc64, false>();
+    if (batch) return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false, true>()
+                                              : mc_kernel_ptr<T, kAcc64, false, true>();
+    if (debug) return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, true, false>()
+                                              : mc_kernel_ptr<T, kAcc64, true, false>();
+    return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false, false>()
+                                   : mc_kernel_ptr<T, kAcc64, false, false>();
 }
 
 }  // namespace
 
 template <typename T>
-cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, int grid, cudaStream_t s)
+cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s)
 {
-    if (debug) {
-        if (acc_mode == kAccKahan32) mc_kernel<T, kAccKahan32, true><<<grid, kMcThreads, 0, s>>>(P);
-        else mc_kernel<T, kAcc64, true><<<grid, kMcThreads, 0, s>>>(P);
+    const bool kahan = acc_mode == kAccKahan32;
+    if (batch) {
+        if (kahan) mc_kernel<T, kAccKahan32, false, true><<<grid, kMcThreads, 0, s>>>(P);
+        else mc_kernel<T, kAcc64, false, true><<<grid, kMcThreads, 0, s>>>(P);
+    } else if (debug) {
+        if (kahan) mc_kernel<T, kAccKahan32, true, false><<<grid, kMcThreads, 0, s>>>(P);
+        else mc_kernel<T, kAcc64, true, false><<<grid, kMcThreads, 0, s>>>(P);
     } else {
-        if (acc_mode == kAccKahan32) mc_kernel<T, kAccKahan32, false><<<grid, kMcThreads, 0, s>>>(P);
-        else mc_kernel<T, kAcc64, false><<<grid, kMcThreads, 0, s>>>(P);
+        if (kahan) mc_kernel<T, kAccKahan32, false, false><<<grid, kMcThreads, 0, s>>>(P);
+        else mc_kernel<T, kAcc64, false, false><<<grid, kMcThreads, 0, s>>>(P);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-int mc_max_blocks_per_sm(int acc_mode, bool debug)
+int mc_max_blocks_per_sm(int acc_mode, bool debug, bool batch)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_mc<T>(acc_mode, debug), kMcThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_mc<T>(acc_mode, debug, batch), kMcThreads,
                                                       0) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
-template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, int, cudaStream_t);
-template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, int, cudaStream_t);
-template int mc_max_blocks_per_sm<float>(int, bool);
-template int mc_max_blocks_per_sm<double>(int, bool);
+template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, bool, int, cudaStream_t);
+template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, bool, int, cudaStream_t);
+template int mc_max_blocks_per_sm<float>(int, bool, bool);
+template int mc_max_blocks_per_sm<double>(int, bool, bool);
 
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
                            int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s)

@@ -150,19 +150,22 @@ sdd_status run(const sdd_params* P, const Buffers& b, int M, int acc_mode, int32
         return SDD_ERR_CUDA;
     }
     McParams<T> mp{};
-    mp.mon = static_cast<const Mon4<T>*>(b.mon);
-    mp.disp = static_cast<const Disp2<T>*>(b.disp);
-    mp.nodes = b.nodes; mp.shift = b.shift;
+    McProblem<T>& R = mp.prob;
+    R.mon = static_cast<const Mon4<T>*>(b.mon);
+    R.disp = static_cast<const Disp2<T>*>(b.disp);
+    R.nodes = b.nodes;
+    R.nx = P->nx; R.ny = P->ny; R.periodic = P->periodic; R.form = P->form; R.K = P->substeps;
+    R.bicubic = P->bicubic; R.bb = P->bb_test;
+    const T ds = (T)P->dt / (T)P->substeps;
+    R.cb = ds / (T)P->tau;
+    R.Lx = (T)P->Lx; R.Ly = (T)P->Ly;
+    R.key0 = (uint32_t)(P->seed & 0xFFFFFFFFu);
+    R.key1 = (uint32_t)(P->seed >> 32);
+    R.tstep = (uint32_t)step_index;
+    R.node_offset = 0;
+    mp.shift = b.shift;
     mp.node_of = b.node_of; mp.p_begin = b.p_begin; mp.p_count = b.p_count; mp.task_off = b.task_off;
     mp.n_active = b.n_active; mp.task_counter = b.task_counter; mp.slots = b.slots;
-    mp.nx = P->nx; mp.ny = P->ny; mp.periodic = P->periodic; mp.form = P->form; mp.K = P->substeps;
-    mp.bicubic = P->bicubic; mp.bb = P->bb_test;
-    const T ds = (T)P->dt / (T)P->substeps;
-    mp.cb = ds / (T)P->tau;
-    mp.Lx = (T)P->Lx; mp.Ly = (T)P->Ly;
-    mp.key0 = (uint32_t)(P->seed & 0xFFFFFFFFu);
-    mp.key1 = (uint32_t)(P->seed >> 32);
-    mp.tstep = (uint32_t)step_index;
 
     PlanParams pp{};
     pp.M = M; pp.n_done = b.n_done; pp.next_total = b.next_total; pp.node_of = b.node_of;
@@ -174,14 +177,14 @@ sdd_status run(const sdd_params* P, const Buffers& b, int M, int acc_mode, int32
     rp.paths_run = b.paths_run; rp.next_total = b.next_total; rp.se_target = 0.0;
     rp.max_paths = P->paths_per_node;
 
-    const int grid = nsm * mc_max_blocks_per_sm<T>(acc_mode, false);
+    const int grid = nsm * mc_max_blocks_per_sm<T>(acc_mode, false, false);
     const int64_t rounds = (P->paths_per_node + kMaxChunk - 1) / kMaxChunk;
     if (launch_mc_init(M, P->paths_per_node, P->paths_per_node, b.acc, b.n_done, b.steps, b.paths_run,
                        b.next_total, s) != cudaSuccess)
         return SDD_ERR_CUDA;
     for (int64_t r = 0; r < rounds; ++r) {
         if (launch_plan(pp, s) != cudaSuccess) return SDD_ERR_CUDA;
-        if (launch_mc<T>(mp, acc_mode, false, grid, s) != cudaSuccess) return SDD_ERR_CUDA;
+        if (launch_mc<T>(mp, acc_mode, false, false, grid, s) != cudaSuccess) return SDD_ERR_CUDA;
         if (launch_reduce(rp, M, s) != cudaSuccess) return SDD_ERR_CUDA;
     }
     return SDD_OK;
@@ -198,7 +201,8 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
         return SDD_ERR_INVALID_ARG;
     if ((P->periodic != 0 && P->periodic != 1) || (P->form != SDD_FORM_DIV && P->form != SDD_FORM_WINSLOW) ||
         P->precision < SDD_FP64 || P->precision > SDD_FP32_KAHAN || (P->bicubic != 0 && P->bicubic != 1) ||
-        (P->bb_test != 0 && P->bb_test != 1) || P->substeps < 1 || P->reserved0 != 0)
+        (P->bb_test != 0 && P->bb_test != 1) || P->substeps < 1 || P->substeps > (1 << 20) ||
+        P->reserved0 != 0)
         return SDD_ERR_INVALID_ARG;
     if (!(P->Lx > 0) || !(P->Ly > 0) || !(P->tau > 0) || !(P->dt > 0) || P->se_target != 0.0 ||
         P->paths_per_node < 2 || P->paths_per_node > (int64_t(1) << 31))

@@ -29,7 +29,7 @@ __device__ __forceinline__ double min_image(double d, double L, int periodic)
     return periodic ? d - L * floor(d / L + 0.5) : d;
 }
 
-__device__ double monitor_value(const PrepParams& P, double x, double y)
+__device__ double monitor_value(const PrepParams& P, double x, double y, double t)
 {
     const double* q = P.params;
     if (P.kind == kMonGauss) {
@@ -41,7 +41,7 @@ __device__ double monitor_value(const PrepParams& P, double x, double y)
         const double dx = min_image(x - q[4], P.Lx, P.periodic);
         const double dy = min_image(y - q[5], P.Ly, P.periodic);
         const double r = sqrt(dx * dx + dy * dy);
-        const double u = tanh(q[1] * (r - q[2] - q[3] * P.t));
+        const double u = tanh(q[1] * (r - q[2] - q[3] * t));
         const double g = q[1] * (1.0 - u * u);      // |grad u|
         return sqrt(1.0 + q[0] * g * g);
     }
@@ -57,12 +57,13 @@ __device__ double monitor_value(const PrepParams& P, double x, double y)
 __global__ void prep_omega_kernel(const PrepParams P)
 {
     const int n = P.nx * P.ny;
+    const double t = P.t_dev ? *P.t_dev : P.t;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
         const int i = id % P.nx, j = id / P.nx;
         const int ci = P.periodic ? i % (P.nx - 1) : i;
         const int cj = P.periodic ? j % (P.ny - 1) : j;
         const int c = cj * P.nx + ci;
-        P.om64[id] = P.kind == 0 ? P.omega_in[c] : monitor_value(P, P.x[c], P.y[c]);
+        P.om64[id] = P.kind == 0 ? P.omega_in[c] : monitor_value(P, P.x[c], P.y[c], t);
     }
 }
 

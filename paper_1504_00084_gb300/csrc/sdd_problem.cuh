@@ -1,0 +1,94 @@
+// Host-side state of one SDD problem (internal; shared by the C-ABI translation units).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "sdd.h"
+#include "sdd_internal.cuh"
+
+struct sdd_problem {
+    sdd_params prm{};
+    cudaStream_t stream = nullptr;
+    int M = 0;
+    std::vector<int32_t> ij;
+    int mc_grid = 1;
+    bool fp64 = true;
+    int acc_mode = sdd::kAcc64;
+    int64_t step = 0;
+    bool have_est = false;
+    // monitor
+    int mon_kind = 0;
+    int n_params = 0;
+    double mon_params[64] = {0};
+    // device: mesh and monitor
+    double *x = nullptr, *y = nullptr, *xn = nullptr, *yn = nullptr;
+    double *om64 = nullptr, *wxi64 = nullptr, *weta64 = nullptr, *omega_nodal = nullptr;
+    void *mon = nullptr, *disp = nullptr;
+    int2* nodes = nullptr;
+    double* shift = nullptr;
+    // device: interface MC
+    double* acc = nullptr;
+    int64_t *n_done = nullptr, *steps = nullptr, *paths_run = nullptr, *next_total = nullptr;
+    int32_t* node_of = nullptr;
+    int64_t *p_begin = nullptr, *p_count = nullptr, *task_off = nullptr;
+    int32_t *n_active = nullptr, *task_counter = nullptr;
+    sdd::TaskSlot* slots = nullptr;
+    int64_t slot_cap = 0;
+    double *est = nullptr, *se = nullptr;
+    // device: solves
+    double *ce64 = nullptr, *cn64 = nullptr;
+    void *ce = nullptr, *cn = nullptr, *vec = nullptr;
+    int32_t *st_iters = nullptr, *st_outer = nullptr, *st_ok = nullptr;
+    double* st_res = nullptr;
+    // host
+    int32_t* h_n_active = nullptr;  // pinned
+    sdd_stats stats{};
+    std::vector<void*> allocs;
+    std::vector<cudaEvent_t> ev;  // start/stop pairs around path-kernel launches
+    int64_t launches = 0;         // kernels launched since creation
+
+    template <typename P>
+    cudaError_t dalloc(P** p, size_t bytes)
+    {
+        void* v = nullptr;
+        cudaError_t e = cudaMalloc(&v, bytes < 16 ? 16 : bytes);
+        if (e == cudaSuccess) {
+            allocs.push_back(v);
+            *p = static_cast<P*>(v);
+        }
+        return e;
+    }
+    ~sdd_problem()
+    {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (void* v : allocs) cudaFree(v);
+        if (h_n_active) cudaFreeHost(h_n_active);
+    }
+};
+
+// Sets the calling thread's sdd_last_error message and returns s.
+sdd_status sdd_fail(sdd_status s, const char* msg);
+
+// Path-kernel record of a problem at its current step.
+template <typename T>
+inline sdd::McProblem<T> mc_problem(const sdd_problem* p)
+{
+    sdd::McProblem<T> R{};
+    R.mon = static_cast<const sdd::Mon4<T>*>(p->mon);
+    R.disp = static_cast<const sdd::Disp2<T>*>(p->disp);
+    R.nodes = p->nodes;
+    R.nx = p->prm.nx; R.ny = p->prm.ny; R.periodic = p->prm.periodic; R.form = p->prm.form;
+    R.K = p->prm.substeps; R.bicubic = p->prm.bicubic; R.bb = p->prm.bb_test;
+    const T ds = (T)p->prm.dt / (T)p->prm.substeps;
+    R.cb = ds / (T)p->prm.tau;
+    R.Lx = (T)p->prm.Lx; R.Ly = (T)p->prm.Ly;
+    R.key0 = (uint32_t)(p->prm.seed & 0xFFFFFFFFu);
+    R.key1 = (uint32_t)(p->prm.seed >> 32);
+    R.tstep = (uint32_t)p->step;
+    R.node_offset = 0;
+    return R;
+}
+

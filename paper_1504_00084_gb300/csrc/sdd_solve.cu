@@ -81,13 +81,13 @@ __global__ void faces_kernel(const SolveParams P, int inner_fp64)
     }
 }
 
+// Subdomain `sub` of the problem described by P, solved by the calling CTA.
 template <typename TI>
-__global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_constant__ SolveParams P)
+__device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double* sh)
 {
-    __shared__ double sh[32 * 8 + 8];
     const int nx = P.nx, ny = P.ny;
     const int sx = (nx - 1) / P.px, sy = (ny - 1) / P.py;
-    const int I = blockIdx.x % P.px, J = blockIdx.x / P.px;
+    const int I = sub % P.px, J = sub / P.px;
     const int i0 = I * sx, j0 = J * sy;
     const int ni = sx - 1, nj = sy - 1;
     const int nint = ni * nj;
@@ -244,14 +244,60 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_const
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        P.stat_iters[blockIdx.x] = iters;
-        P.stat_outer[blockIdx.x] = outer;
-        P.stat_ok[blockIdx.x] = ok;
-        P.stat_res[blockIdx.x] = rel;
+        P.stat_iters[sub] = iters;
+        P.stat_outer[sub] = outer;
+        P.stat_ok[sub] = ok;
+        P.stat_res[sub] = rel;
     }
 }
 
+template <typename TI>
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_constant__ SolveParams P)
+{
+    __shared__ double sh[32 * 8 + 8];
+    solve_body<TI>(P, blockIdx.x, sh);
+}
+
+// Batched: CTA b solves subdomain b - sub_off[p] of problem p, sub_off[p] <= b < sub_off[p + 1].
+template <typename TI>
+__global__ void __launch_bounds__(kSolveThreads) solve_batch_kernel(const SolveParams* probs,
+                                                                    const int32_t* sub_off, int n)
+{
+    __shared__ double sh[32 * 8 + 8];
+    __shared__ SolveParams sp;
+    __shared__ int sub;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sub_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        sp = probs[lo];
+        sub = (int)blockIdx.x - sub_off[lo];
+    }
+    __syncthreads();
+    solve_body<TI>(sp, sub, sh);
+}
+
 }  // namespace
+
+cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s)
+{
+    const long n = (long)P.nx * P.ny;
+    faces_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(P, fp64_inner ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
+                               bool fp64_inner, cudaStream_t s)
+{
+    if (total_subs <= 0) return cudaSuccess;
+    if (fp64_inner)
+        solve_batch_kernel<double><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+    else
+        solve_batch_kernel<float><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s)
 {
