@@ -38,6 +38,10 @@ OPS_PER_PATH_STEP = 230
 SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_PEAK_OPS = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6  # lane-ops/s
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of one path-kernel launch on this grid, from an ncu
+# capture of the current kernel: the cold fill of the packed monitor and mesh records (~1.6 MB
+# of FP32 data per 257x257 grid), which does not grow with the number of paths.
+MC_TRAFFIC_BYTES_PER_LAUNCH = 1.28e6
 
 
 def parse():
@@ -58,6 +62,8 @@ def parse():
                     help="front: the 257x257 / 4x4 moving-front problem (the benchmark line); "
                          "mix: the batch of 64 uneven problems, batched vs one at a time")
     ap.add_argument("--mix-n", type=int, default=64)
+    ap.add_argument("--mix-batched-only", action="store_true",
+                    help="mix: skip the one-at-a-time comparisons (profiling case)")
     ap.add_argument("--mc-only", type=int, default=0,
                     help="profiling case: run `steps` interface-MC calls at this fixed N per node and "
                          "print the library's counters (not a benchmark line)")
@@ -317,7 +323,8 @@ def run_ours(args):
            "gpu_launches": int(launches),
            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK_OPS / 1e12,
                         "unit": "Tops/s (32-bit lane ops)", "frac": achieved / ALU_PEAK_OPS,
-                        "traffic": None, "kernel": "mc_kernel<float>",
+                        "traffic": MC_TRAFFIC_BYTES_PER_LAUNCH if args.precision == "kahan" else None,
+                        "traffic_unit": "bytes per launch", "kernel": "mc_kernel<float>",
                         "ops_per_path_step": OPS_PER_PATH_STEP,
                         "kernel_ms": mc_ms, "kernel_launches": mc_launches,
                         "kernel_share_of_step": (mc_ms / 1e3) / T if T > 0 else None,
@@ -394,8 +401,15 @@ def run_mix(args):
     st = b.stats()
     T = e0.elapsed_time(e1) / 1e3
     batch = {"s_per_step": T / args.steps, "interface_node_estimates_per_s": M * args.steps / T,
-             "path_steps_last_step": st["path_steps"], "launches_per_step": (st["kernel_launches"] - l0) / args.steps}
+             "path_steps_last_step": st["path_steps"], "launches_per_step": (st["kernel_launches"] - l0) / args.steps,
+             "solve_iters_max": st["solve_iters_max"], "solve_outer_max": st["solve_outer_max"],
+             "solve_rel_residual": st["solve_rel_residual"]}
     b.close()
+    if args.mix_batched_only:
+        for h in hs:
+            h.close()
+        print(json.dumps({"workload": "mix", "interface_nodes": M, "batched_fp32_graph": batch}))
+        return 0
 
     def one_at_a_time(handles, steps):
         for h in handles:

@@ -64,7 +64,9 @@ enum {
     SDD_MONITOR_GAUSS = 1, /* sqrt(1 + a exp(-b |x - c|^2)); params a, b, cx, cy                */
     SDD_MONITOR_FRONT = 2, /* sqrt(1 + alpha |grad u|^2), u = tanh(R (|x - c| - r0 - v t));
                               params alpha, R, r0, v, cx, cy (the arc-length monitor, Sec. 1)   */
-    SDD_MONITOR_BUMPS = 3  /* 1 + sum_k a_k exp(-|x - c_k|^2 / w_k^2); params (a, w, cx, cy)*   */
+    SDD_MONITOR_BUMPS = 3, /* 1 + sum_k a_k exp(-|x - c_k|^2 / w_k^2); params (a, w, cx, cy)*   */
+    SDD_MONITOR_RINGS = 4  /* sqrt(1 + alpha |grad u|^2), u = sum_k tanh(R (|x - c_k|^2 - r2));
+                              params alpha, R, r2, (cx, cy)* (the five-ring problem, Sec. 4.2)  */
 };
 
 typedef struct {
@@ -137,7 +139,8 @@ sdd_status sdd_set_monitor(sdd_problem* p, const double* omega);
 
 /* Analytic monitor re-evaluated on the current mesh at t^n before each MC call and step
  * (the MP procedure: omega from u^n on x^n, Sec. 2 and Sec. 3.6).  Periodic problems use
- * the minimum-image offset x - c.  n_params: 4 (GAUSS), 6 (FRONT), 4k with k <= 16 (BUMPS). */
+ * the minimum-image offset x - c.  n_params: 4 (GAUSS), 6 (FRONT), 4k with k <= 16 (BUMPS),
+ * 3 + 2k with 1 <= k <= 30 (RINGS). */
 sdd_status sdd_set_monitor_analytic(sdd_problem* p, int32_t kind, const double* params,
                                     int32_t n_params);
 
@@ -177,6 +180,12 @@ sdd_status sdd_interface_layout(int32_t nx, int32_t ny, int32_t px, int32_t py, 
  * (max of both components): n_done when se <= target or n_done >= max_paths, else
  * min(max_paths, max(n_done + 1024, 1024 ceil(1.1 n_done (se/target)^2 / 1024))). */
 int64_t sdd_adaptive_next_total(int64_t n_done, double se, double target, int64_t max_paths);
+
+/* Geometric mesh quality of the current mesh (Eq. 8): per cell Q = tr(J^T J) / (2 |det J|),
+ * J from the mean of the cell's two xi-edges and two eta-edges, Q >= 1 with equality for a
+ * square cell (Sec. 3.7).  q_cells: (nx-1)*(ny-1) doubles, row-major (nullable); *q_max and
+ * *q_mean (nullable): the maximum and mean over the cells.  Returns when written. */
+sdd_status sdd_mesh_quality(sdd_problem* p, double* q_cells, double* q_max, double* q_mean);
 
 /* Test hook: the monitor as frozen for the next MC call (nx*ny each, FP64, nullable):
  * omega and its finite-difference gradient (Sec. 3.4). */

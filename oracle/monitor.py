@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from workloads import MONITOR_BUMPS, MONITOR_FRONT, MONITOR_GAUSS, MONITOR_NODAL
+from workloads import MONITOR_BUMPS, MONITOR_FRONT, MONITOR_GAUSS, MONITOR_NODAL, MONITOR_RINGS
 
 
 def _offsets(x, y, cx, cy, periodic, Lx, Ly):
@@ -29,6 +29,9 @@ def analytic_monitor(kind, params, x, y, t, periodic=0, Lx=1.0, Ly=1.0):
                                        r = |x - c|, so |grad u| = R (1 - u^2)  (the arc-length
                                        monitor of Sec. 1 / Sec. 4.1 for an analytic u)
     BUMPS  (a_1, w_1, cx_1, cy_1, ...): 1 + sum_i a_i exp(-|x - c_i|^2 / w_i^2)
+    RINGS  (alpha, R, r2, cx_1, cy_1, ...): sqrt(1 + alpha |grad u|^2) with
+                                       u = sum_k tanh(R (|x - c_k|^2 - r2))  (the five-ring
+                                       problem of Sec. 4.2), grad u = sum_k R (1 - u_k^2) 2 (x - c_k)
     """
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
@@ -50,6 +53,17 @@ def analytic_monitor(kind, params, x, y, t, periodic=0, Lx=1.0, Ly=1.0):
             a, w, cx, cy = params[4 * q:4 * q + 4]
             dx, dy = _offsets(x, y, cx, cy, periodic, Lx, Ly)
             om = om + a * np.exp(-(dx * dx + dy * dy) / (w * w))
+    elif kind == MONITOR_RINGS:
+        alpha, R, r2 = params[:3]
+        gx = np.zeros_like(x)
+        gy = np.zeros_like(x)
+        for q in range(3, len(params) - 1, 2):
+            dx, dy = _offsets(x, y, params[q], params[q + 1], periodic, Lx, Ly)
+            uk = np.tanh(R * (dx * dx + dy * dy - r2))
+            f = R * (1.0 - uk * uk) * 2.0
+            gx = gx + f * dx
+            gy = gy + f * dy
+        om = np.sqrt(1.0 + alpha * (gx * gx + gy * gy))
     else:
         raise ValueError(f"unknown analytic monitor kind {kind}")
     return om

@@ -97,3 +97,50 @@ def single_domain_step(omega, xn, yn, dt, tau, form, Lx=1.0, Ly=1.0):
         out_x[j, i] = xs[P]
         out_y[j, i] = ys[P]
     return out_x, out_y
+
+
+def periodic_single_domain_step(omega, xn, yn, dt, tau, form, Lx=1.0, Ly=1.0):
+    """One backward-Euler step on the whole doubly periodic domain (no interfaces): the
+    single-domain reference of the paper's periodic experiments (Sec. 4.2, Sec. 3.7).
+
+    Unknowns are the (nx-1) x (ny-1) distinct nodes; a neighbour across the seam i = nx-1 is
+    node 0 with x shifted by Lx (likewise y and Ly across j = ny-1), the direct-coordinate
+    extension of Sec. 2.  Returns full-grid arrays including the wrap column and row."""
+    ny, nx = omega.shape
+    mx, my = nx - 1, ny - 1
+    hx2 = float(nx - 1) ** 2
+    hy2 = float(ny - 1) ** 2
+    r = dt / tau
+    n = mx * my
+    idx = lambda i, j: (j % my) * mx + (i % mx)
+    rows, cols, vals = [], [], []
+    bx = np.zeros(n)
+    by = np.zeros(n)
+    for j in range(my):
+        for i in range(mx):
+            P = idx(i, j)
+            wP = omega[j, i]
+            d = wP if form == 1 else 1.0
+            bx[P] = d * xn[j, i]
+            by[P] = d * yn[j, i]
+            diag = d
+            for (di, dj, h2) in ((1, 0, hx2), (-1, 0, hx2), (0, 1, hy2), (0, -1, hy2)):
+                ii, jj = i + di, j + dj
+                a = r * 0.5 * (wP + omega[jj % my, ii % mx]) * h2
+                diag += a
+                rows.append(P); cols.append(idx(ii, jj)); vals.append(-a)
+                # period offsets of the neighbour's coordinates across the seams
+                bx[P] += a * Lx * (ii // mx)
+                by[P] += a * Ly * (jj // my)
+            rows.append(P); cols.append(P); vals.append(diag)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n)).tocsc()
+    lu = spla.splu(A)
+    sx, sy = lu.solve(bx), lu.solve(by)
+    out_x = np.empty((ny, nx))
+    out_y = np.empty((ny, nx))
+    for j in range(ny):
+        for i in range(nx):
+            P = idx(i, j)
+            out_x[j, i] = sx[P] + Lx * (i // mx)
+            out_y[j, i] = sy[P] + Ly * (j // my)
+    return out_x, out_y

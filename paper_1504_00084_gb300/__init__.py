@@ -27,7 +27,7 @@ SDD_ERR_NO_DEVICE = 6
 
 SDD_FORM_DIV, SDD_FORM_WINSLOW = 0, 1
 SDD_FP64, SDD_FP32_ACC64, SDD_FP32_KAHAN = 0, 1, 2
-SDD_MONITOR_NODAL, SDD_MONITOR_GAUSS, SDD_MONITOR_FRONT, SDD_MONITOR_BUMPS = 0, 1, 2, 3
+SDD_MONITOR_NODAL, SDD_MONITOR_GAUSS, SDD_MONITOR_FRONT, SDD_MONITOR_BUMPS, SDD_MONITOR_RINGS = 0, 1, 2, 3, 4
 
 
 class SddParams(ctypes.Structure):
@@ -61,6 +61,7 @@ EXPORTS = [
     "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
     "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
     "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy",
+    "sdd_mesh_quality",
 ]
 
 
@@ -93,6 +94,7 @@ def _load():
         "sdd_batch_step": ([P], I32),
         "sdd_batch_get_stats": ([P, ctypes.POINTER(SddStats)], I32),
         "sdd_batch_destroy": ([P], None),
+        "sdd_mesh_quality": ([P, P, ctypes.POINTER(F64), ctypes.POINTER(F64)], I32),
         "sdd_status_string": ([I32], ctypes.c_char_p),
         "sdd_last_error": ([], ctypes.c_char_p),
     }
@@ -322,6 +324,14 @@ class SddProblem:
         y = np.zeros((self.ny, self.nx))
         sdd_get_mesh(self.h, x, y)
         return x, y
+
+    def quality(self):
+        """Per-cell geometric quality Q (Eq. 8), its maximum and mean, on the current mesh."""
+        q = np.zeros((self.ny - 1, self.nx - 1))
+        qmax, qmean = ctypes.c_double(), ctypes.c_double()
+        _check(lib.sdd_mesh_quality(self.h, q.ctypes.data, ctypes.byref(qmax), ctypes.byref(qmean)),
+               "sdd_mesh_quality")
+        return q, qmax.value, qmean.value
 
     def monitor(self):
         w, a, b = (np.zeros((self.ny, self.nx)) for _ in range(3))

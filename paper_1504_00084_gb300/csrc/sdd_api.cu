@@ -312,6 +312,7 @@ sdd_status run_solve(sdd_problem* p)
     S.r = p->prm.dt / p->prm.tau; S.rtol = p->prm.solve_rtol; S.max_iter = p->prm.solve_max_iter;
     S.om64 = p->om64; S.xcur = p->x; S.ycur = p->y; S.xnew = p->xn; S.ynew = p->yn;
     S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
+    S.mg = p->mg; S.mg_stride = p->mg_stride;
     S.stat_iters = p->st_iters; S.stat_outer = p->st_outer; S.stat_ok = p->st_ok; S.stat_res = p->st_res;
     SDD_CK(launch_solve(S, p->fp64, p->stream));
     p->launches += 2;
@@ -418,6 +419,9 @@ sdd_status sdd_create_problem(const sdd_params* params, const double* x0, const 
     ALLOC(p->vec, N * 4 * 2 * rs);
     const int ns = params->px * params->py;
     ALLOC(p->st_iters, ns * 4); ALLOC(p->st_outer, ns * 4); ALLOC(p->st_ok, ns * 4); ALLOC(p->st_res, ns * 8);
+    ALLOC(p->quality, (N + 2) * 8);
+    p->mg_stride = mg_bytes((params->nx - 1) / params->px - 1, (params->ny - 1) / params->py - 1, rs);
+    ALLOC(p->mg, p->mg_stride * ns);
 #undef ALLOC
     if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_n_active, 16, cudaHostAllocDefault);
     if (e != cudaSuccess) {
@@ -508,7 +512,9 @@ sdd_status sdd_set_monitor_analytic(sdd_problem* p, int32_t kind, const double* 
     if (kind == SDD_MONITOR_FRONT && n_params != 6) return fail(SDD_ERR_INVALID_ARG, "FRONT needs 6 params");
     if (kind == SDD_MONITOR_BUMPS && (n_params % 4 || n_params < 0 || n_params > 64))
         return fail(SDD_ERR_INVALID_ARG, "BUMPS needs 4k params, k <= 16");
-    if (kind < SDD_MONITOR_GAUSS || kind > SDD_MONITOR_BUMPS) return fail(SDD_ERR_INVALID_ARG, "bad monitor kind");
+    if (kind == SDD_MONITOR_RINGS && (n_params < 5 || (n_params - 3) % 2 || n_params > 63))
+        return fail(SDD_ERR_INVALID_ARG, "RINGS needs 3 + 2k params, 1 <= k <= 30");
+    if (kind < SDD_MONITOR_GAUSS || kind > SDD_MONITOR_RINGS) return fail(SDD_ERR_INVALID_ARG, "bad monitor kind");
     if (n_params > 0 && !params) return fail(SDD_ERR_INVALID_ARG, "params is NULL");
     p->mon_kind = kind;
     p->n_params = n_params;
@@ -597,6 +603,22 @@ sdd_status sdd_get_monitor(sdd_problem* p, double* omega, double* w_xi, double* 
     SDD_TRY(copy_out(p, w_xi, p->wxi64, N * 8));
     SDD_TRY(copy_out(p, w_eta, p->weta64, N * 8));
     SDD_CK(cudaStreamSynchronize(p->stream));
+    return SDD_OK;
+}
+
+sdd_status sdd_mesh_quality(sdd_problem* p, double* q_cells, double* q_max, double* q_mean)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    const int nx = p->prm.nx, ny = p->prm.ny;
+    const size_t nc = (size_t)(nx - 1) * (ny - 1);
+    SDD_CK(launch_quality(nx, ny, p->x, p->y, p->quality, p->quality + nc, p->stream));
+    p->launches += 2;
+    double st[2] = {0.0, 0.0};
+    SDD_TRY(copy_out(p, q_cells, p->quality, nc * 8));
+    SDD_CK(cudaMemcpyAsync(st, p->quality + nc, 16, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    if (q_max) *q_max = st[0];
+    if (q_mean) *q_mean = st[1];
     return SDD_OK;
 }
 

@@ -167,14 +167,45 @@ struct SolveParams {
     void* ce;                  // the same in the inner precision
     void* cn;
     void* vec;                 // inner vectors: 4 x nx*ny pairs (e, r, p, q), rims zero
+    void* mg;                  // multigrid workspace: mg_stride bytes per subdomain
+    size_t mg_stride;
     int32_t* stat_iters;       // per subdomain: PCG iterations, refinement sweeps, converged
     int32_t* stat_outer;
     int32_t* stat_ok;
     double* stat_res;          // per subdomain: final relative residual (max of x, y)
 };
 
+// Multigrid hierarchy of an n x m subdomain interior: levels while both sizes stay odd and
+// >= 3 (n -> (n-1)/2), and the bytes of its per-level arrays (x, b, t pairs; faces; identity).
+__host__ __device__ inline int mg_levels(int n, int m)
+{
+    int l = 1;
+    while (n >= 3 && m >= 3 && (n & 1) && (m & 1) && l < 16) {
+        n = (n - 1) / 2;
+        m = (m - 1) / 2;
+        ++l;
+    }
+    return l;
+}
+__host__ __device__ inline size_t mg_align(size_t b) { return (b + 255) / 256 * 256; }
+__host__ __device__ inline size_t mg_bytes(int n, int m, size_t real_bytes)
+{
+    const int L = mg_levels(n, m);
+    size_t total = 0;
+    for (int l = 0; l < L; ++l) {
+        const size_t nn = (size_t)n * m;
+        total += 3 * mg_align(nn * 2 * real_bytes) + mg_align((size_t)(n + 1) * m * real_bytes) +
+                 mg_align((size_t)n * (m + 1) * real_bytes) + mg_align(nn * real_bytes);
+        n = (n - 1) / 2;
+        m = (m - 1) / 2;
+    }
+    return total;
+}
+
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t s);
+cudaError_t launch_quality(int nx, int ny, const double* x, const double* y, double* q, double* stats,
+                           cudaStream_t s);
 cudaError_t launch_shift(const int2* nodes, int M, int nx, const double* x, const double* y,
                          double* shift, cudaStream_t s);
 cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, const int2* nodes,

@@ -22,7 +22,7 @@ namespace sdd {
 
 namespace {
 
-constexpr int kMonGauss = 1, kMonFront = 2;  // otherwise bumps (3) or nodal (0)
+constexpr int kMonGauss = 1, kMonFront = 2, kMonRings = 4;  // otherwise bumps (3) or nodal (0)
 
 __device__ __forceinline__ double min_image(double d, double L, int periodic)
 {
@@ -44,6 +44,18 @@ __device__ double monitor_value(const PrepParams& P, double x, double y, double 
         const double u = tanh(q[1] * (r - q[2] - q[3] * t));
         const double g = q[1] * (1.0 - u * u);      // |grad u|
         return sqrt(1.0 + q[0] * g * g);
+    }
+    if (P.kind == kMonRings) {                       // sum of tanh rings (five-ring problem)
+        double gx = 0.0, gy = 0.0;
+        for (int b = 3; b + 1 < P.n_params; b += 2) {
+            const double dx = min_image(x - q[b], P.Lx, P.periodic);
+            const double dy = min_image(y - q[b + 1], P.Ly, P.periodic);
+            const double uk = tanh(q[1] * (dx * dx + dy * dy - q[2]));
+            const double f = q[1] * (1.0 - uk * uk) * 2.0;
+            gx += f * dx;
+            gy += f * dy;
+        }
+        return sqrt(1.0 + q[0] * (gx * gx + gy * gy));
     }
     double w = 1.0;                                  // bumps
     for (int b = 0; b + 3 < P.n_params; b += 4) {
@@ -165,6 +177,45 @@ __global__ void scatter_iface_kernel(int nx, int ny, int periodic, double Lx, do
     }
 }
 
+// Geometric quality Q = tr(J^T J) / (2 |det J|) of every cell (Eq. 8), J from the mean of the
+// cell's two xi-edges and two eta-edges; then the maximum and mean over the cells.
+__global__ void quality_kernel(int nx, int ny, const double* x, const double* y, double* q)
+{
+    const long nc = (long)(nx - 1) * (ny - 1);
+    for (long c = blockIdx.x * (long)blockDim.x + threadIdx.x; c < nc; c += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(c % (nx - 1)), j = (int)(c / (nx - 1));
+        const long a = (long)j * nx + i, b = a + 1, d = a + nx, e = d + 1;
+        const double x_xi = 0.5 * ((x[b] - x[a]) + (x[e] - x[d]));
+        const double y_xi = 0.5 * ((y[b] - y[a]) + (y[e] - y[d]));
+        const double x_eta = 0.5 * ((x[d] - x[a]) + (x[e] - x[b]));
+        const double y_eta = 0.5 * ((y[d] - y[a]) + (y[e] - y[b]));
+        const double tr = x_xi * x_xi + y_xi * y_xi + x_eta * x_eta + y_eta * y_eta;
+        q[c] = 0.5 * tr / fabs(x_xi * y_eta - x_eta * y_xi);
+    }
+}
+
+__global__ void max_mean_kernel(long n, const double* v, double* out)
+{
+    __shared__ double smax[32], ssum[32];
+    double m = -INFINITY, s = 0.0;
+    for (long k = threadIdx.x; k < n; k += blockDim.x) {
+        m = fmax(m, v[k]);
+        s += v[k];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { smax[w] = m; ssum[w] = s; }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // holds warp 0's totals; add the other warps in order
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) { m = fmax(m, smax[k]); s += ssum[k]; }
+        out[0] = m;
+        out[1] = s / (double)n;
+    }
+}
+
 inline int blocks_for(long n, int threads) { return (int)((n + threads - 1) / threads); }
 
 }  // namespace
@@ -179,6 +230,15 @@ cudaError_t launch_prep(const PrepParams& P, cudaStream_t s)
         prep_pack_kernel<double><<<blocks, threads, 0, s>>>(P);
     else
         prep_pack_kernel<float><<<blocks, threads, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quality(int nx, int ny, const double* x, const double* y, double* q, double* stats,
+                           cudaStream_t s)
+{
+    const long nc = (long)(nx - 1) * (ny - 1);
+    quality_kernel<<<blocks_for(nc, 256), 256, 0, s>>>(nx, ny, x, y, q);
+    max_mean_kernel<<<1, 1024, 0, s>>>(nc, q, stats);
     return cudaGetLastError();
 }
 

@@ -41,8 +41,11 @@ struct sdd_problem {
     // device: solves
     double *ce64 = nullptr, *cn64 = nullptr;
     void *ce = nullptr, *cn = nullptr, *vec = nullptr;
+    void* mg = nullptr;             // multigrid workspace, mg_stride bytes per subdomain
+    size_t mg_stride = 0;
     int32_t *st_iters = nullptr, *st_outer = nullptr, *st_ok = nullptr;
     double* st_res = nullptr;
+    double* quality = nullptr;      // (nx-1)(ny-1) cell qualities + 2 stats
     // host
     int32_t* h_n_active = nullptr;  // pinned
     sdd_stats stats{};

@@ -9,8 +9,16 @@
 //
 // One CTA per subdomain.  Outer loop in FP64: residual b - A x of the current iterate (rims
 // included), stop when ||r||_2 <= rtol ||b||_2 for both components.  Inner solve A e = r by
-// Jacobi-preconditioned CG in the inner precision (FP32 for the FP32 modes, FP64 otherwise),
-// then x += e (iterative refinement).  Inner vectors live in full-grid arrays whose rim
+// conjugate gradients in the inner precision (FP32 for the FP32 modes, FP64 otherwise),
+// preconditioned by one symmetric multigrid V-cycle, then x += e (iterative refinement).
+//
+// Multigrid: the subdomain's interior (n x m nodes, n and m odd) coarsens to the nodes of odd
+// index, ((n-1)/2) x ((m-1)/2), for as long as both stay odd and >= 3.  Coarse face
+// coefficients are a quarter of the series combination 2ab/(a+b) of the two fine faces a
+// coarse face spans (the operator rediscretised at twice the spacing); the identity term is
+// injected.  Red-black Gauss-Seidel smoothing (red-black before, black-red after: a symmetric
+// cycle), full-weighting restriction, bilinear prolongation, symmetric Gauss-Seidel sweeps on
+// the coarsest level; zero rims on every level (the cycle acts on residual equations).  Inner vectors live in full-grid arrays whose rim
 // entries stay zero, so A p needs no rim special cases.  All reductions are fixed-order
 // block trees: the solve is deterministic.
 #include <math.h>
@@ -23,6 +31,7 @@ namespace {
 
 constexpr int kSolveThreads = 512;
 constexpr int kMaxOuter = 12;
+constexpr int kCoarseSweeps = 4;  // symmetric Gauss-Seidel sweeps on the coarsest level
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename TI> struct Pair {
@@ -81,6 +90,211 @@ __global__ void faces_kernel(const SolveParams P, int inner_fp64)
     }
 }
 
+
+// ------------------------------------------------------------------------------------------
+// Multigrid hierarchy of one subdomain: compact per-level arrays in the subdomain's workspace.
+// ------------------------------------------------------------------------------------------
+template <typename TI> struct MgLevel {
+    int nx, ny;
+    Pair<TI>* x;   // correction
+    Pair<TI>* b;   // right-hand side
+    Pair<TI>* t;   // residual
+    TI* ce;        // faces along xi: (nx + 1) per row, face f between nodes f-1 and f
+    TI* cn;        // faces along eta: (ny + 1) rows of nx
+    TI* d;         // identity term
+};
+
+template <typename TI>
+__device__ __forceinline__ MgLevel<TI> mg_level(void* base, int nx0, int ny0, int l)
+{
+    char* ptr = static_cast<char*>(base);
+    int nx = nx0, ny = ny0;
+    for (int k = 0;; ++k) {
+        MgLevel<TI> L;
+        L.nx = nx; L.ny = ny;
+        const size_t nn = (size_t)nx * ny;
+        L.x = reinterpret_cast<Pair<TI>*>(ptr); ptr += mg_align(nn * sizeof(Pair<TI>));
+        L.b = reinterpret_cast<Pair<TI>*>(ptr); ptr += mg_align(nn * sizeof(Pair<TI>));
+        L.t = reinterpret_cast<Pair<TI>*>(ptr); ptr += mg_align(nn * sizeof(Pair<TI>));
+        L.ce = reinterpret_cast<TI*>(ptr); ptr += mg_align((size_t)(nx + 1) * ny * sizeof(TI));
+        L.cn = reinterpret_cast<TI*>(ptr); ptr += mg_align((size_t)nx * (ny + 1) * sizeof(TI));
+        L.d = reinterpret_cast<TI*>(ptr); ptr += mg_align(nn * sizeof(TI));
+        if (k == l) return L;
+        nx = (nx - 1) / 2;
+        ny = (ny - 1) / 2;
+    }
+}
+
+template <typename TI>
+__device__ __forceinline__ TI mg_diag(const MgLevel<TI>& L, int i, int j)
+{
+    return L.d[j * L.nx + i] + L.ce[j * (L.nx + 1) + i] + L.ce[j * (L.nx + 1) + i + 1] +
+           L.cn[j * L.nx + i] + L.cn[(j + 1) * L.nx + i];
+}
+
+// sum over the four neighbours of c_nb * x_nb (zero outside the level's interior)
+template <typename TI>
+__device__ __forceinline__ Pair<TI> mg_offdiag(const MgLevel<TI>& L, int i, int j)
+{
+    const int nx = L.nx, ny = L.ny, id = j * nx + i;
+    Pair<TI> s{(TI)0, (TI)0};
+    if (i > 0) { const TI c = L.ce[j * (nx + 1) + i]; s.x += c * L.x[id - 1].x; s.y += c * L.x[id - 1].y; }
+    if (i < nx - 1) { const TI c = L.ce[j * (nx + 1) + i + 1]; s.x += c * L.x[id + 1].x; s.y += c * L.x[id + 1].y; }
+    if (j > 0) { const TI c = L.cn[j * nx + i]; s.x += c * L.x[id - nx].x; s.y += c * L.x[id - nx].y; }
+    if (j < ny - 1) { const TI c = L.cn[(j + 1) * nx + i]; s.x += c * L.x[id + nx].x; s.y += c * L.x[id + nx].y; }
+    return s;
+}
+
+// one Gauss-Seidel half-sweep over the nodes of one colour ((i + j) % 2 == colour)
+template <typename TI>
+__device__ __forceinline__ void mg_half_sweep(const MgLevel<TI>& L, int colour)
+{
+    const int n = L.nx * L.ny;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+        const int i = k % L.nx, j = k / L.nx;
+        if (((i + j) & 1) != colour) continue;
+        const Pair<TI> o = mg_offdiag(L, i, j);
+        const TI dg = mg_diag(L, i, j);
+        const Pair<TI> bb = L.b[k];
+        L.x[k] = Pair<TI>{(bb.x + o.x) / dg, (bb.y + o.y) / dg};
+    }
+    __syncthreads();
+}
+
+template <typename TI>
+__device__ __forceinline__ void mg_zero(const MgLevel<TI>& L)
+{
+    for (int k = threadIdx.x; k < L.nx * L.ny; k += blockDim.x) L.x[k] = Pair<TI>{(TI)0, (TI)0};
+    __syncthreads();
+}
+
+// b_{l+1} = full weighting of the residual t_l = b_l - A_l x_l
+template <typename TI>
+__device__ __forceinline__ void mg_restrict(const MgLevel<TI>& F, const MgLevel<TI>& C)
+{
+    for (int k = threadIdx.x; k < F.nx * F.ny; k += blockDim.x) {
+        const int i = k % F.nx, j = k / F.nx;
+        const Pair<TI> o = mg_offdiag(F, i, j);
+        const TI dg = mg_diag(F, i, j);
+        const Pair<TI> xv = F.x[k], bv = F.b[k];
+        F.t[k] = Pair<TI>{bv.x - (dg * xv.x - o.x), bv.y - (dg * xv.y - o.y)};
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < C.nx * C.ny; k += blockDim.x) {
+        const int I = k % C.nx, J = k / C.nx;
+        const int i = 2 * I + 1, j = 2 * J + 1;
+        Pair<TI> acc{(TI)0, (TI)0};
+#pragma unroll
+        for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll
+            for (int di = -1; di <= 1; ++di) {
+                const TI w = (TI)((di == 0 ? 2 : 1) * (dj == 0 ? 2 : 1)) * (TI)0.0625;
+                const Pair<TI> tv = F.t[(j + dj) * F.nx + (i + di)];
+                acc.x += w * tv.x;
+                acc.y += w * tv.y;
+            }
+        C.b[k] = acc;
+    }
+    __syncthreads();
+}
+
+// x_l += bilinear interpolation of x_{l+1} (coarse rims are zero)
+template <typename TI>
+__device__ __forceinline__ void mg_prolong(const MgLevel<TI>& F, const MgLevel<TI>& C)
+{
+    for (int k = threadIdx.x; k < F.nx * F.ny; k += blockDim.x) {
+        const int i = k % F.nx, j = k / F.nx;
+        // coarse neighbours: odd fine index 2I+1 -> I; even fine index 2I -> I-1 and I
+        const int Ia = (i & 1) ? (i - 1) / 2 : i / 2 - 1, Ib = (i & 1) ? Ia : i / 2;
+        const int Ja = (j & 1) ? (j - 1) / 2 : j / 2 - 1, Jb = (j & 1) ? Ja : j / 2;
+        const TI wi = (i & 1) ? (TI)1 : (TI)0.5, wj = (j & 1) ? (TI)1 : (TI)0.5;
+        Pair<TI> s{(TI)0, (TI)0};
+        const int Is[2] = {Ia, Ib}, Js[2] = {Ja, Jb};
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (((i & 1) && a == 1) || ((j & 1) && c == 1)) continue;
+                const int I = Is[a], J = Js[c];
+                if (I < 0 || I >= C.nx || J < 0 || J >= C.ny) continue;
+                const Pair<TI> v = C.x[J * C.nx + I];
+                s.x += wi * wj * v.x;
+                s.y += wi * wj * v.y;
+            }
+        F.x[k].x += s.x;
+        F.x[k].y += s.y;
+    }
+    __syncthreads();
+}
+
+// Coefficients of every level from the fine face coefficients of the subdomain.
+template <typename TI>
+__device__ void mg_setup(const SolveParams& P, int i0, int j0, int nx0, int ny0, int levels)
+{
+    const TI* ce = static_cast<const TI*>(P.ce);
+    const TI* cn = static_cast<const TI*>(P.cn);
+    const int nx = P.nx;
+    const MgLevel<TI> L0 = mg_level<TI>(P.mg, nx0, ny0, 0);
+    for (int k = threadIdx.x; k < (nx0 + 1) * ny0; k += blockDim.x) {
+        const int f = k % (nx0 + 1), j = k / (nx0 + 1);
+        L0.ce[k] = ce[(long)(j0 + 1 + j) * nx + (i0 + f)];
+    }
+    for (int k = threadIdx.x; k < nx0 * (ny0 + 1); k += blockDim.x) {
+        const int i = k % nx0, g = k / nx0;
+        L0.cn[k] = cn[(long)(j0 + g) * nx + (i0 + 1 + i)];
+    }
+    for (int k = threadIdx.x; k < nx0 * ny0; k += blockDim.x) {
+        const int i = k % nx0, j = k / nx0;
+        L0.d[k] = P.form == 0 ? (TI)1 : (TI)P.om64[(long)(j0 + 1 + j) * nx + (i0 + 1 + i)];
+    }
+    __syncthreads();
+    for (int l = 0; l + 1 < levels; ++l) {
+        const MgLevel<TI> F = mg_level<TI>(P.mg, nx0, ny0, l), C = mg_level<TI>(P.mg, nx0, ny0, l + 1);
+        for (int k = threadIdx.x; k < (C.nx + 1) * C.ny; k += blockDim.x) {
+            const int f = k % (C.nx + 1), J = k / (C.nx + 1);
+            const TI a = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f], b = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f + 1];
+            C.ce[k] = (TI)0.5 * a * b / (a + b);
+        }
+        for (int k = threadIdx.x; k < C.nx * (C.ny + 1); k += blockDim.x) {
+            const int I = k % C.nx, g = k / C.nx;
+            const TI a = F.cn[(2 * g) * F.nx + 2 * I + 1], b = F.cn[(2 * g + 1) * F.nx + 2 * I + 1];
+            C.cn[k] = (TI)0.5 * a * b / (a + b);
+        }
+        for (int k = threadIdx.x; k < C.nx * C.ny; k += blockDim.x) {
+            const int I = k % C.nx, J = k / C.nx;
+            C.d[k] = F.d[(2 * J + 1) * F.nx + 2 * I + 1];
+        }
+        __syncthreads();
+    }
+}
+
+// x_0 = V-cycle(b_0): one symmetric multigrid cycle.
+template <typename TI>
+__device__ void mg_vcycle(void* base, int nx0, int ny0, int levels)
+{
+    for (int l = 0; l + 1 < levels; ++l) {
+        const MgLevel<TI> F = mg_level<TI>(base, nx0, ny0, l);
+        mg_zero(F);
+        mg_half_sweep(F, 0);
+        mg_half_sweep(F, 1);
+        mg_restrict(F, mg_level<TI>(base, nx0, ny0, l + 1));
+    }
+    const MgLevel<TI> Lc = mg_level<TI>(base, nx0, ny0, levels - 1);
+    mg_zero(Lc);
+    for (int s = 0; s < kCoarseSweeps; ++s) {
+        mg_half_sweep(Lc, 0);
+        mg_half_sweep(Lc, 1);
+        mg_half_sweep(Lc, 1);
+        mg_half_sweep(Lc, 0);
+    }
+    for (int l = levels - 2; l >= 0; --l) {
+        const MgLevel<TI> F = mg_level<TI>(base, nx0, ny0, l);
+        mg_prolong(F, mg_level<TI>(base, nx0, ny0, l + 1));
+        mg_half_sweep(F, 1);
+        mg_half_sweep(F, 0);
+    }
+}
+
 // Subdomain `sub` of the problem described by P, solved by the calling CTA.
 template <typename TI>
 __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double* sh)
@@ -125,6 +339,20 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
     __syncthreads();
     block_sum<2>(bn, sh);
 
+    // multigrid hierarchy of this subdomain
+    void* mgbase = static_cast<char*>(P.mg) + (size_t)sub * P.mg_stride;
+    SolveParams Pm = P;
+    Pm.mg = mgbase;
+    const int levels = mg_levels(ni, nj);
+    if (nint > 0) mg_setup<TI>(Pm, i0, j0, ni, nj, levels);
+    const MgLevel<TI> L0 = mg_level<TI>(mgbase, ni, nj, 0);
+    // z = V-cycle(r) into L0.x (interior-compact), from the full-grid residual r
+    auto precondition = [&]() {
+        for (int t = threadIdx.x; t < nint; t += blockDim.x) L0.b[t] = r[node(t)];
+        __syncthreads();
+        mg_vcycle<TI>(mgbase, ni, nj, levels);
+    };
+
     const bool fp64_inner = sizeof(TI) == 8;
     int iters = 0, outer = 0, ok = 0;
     double rel = 0.0;
@@ -164,13 +392,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
             if (t > 0.5) t = 0.5;
             tol_rel[c] = t;
         }
-        // CG start: e = 0, p = z = r / diag
+        // CG start: e = 0, p = z = M^-1 r (one V-cycle)
+        precondition();
         double rz[2] = {0.0, 0.0}, rr0[2] = {0.0, 0.0};
         for (int t = threadIdx.x; t < nint; t += blockDim.x) {
             const long id = node(t);
-            const TI diag = (TI)dP(id) + ce[id] + ce[id - 1] + cn[id] + cn[id - nx];
             const Pair<TI> rv = r[id];
-            const Pair<TI> z = Pair<TI>{rv.x / diag, rv.y / diag};
+            const Pair<TI> z = L0.x[t];
             e[id] = Pair<TI>{(TI)0, (TI)0};
             p[id] = z;
             rz[0] += (double)rv.x * (double)z.x;
@@ -206,15 +434,19 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
             double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z (x, y), r.r (x, y)
             for (int t = threadIdx.x; t < nint; t += blockDim.x) {
                 const long id = node(t);
-                const TI diag = (TI)dP(id) + ce[id] + ce[id - 1] + cn[id] + cn[id - nx];
                 const Pair<TI> pc = p[id], qv = q[id];
                 Pair<TI> ev = e[id], rv = r[id];
                 ev.x += ax * pc.x; ev.y += ay * pc.y;
                 rv.x -= ax * qv.x; rv.y -= ay * qv.y;
                 e[id] = ev;
                 r[id] = rv;
-                v[0] += (double)rv.x * (double)(rv.x / diag);
-                v[1] += (double)rv.y * (double)(rv.y / diag);
+            }
+            __syncthreads();
+            precondition();
+            for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+                const Pair<TI> rv = r[node(t)], z = L0.x[t];
+                v[0] += (double)rv.x * (double)z.x;
+                v[1] += (double)rv.y * (double)z.y;
                 v[2] += (double)rv.x * (double)rv.x;
                 v[3] += (double)rv.y * (double)rv.y;
             }
@@ -228,9 +460,8 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
             rz[1] = v[1];
             for (int t = threadIdx.x; t < nint; t += blockDim.x) {
                 const long id = node(t);
-                const TI diag = (TI)dP(id) + ce[id] + ce[id - 1] + cn[id] + cn[id - nx];
-                const Pair<TI> rv = r[id], pc = p[id];
-                p[id] = Pair<TI>{rv.x / diag + bx * pc.x, rv.y / diag + by * pc.y};
+                const Pair<TI> z = L0.x[t], pc = p[id];
+                p[id] = Pair<TI>{z.x + bx * pc.x, z.y + by * pc.y};
             }
             __syncthreads();
         }

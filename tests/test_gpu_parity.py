@@ -39,7 +39,8 @@ def test_philox_bit_exact(S):
     W.c1_front(W.PREC_FP64).replace(nx=65, ny=65),
     W.c1_front(W.PREC_FP64, periodic=1).replace(nx=65, ny=65),
     W.c3_mix(4)[1].replace(precision=W.PREC_FP64),
-], ids=["gauss", "front", "front_periodic", "bumps"])
+    W.five_ring(2),
+], ids=["gauss", "front", "front_periodic", "bumps", "rings"])
 def test_monitor_and_gradient(S, prob):
     x, y = W.sine_mode_mesh(prob, amp=0.01, periodic_mode=bool(prob.periodic))
     h = gpu_problem(prob, x, y)

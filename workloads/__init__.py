@@ -21,6 +21,7 @@ MONITOR_NODAL = 0   # nodal values supplied by the caller
 MONITOR_GAUSS = 1   # sqrt(1 + a exp(-b |x - c|^2))                    params (a, b, cx, cy)
 MONITOR_FRONT = 2   # sqrt(1 + alpha |grad u|^2), u = tanh(R (r - r0 - v t))  params (alpha, R, r0, v, cx, cy)
 MONITOR_BUMPS = 3   # 1 + sum_i a_i exp(-|x - c_i|^2 / w_i^2)          params (a_1, w_1, cx_1, cy_1, a_2, ...)
+MONITOR_RINGS = 4   # sqrt(1 + alpha |grad u|^2), u = sum_k tanh(R (|x - c_k|^2 - r2))  params (alpha, R, r2, cx_1, cy_1, ...)
 
 FORM_DIV = 0        # tau x_t = div(omega grad x)
 FORM_WINSLOW = 1    # tau x_t = (grad omega / omega) . grad x + lap x   (the paper's Eq. for the generator)
@@ -116,6 +117,19 @@ def c2_sine(precision: int = PREC_FP32_ACC64, paths: int = 1000) -> Problem:
     return Problem(name="sine257_4x4", nx=257, ny=257, px=4, py=4, tau=1e-2, dt=1e-3,
                    substeps=100, seed=1, paths_per_node=paths, precision=precision,
                    monitor_kind=MONITOR_BUMPS, monitor_params=[], steps=1, solve_rtol=1e-10)
+
+
+def five_ring(px: int, steps: int = 100, paths: int = 10000, nx: int = 41) -> Problem:
+    """The periodic five-ring problem of the paper's Sec. 4.2: u = sum of five tanh(R (|x - c|^2 - 1/8))
+    rings, R = 30, on [-1, 1)^2 (here shifted to [0, 2)^2, centres (1,1), (1/2,1/2), (1/2,3/2),
+    (3/2,1/2), (3/2,3/2)), arc-length monitor sqrt(1 + 0.2 |grad u|^2), 41 x 41 nodes,
+    dt = 5e-4 up to t = 0.05 (100 steps), one Euler-Maruyama substep per step, 1e4 paths, the
+    paper's generator form (tau = 1)."""
+    centres = [1.0, 1.0, 0.5, 0.5, 0.5, 1.5, 1.5, 0.5, 1.5, 1.5]
+    return Problem(name=f"five_ring{nx}_{px}x{px}", nx=nx, ny=nx, px=px, py=px, periodic=1,
+                   form=FORM_WINSLOW, precision=PREC_FP64, Lx=2.0, Ly=2.0, tau=1.0, dt=5e-4,
+                   substeps=1, seed=1, paths_per_node=paths, monitor_kind=MONITOR_RINGS,
+                   monitor_params=[0.2, 30.0, 0.125] + centres, steps=steps, solve_rtol=1e-12)
 
 
 GRID_CHOICES = (65, 129, 257, 513)
