@@ -58,9 +58,17 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="front", choices=["front", "mix"],
+    ap.add_argument("--workload", default="front", choices=["front", "mix", "serve"],
                     help="front: the 257x257 / 4x4 moving-front problem (the benchmark line); "
-                         "mix: the batch of 64 uneven problems, batched vs one at a time")
+                         "mix: the batch of 64 uneven problems, batched vs one at a time; "
+                         "serve: one-step requests of the mix's shapes with Poisson arrivals through "
+                         "the continuous-batching server")
+    ap.add_argument("--serve-n", type=int, default=64, help="serve: requests")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: mean arrivals per second")
+    ap.add_argument("--serve-first-chunk", type=int, default=10000, help="serve: first paths per node")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0, help="serve: device-memory budget")
+    ap.add_argument("--serve-round-paths", type=int, default=1 << 27,
+                    help="serve: paths per round, oldest requests first (0: all pending chunks)")
     ap.add_argument("--mix-n", type=int, default=64)
     ap.add_argument("--mix-batched-only", action="store_true",
                     help="mix: skip the one-at-a-time comparisons (profiling case)")
@@ -440,12 +448,102 @@ def run_mix(args):
     return 0
 
 
+def run_serve(args):
+    """Serving with continuous batching: requests drawn like the batched mix (grids 65..513, splits
+    2x2..8x8, 1-4 bump monitors), each one alternating step with every interface node at
+    SE <= --se-target, arriving as a Poisson process at --serve-rate per second and served by one
+    sdd_server (device-memory budget --serve-budget-gb).  Reports completed requests/s, interface-node
+    estimates/s and the latency from arrival to result collected (p50, p99)."""
+    import numpy as np
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    n = args.serve_n
+    reqs = [p.replace(precision=W.PREC_FP32_KAHAN, se_target=args.se_target, paths_per_node=args.serve_first_chunk,
+                      max_paths_per_node=args.max_paths)
+            for p in W.c3_mix(n + 2, seed=777, paths=args.serve_first_chunk)]
+    meshes = [W.identity_mesh(p) for p in reqs]
+    params = [S.params_from(p) for p in reqs]
+    mparams = [np.asarray(p.monitor_params, dtype=np.float64) for p in reqs]
+    arrivals = W.poisson_arrivals(n, args.serve_rate)
+    q = S.SddServerParams()
+    q.precision = W.PREC_FP32_KAHAN
+    q.max_resident = 1024
+    q.max_nodes = 1 << 19
+    q.mem_budget_bytes = int(args.serve_budget_gb * (1 << 30))
+    q.se_target = args.se_target
+    q.paths_per_node = args.serve_first_chunk
+    q.max_paths_per_node = args.max_paths
+    q.round_paths = args.serve_round_paths
+    stream = torch.cuda.Stream()
+    srv = S.SddServer(q, stream)
+
+    def submit(k):
+        return srv.submit(params[k], meshes[k][0], meshes[k][1], reqs[k].monitor_kind, mparams[k])
+
+    # warm-up: the last two requests of the draw, not timed
+    warm = [submit(n), submit(n + 1)]
+    got = []
+    while len(got) < len(warm):
+        srv.progress()
+        got += srv.poll()
+    for rid in got:
+        srv.result(rid)
+    s0 = srv.stats()
+    lat, done_at, nodes, ps = [], [], 0, 0
+    id_to_k = {}
+    t0 = time.perf_counter()
+    k = 0
+    while len(lat) < n:
+        now = time.perf_counter() - t0
+        while k < n and arrivals[k] <= now:
+            id_to_k[submit(k)] = k
+            k += 1
+        running, queued = srv.progress()
+        for rid in srv.poll():
+            _, st = S.sdd_server_result(srv.h, rid, None, None, None, None)
+            t = time.perf_counter() - t0
+            lat.append(t - arrivals[id_to_k[rid]])
+            done_at.append(t)
+            nodes += st["M"]
+            ps += st["path_steps"]
+        if running == 0 and queued == 0 and k < n:
+            wait = arrivals[k] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+    s1 = srv.stats()
+    srv.close()
+    T = max(done_at) - arrivals[0]
+    lat_ms = np.sort(np.asarray(lat)) * 1e3
+    out = {"metric": "serving: completed requests/s, interface-node estimates/s, latency p50/p99",
+           "workload": f"{n} one-step requests, grids 65..513, splits 2x2..8x8, bump monitors, "
+                       f"SE <= {args.se_target:g} per node (first chunk {args.serve_first_chunk}), "
+                       f"Poisson arrivals at {args.serve_rate:g}/s, {args.serve_round_paths} paths per round",
+           "requests_per_s": n / T, "interface_node_estimates_per_s": nodes / T,
+           "path_steps_per_s": ps / T, "latency_ms": {"p50": float(np.percentile(lat_ms, 50)),
+                                                      "p99": float(np.percentile(lat_ms, 99)),
+                                                      "max": float(lat_ms[-1])},
+           "offered_span_s": float(arrivals[-1] - arrivals[0]), "makespan_s": T,
+           "rounds": s1["rounds"] - s0["rounds"],
+           "path_kernel_s": (s1["mc_kernel_ms"] - s0["mc_kernel_ms"]) / 1e3,
+           "kernel_launches": s1["kernel_launches"] - s0["kernel_launches"],
+           "allocations": s1["allocations"], "resident_gb": s1["resident_bytes"] / 2 ** 30,
+           "pool_gb": s1["pool_bytes"] / 2 ** 30, "pool_high_water": s1["pool_high_water"]}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.mc_only > 0:
         return run_mc_only(args)
     if args.workload == "mix":
         return run_mix(args)
+    if args.workload == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

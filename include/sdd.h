@@ -231,6 +231,97 @@ sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out);
 /* Release the batch (not its problems). */
 void sdd_batch_destroy(sdd_batch* b);
 
+/* ---- Serving: continuous batching of one-step requests ------------------------------------
+ * A server advances independent requests -- one alternating step each (Sec. 3.6) of a mesh
+ * problem -- that arrive over time.  Requests join and leave the running set between rounds of
+ * the path kernel: a round is ONE persistent path-kernel launch over the interface nodes of all
+ * running requests (a shared node pool in which each request holds a contiguous range), and a
+ * request whose nodes have all reached the service level is finished at once (estimates,
+ * Dirichlet scatter, subdomain solves, on a second stream) while the others keep sampling.
+ * A request's result is bitwise that of sdd_step on a problem created alone with the same
+ * parameters, mesh, monitor and step index (own seed, local node ids in the Philox counter,
+ * per-node path schedule, fixed-order reductions).
+ * Admission is first come, first served, bounded by the node pool, the number of resident
+ * requests and a device-memory budget; with round_paths set, each round's paths also go to
+ * the oldest running requests first, so requests complete close to arrival order instead of
+ * all together.  The device state of collected requests is kept per
+ * grid shape (nx, ny, px, py, periodic) and reused, so steady-state serving allocates no
+ * device memory; cached state is freed (oldest first) only when a new shape needs room.
+ * The paper has no serving layer: this is the system around its method. */
+typedef struct sdd_server sdd_server;
+
+typedef struct {
+    int32_t precision;           /* SDD_FP64 / SDD_FP32_ACC64 / SDD_FP32_KAHAN for every request */
+    int32_t max_resident;        /* requests holding device state at once (running, finishing,
+                                    or finished but not collected), in [1, 2^16]                */
+    int64_t max_nodes;           /* node-pool capacity (interface nodes of resident requests),
+                                    in [1, 2^24]; each pool node costs about 12.5 KB            */
+    int64_t mem_budget_bytes;    /* device bytes for per-request state (pool excluded), 0 = no
+                                    limit                                                       */
+    double se_target;            /* service level, meaning as in sdd_params (0: fixed N)        */
+    int64_t paths_per_node;      /* fixed N, or the first chunk when adaptive, >= 2              */
+    int64_t max_paths_per_node;  /* adaptive cap in [paths_per_node, 2^31]                       */
+    int64_t round_paths;         /* > 0: paths per round at most, given to running requests
+                                    oldest first (a node's chunk is never split, and the first
+                                    pending node always runs); 0: every pending chunk each round */
+} sdd_server_params;
+
+typedef struct {
+    int64_t submitted, completed, collected; /* requests                                        */
+    int32_t queued, running, finishing, done; /* requests in each state now                     */
+    int64_t rounds;              /* path-kernel rounds launched                                 */
+    int64_t kernel_launches;     /* kernels launched by the server                               */
+    double mc_kernel_ms;         /* device time of all completed path-kernel rounds (CUDA events) */
+    int64_t path_steps;          /* substeps taken by the paths of completed requests            */
+    int64_t interface_nodes;     /* interface nodes of completed requests                         */
+    int64_t resident_bytes;      /* device bytes of request state held now (cache included)     */
+    int64_t cached_bytes;        /* of which kept for reuse                                      */
+    int64_t pool_bytes;          /* device bytes of the node pool                                */
+    int64_t pool_high_water;     /* highest pool node index + 1 used so far                       */
+    int64_t allocations;         /* per-request device-state allocations since creation          */
+} sdd_server_stats;
+
+/* Create a server whose work is ordered on `stream` (cudaStream_t, not NULL; a non-blocking
+ * stream is best) plus two internal streams (uploads; finishing requests). */
+sdd_status sdd_server_create(const sdd_server_params* params, void* stream, sdd_server** out);
+
+/* Queue one request: an alternating step of the problem `params` (precision, se_target,
+ * paths_per_node and max_paths_per_node must equal the server's) from the mesh (x0, y0) (HOST
+ * memory, nx*ny each, copied) at time-step index step_index >= 0 (fourth Philox counter word;
+ * time t0 + step_index dt).  Monitor: an analytic kind with its parameters as for
+ * sdd_set_monitor_analytic, or SDD_MONITOR_NODAL with omega (HOST, nx*ny, copied; NULL means
+ * omega = 1).  *id receives the request id (increasing from 1).  Does not touch the GPU. */
+sdd_status sdd_server_submit(sdd_server* s, const sdd_params* params, const double* x0, const double* y0,
+                             int32_t monitor_kind, const double* monitor_params, int32_t n_params,
+                             const double* omega, int32_t step_index, int64_t* id);
+
+/* One scheduling round: collect finishing requests whose work is complete, admit queued ones
+ * (upload, monitor, node-pool init), plan the next path-kernel round over all running requests,
+ * start finishing every request whose nodes are all done, and launch the round.  Waits for the
+ * previous round's reductions (one host round trip per round).  Outputs (nullable): requests
+ * running and queued after the call.  A request that can never fit the memory budget completes
+ * with SDD_ERR_OOM. */
+sdd_status sdd_server_progress(sdd_server* s, int32_t* n_running, int32_t* n_queued);
+
+/* Ids of requests completed since the last poll, oldest first (at most cap; the rest wait for
+ * the next poll); *n receives the count. */
+sdd_status sdd_server_poll(sdd_server* s, int64_t* ids, int32_t cap, int32_t* n);
+
+/* Result of a completed request: the new mesh (x, y: nx*ny each), its interface estimates and
+ * standard errors (est_xy, se_xy: M x 2, node-id order), and its counters (st: M, step_index +
+ * 1, t, path_steps, paths, mc_rounds = rounds launched while it had pending nodes,
+ * nodes_not_reached, max_se, solve maxima).  Host or device pointers, each nullable; returns when host outputs are written.
+ * Releases the request (its id becomes invalid).  Returns the request's own status:
+ * SDD_ERR_SE_NOT_REACHED or SDD_ERR_NOT_CONVERGED with outputs written, SDD_ERR_OOM without. */
+sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, double* est_xy, double* se_xy,
+                             sdd_stats* st);
+
+/* Counters of the server (waits for nothing). */
+sdd_status sdd_server_get_stats(sdd_server* s, sdd_server_stats* out);
+
+/* Wait for the server's streams and release everything, including uncollected requests. */
+void sdd_server_destroy(sdd_server* s);
+
 /* Allocation-free interface Monte Carlo.  The paper has no counterpart: this entry point
  * serves callers that cannot call cudaMalloc -- for instance a host framework whose caching
  * allocator owns the device memory budget and forbids allocations outside it, or a

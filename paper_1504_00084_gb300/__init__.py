@@ -54,6 +54,26 @@ class SddStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SddServerParams(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_resident", ctypes.c_int32),
+                ("max_nodes", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
+                ("se_target", ctypes.c_double), ("paths_per_node", ctypes.c_int64),
+                ("max_paths_per_node", ctypes.c_int64), ("round_paths", ctypes.c_int64)]
+
+
+class SddServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("collected", ctypes.c_int64),
+                ("queued", ctypes.c_int32), ("running", ctypes.c_int32), ("finishing", ctypes.c_int32),
+                ("done", ctypes.c_int32), ("rounds", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("mc_kernel_ms", ctypes.c_double), ("path_steps", ctypes.c_int64),
+                ("interface_nodes", ctypes.c_int64), ("resident_bytes", ctypes.c_int64),
+                ("cached_bytes", ctypes.c_int64), ("pool_bytes", ctypes.c_int64),
+                ("pool_high_water", ctypes.c_int64), ("allocations", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTS = [
     "sdd_create_problem", "sdd_destroy_problem", "sdd_set_stream", "sdd_set_mesh", "sdd_get_mesh",
     "sdd_set_monitor", "sdd_set_monitor_analytic", "sdd_interface_mc", "sdd_subdomain_solve",
@@ -62,6 +82,8 @@ EXPORTS = [
     "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
     "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy",
     "sdd_mesh_quality",
+    "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
+    "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
 ]
 
 
@@ -95,6 +117,14 @@ def _load():
         "sdd_batch_get_stats": ([P, ctypes.POINTER(SddStats)], I32),
         "sdd_batch_destroy": ([P], None),
         "sdd_mesh_quality": ([P, P, ctypes.POINTER(F64), ctypes.POINTER(F64)], I32),
+        "sdd_server_create": ([ctypes.POINTER(SddServerParams), P, ctypes.POINTER(P)], I32),
+        "sdd_server_submit": ([P, ctypes.POINTER(SddParams), P, P, I32, P, I32, P, I32,
+                               ctypes.POINTER(I64)], I32),
+        "sdd_server_progress": ([P, ctypes.POINTER(I32), ctypes.POINTER(I32)], I32),
+        "sdd_server_poll": ([P, P, I32, ctypes.POINTER(I32)], I32),
+        "sdd_server_result": ([P, I64, P, P, P, P, ctypes.POINTER(SddStats)], I32),
+        "sdd_server_get_stats": ([P, ctypes.POINTER(SddServerStats)], I32),
+        "sdd_server_destroy": ([P], None),
         "sdd_status_string": ([I32], ctypes.c_char_p),
         "sdd_last_error": ([], ctypes.c_char_p),
     }
@@ -387,6 +417,108 @@ class SddBatch:
     def close(self):
         if self.h:
             sdd_batch_destroy(self.h)
+            self.h = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------------------
+# Serving (continuous batching of one-step requests).
+# --------------------------------------------------------------------------------------
+
+def sdd_server_create(params: SddServerParams, stream) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.sdd_server_create(ctypes.byref(params), _stream_handle(stream), ctypes.byref(h)),
+           "sdd_server_create")
+    return h.value
+
+
+def sdd_server_submit(s: int, params: SddParams, x0, y0, monitor_kind: int = SDD_MONITOR_NODAL,
+                      monitor_params=None, omega=None, step_index: int = 0) -> int:
+    mp = None if monitor_params is None else np.ascontiguousarray(monitor_params, dtype=np.float64)
+    n = 0 if mp is None else int(mp.size)
+    rid = ctypes.c_int64()
+    _check(lib.sdd_server_submit(s, ctypes.byref(params), _ptr(x0), _ptr(y0), monitor_kind, _ptr(mp), n,
+                                 _ptr(omega), step_index, ctypes.byref(rid)), "sdd_server_submit")
+    return rid.value
+
+
+def sdd_server_progress(s: int):
+    nr, nq = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib.sdd_server_progress(s, ctypes.byref(nr), ctypes.byref(nq)), "sdd_server_progress")
+    return nr.value, nq.value
+
+
+def sdd_server_poll(s: int, cap: int = 1024):
+    ids = np.zeros(max(cap, 1), dtype=np.int64)
+    n = ctypes.c_int32()
+    _check(lib.sdd_server_poll(s, _ptr(ids), cap, ctypes.byref(n)), "sdd_server_poll")
+    return [int(v) for v in ids[:n.value]]
+
+
+def sdd_server_result(s: int, rid: int, x=None, y=None, est_xy=None, se_xy=None,
+                      ok=(SDD_OK, SDD_ERR_SE_NOT_REACHED)):
+    st = SddStats()
+    status = _check(lib.sdd_server_result(s, rid, _ptr(x), _ptr(y), _ptr(est_xy), _ptr(se_xy),
+                                          ctypes.byref(st)), "sdd_server_result", ok=ok)
+    return status, st.as_dict()
+
+
+def sdd_server_get_stats(s: int) -> dict:
+    o = SddServerStats()
+    _check(lib.sdd_server_get_stats(s, ctypes.byref(o)), "sdd_server_get_stats")
+    return o.as_dict()
+
+
+def sdd_server_destroy(s: int) -> None:
+    lib.sdd_server_destroy(s)
+
+
+class SddServer:
+    """Owning handle of a server; results come back as numpy arrays."""
+
+    def __init__(self, params: SddServerParams, stream):
+        self.h = sdd_server_create(params, stream)
+        self.shapes = {}
+
+    def submit(self, params: SddParams, x0, y0, monitor_kind=SDD_MONITOR_NODAL, monitor_params=None,
+               omega=None, step_index=0) -> int:
+        rid = sdd_server_submit(self.h, params, x0, y0, monitor_kind, monitor_params, omega, step_index)
+        M = int(sdd_interface_layout(params.nx, params.ny, params.px, params.py, params.periodic).shape[0])
+        self.shapes[rid] = (params.nx, params.ny, M)
+        return rid
+
+    def progress(self):
+        return sdd_server_progress(self.h)
+
+    def poll(self, cap=1024):
+        return sdd_server_poll(self.h, cap)
+
+    def result(self, rid, ok=(SDD_OK, SDD_ERR_SE_NOT_REACHED)):
+        nx, ny, M = self.shapes.pop(rid)
+        x = np.empty((ny, nx))
+        y = np.empty((ny, nx))
+        est = np.empty((max(M, 1), 2))
+        se = np.empty((max(M, 1), 2))
+        status, st = sdd_server_result(self.h, rid, x, y, est, se, ok=ok)
+        return {"x": x, "y": y, "est": est[:M], "se": se[:M], "stats": st, "status": status}
+
+    def stats(self):
+        return sdd_server_get_stats(self.h)
+
+    def close(self):
+        if self.h:
+            sdd_server_destroy(self.h)
             self.h = 0
 
     def __enter__(self):

@@ -16,7 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libsdd.so")
-SOURCES = ["sdd_api.cu", "sdd_prep.cu", "sdd_mc.cu", "sdd_solve.cu", "sdd_noalloc.cu", "sdd_batch.cu"]
+SOURCES = ["sdd_api.cu", "sdd_prep.cu", "sdd_mc.cu", "sdd_solve.cu", "sdd_noalloc.cu", "sdd_batch.cu",
+           "sdd_server.cu"]
 HEADERS = [os.path.join(CSRC, "sdd_internal.cuh"), os.path.join(CSRC, "sdd_problem.cuh"),
            os.path.join(ROOT, "include", "sdd.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

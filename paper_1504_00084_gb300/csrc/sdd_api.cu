@@ -137,24 +137,15 @@ sdd_status copy_out(sdd_problem* p, void* dst, const void* src, size_t bytes)
 sdd_status check_boundary(const sdd_problem* p, const double* x, const double* y)
 {
     if (p->prm.periodic) return SDD_OK;
-    const int nx = p->prm.nx, ny = p->prm.ny;
-    std::vector<double> hx((size_t)nx * ny), hy((size_t)nx * ny);
-    if (cudaMemcpy(hx.data(), x, hx.size() * 8, cudaMemcpyDefault) != cudaSuccess ||
-        cudaMemcpy(hy.data(), y, hy.size() * 8, cudaMemcpyDefault) != cudaSuccess) {
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    std::vector<double> hx(N), hy(N);
+    if (cudaMemcpy(hx.data(), x, N * 8, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(hy.data(), y, N * 8, cudaMemcpyDefault) != cudaSuccess) {
         cudaGetLastError();
         return fail(SDD_ERR_INVALID_ARG, "mesh pointers are not readable");
     }
-    const double tol = 1e-12 * (p->prm.Lx + p->prm.Ly);
-    for (int j = 0; j < ny; ++j)
-        for (int i = 0; i < nx; ++i) {
-            if (i != 0 && j != 0 && i != nx - 1 && j != ny - 1) continue;
-            const double bx = p->prm.Lx * ((double)i / (double)(nx - 1));
-            const double by = p->prm.Ly * ((double)j / (double)(ny - 1));
-            const size_t id = (size_t)j * nx + i;
-            if (!(fabs(hx[id] - bx) <= tol) || !(fabs(hy[id] - by) <= tol))
-                return fail(SDD_ERR_INVALID_ARG,
-                            "Dirichlet mesh must equal (Lx xi, Ly eta) on the boundary");
-        }
+    if (!sdd_boundary_ok(p->prm, hx.data(), hy.data()))
+        return fail(SDD_ERR_INVALID_ARG, "Dirichlet mesh must equal (Lx xi, Ly eta) on the boundary");
     return SDD_OK;
 }
 
@@ -339,6 +330,135 @@ sdd_status run_solve(sdd_problem* p)
 
 }  // namespace
 
+// ---- Problem allocation (shared with the batch and server translation units) -------------
+
+namespace {
+
+// Every device array of a problem in allocation order; with_mc adds the problem's own interface
+// Monte Carlo state (node sums, round plan, task slots, estimates).  p->prm, p->M and
+// p->slot_cap must be set.
+template <typename F>
+void problem_arrays(sdd_problem* p, bool with_mc, F&& f)
+{
+    const sdd_params& q = p->prm;
+    const size_t N = (size_t)q.nx * q.ny;
+    const size_t M = (size_t)p->M;
+    const size_t rs = q.precision == SDD_FP64 ? 8 : 4;
+    const int ns = q.px * q.py;
+    f((void**)&p->x, N * 8); f((void**)&p->y, N * 8); f((void**)&p->xn, N * 8); f((void**)&p->yn, N * 8);
+    f((void**)&p->om64, N * 8); f((void**)&p->wxi64, N * 8); f((void**)&p->weta64, N * 8);
+    f((void**)&p->omega_nodal, N * 8);
+    f((void**)&p->mon, N * 4 * rs); f((void**)&p->disp, N * 2 * rs);
+    f((void**)&p->nodes, (M + 1) * sizeof(int2));
+    if (with_mc) {
+        f((void**)&p->shift, (M + 1) * 16);
+        f((void**)&p->acc, (M + 1) * 32); f((void**)&p->n_done, (M + 1) * 8); f((void**)&p->steps, (M + 1) * 8);
+        f((void**)&p->paths_run, (M + 1) * 8); f((void**)&p->next_total, (M + 1) * 8);
+        f((void**)&p->node_of, (M + 1) * 4); f((void**)&p->p_begin, (M + 1) * 8); f((void**)&p->p_count, (M + 1) * 8);
+        f((void**)&p->task_off, (M + 2) * 8); f((void**)&p->n_active, 16); f((void**)&p->task_counter, 16);
+        f((void**)&p->slots, (size_t)p->slot_cap * sizeof(TaskSlot));
+        f((void**)&p->est, (M + 1) * 16); f((void**)&p->se, (M + 1) * 16);
+    }
+    f((void**)&p->ce64, N * 8); f((void**)&p->cn64, N * 8); f((void**)&p->ce, N * rs); f((void**)&p->cn, N * rs);
+    f((void**)&p->vec, N * 4 * 2 * rs);
+    f((void**)&p->st_iters, (size_t)ns * 4); f((void**)&p->st_outer, (size_t)ns * 4);
+    f((void**)&p->st_ok, (size_t)ns * 4); f((void**)&p->st_res, (size_t)ns * 8);
+    f((void**)&p->quality, (N + 2) * 8);
+    f((void**)&p->mg, p->mg_stride * ns);
+}
+
+// Problem shell: parameters, interface layout, sizes; no device memory yet.
+sdd_problem* problem_shell(const sdd_params& prm, cudaStream_t stream)
+{
+    sdd_problem* p = new sdd_problem();
+    p->prm = prm;
+    p->stream = stream;
+    p->fp64 = prm.precision == SDD_FP64;
+    p->acc_mode = prm.precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
+    layout(prm.nx, prm.ny, prm.px, prm.py, prm.periodic, p->ij);
+    p->M = (int)(p->ij.size() / 2);
+    p->slot_cap = (int64_t)(p->M > 0 ? p->M : 1) * kSlotsPerNode;
+    const size_t rs = p->fp64 ? 8 : 4;
+    p->mg_stride = mg_bytes((prm.nx - 1) / prm.px - 1, (prm.ny - 1) / prm.py - 1, rs);
+    p->stats.M = p->M;
+    p->stats.t = prm.t0;
+    return p;
+}
+
+size_t alloc_rounded(size_t bytes) { return ((bytes < 16 ? 16 : bytes) + 511) / 512 * 512; }
+
+}  // namespace
+
+sdd_status sdd_validate_params(const sdd_params* P) { return validate(P); }
+
+void sdd_layout(int nx, int ny, int px, int py, int periodic, std::vector<int32_t>& ij)
+{
+    layout(nx, ny, px, py, periodic, ij);
+}
+
+size_t sdd_problem_device_bytes(const sdd_params& prm, bool with_mc)
+{
+    sdd_problem* p = problem_shell(prm, nullptr);
+    size_t total = 0;
+    problem_arrays(p, with_mc, [&](void**, size_t b) { total += alloc_rounded(b); });
+    delete p;
+    return total;
+}
+
+sdd_status sdd_alloc_problem(const sdd_params& prm, cudaStream_t stream, bool with_mc, sdd_problem** out)
+{
+    *out = nullptr;
+    sdd_problem* p = problem_shell(prm, stream);
+    cudaError_t e = cudaSuccess;
+    problem_arrays(p, with_mc, [&](void** ptr, size_t b) {
+        if (e == cudaSuccess) e = p->dalloc(ptr, b);
+        if (e == cudaSuccess) p->dev_bytes += alloc_rounded(b);
+    });
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_n_active, 16, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const std::string msg = std::string("allocation failed: ") + cudaGetErrorString(e);
+        delete p;
+        return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, msg);
+    }
+    const size_t N = (size_t)prm.nx * prm.ny;
+    const size_t rs = p->fp64 ? 8 : 4;
+    e = cudaMemsetAsync(p->vec, 0, N * 4 * 2 * rs, p->stream);
+    if (e == cudaSuccess && p->M > 0)
+        e = cudaMemcpyAsync(p->nodes, p->ij.data(), (size_t)p->M * sizeof(int2), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // p->ij is pageable host memory
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        const std::string msg = std::string("problem setup: ") + cudaGetErrorString(e);
+        delete p;
+        return fail(SDD_ERR_CUDA, msg);
+    }
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int per_sm = p->fp64 ? mc_max_blocks_per_sm<double>(p->acc_mode, false, false)
+                               : mc_max_blocks_per_sm<float>(p->acc_mode, false, false);
+    p->mc_grid = nsm * per_sm;
+    *out = p;
+    return SDD_OK;
+}
+
+bool sdd_boundary_ok(const sdd_params& prm, const double* hx, const double* hy)
+{
+    if (prm.periodic) return true;
+    const int nx = prm.nx, ny = prm.ny;
+    const double tol = 1e-12 * (prm.Lx + prm.Ly);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            if (i != 0 && j != 0 && i != nx - 1 && j != ny - 1) continue;
+            const double bx = prm.Lx * ((double)i / (double)(nx - 1));
+            const double by = prm.Ly * ((double)j / (double)(ny - 1));
+            const size_t id = (size_t)j * nx + i;
+            if (!(fabs(hx[id] - bx) <= tol) || !(fabs(hy[id] - by) <= tol)) return false;
+        }
+    return true;
+}
+
 extern "C" {
 
 const char* sdd_status_string(sdd_status s)
@@ -387,60 +507,21 @@ sdd_status sdd_create_problem(const sdd_params* params, const double* x0, const 
         cudaGetLastError();
         return fail(SDD_ERR_NO_DEVICE, "no CUDA device visible");
     }
-    sdd_problem* p = new sdd_problem();
-    p->prm = *params;
-    p->stream = static_cast<cudaStream_t>(stream);
-    p->fp64 = params->precision == SDD_FP64;
-    p->acc_mode = params->precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
-    layout(params->nx, params->ny, params->px, params->py, params->periodic, p->ij);
-    p->M = (int)(p->ij.size() / 2);
+    sdd_problem* p = nullptr;
+    SDD_TRY(sdd_alloc_problem(*params, static_cast<cudaStream_t>(stream), true, &p));
     auto bail = [&](sdd_status s) { delete p; return s; };
     {
         sdd_status s = check_boundary(p, x0, y0);
         if (s != SDD_OK) return bail(s);
     }
     const size_t N = (size_t)params->nx * params->ny;
-    const size_t M = (size_t)p->M;
-    const size_t rs = p->fp64 ? 8 : 4;
-    p->slot_cap = (int64_t)(M > 0 ? M : 1) * kSlotsPerNode;
-    cudaError_t e = cudaSuccess;
-#define ALLOC(ptr, bytes) if (e == cudaSuccess) e = p->dalloc(&(ptr), (bytes))
-    ALLOC(p->x, N * 8); ALLOC(p->y, N * 8); ALLOC(p->xn, N * 8); ALLOC(p->yn, N * 8);
-    ALLOC(p->om64, N * 8); ALLOC(p->wxi64, N * 8); ALLOC(p->weta64, N * 8); ALLOC(p->omega_nodal, N * 8);
-    ALLOC(p->mon, N * 4 * rs); ALLOC(p->disp, N * 2 * rs);
-    ALLOC(p->nodes, (M + 1) * sizeof(int2)); ALLOC(p->shift, (M + 1) * 16);
-    ALLOC(p->acc, (M + 1) * 32); ALLOC(p->n_done, (M + 1) * 8); ALLOC(p->steps, (M + 1) * 8);
-    ALLOC(p->paths_run, (M + 1) * 8); ALLOC(p->next_total, (M + 1) * 8);
-    ALLOC(p->node_of, (M + 1) * 4); ALLOC(p->p_begin, (M + 1) * 8); ALLOC(p->p_count, (M + 1) * 8);
-    ALLOC(p->task_off, (M + 2) * 8); ALLOC(p->n_active, 16); ALLOC(p->task_counter, 16);
-    ALLOC(p->slots, (size_t)p->slot_cap * sizeof(TaskSlot));
-    ALLOC(p->est, (M + 1) * 16); ALLOC(p->se, (M + 1) * 16);
-    ALLOC(p->ce64, N * 8); ALLOC(p->cn64, N * 8); ALLOC(p->ce, N * rs); ALLOC(p->cn, N * rs);
-    ALLOC(p->vec, N * 4 * 2 * rs);
-    const int ns = params->px * params->py;
-    ALLOC(p->st_iters, ns * 4); ALLOC(p->st_outer, ns * 4); ALLOC(p->st_ok, ns * 4); ALLOC(p->st_res, ns * 8);
-    ALLOC(p->quality, (N + 2) * 8);
-    p->mg_stride = mg_bytes((params->nx - 1) / params->px - 1, (params->ny - 1) / params->py - 1, rs);
-    ALLOC(p->mg, p->mg_stride * ns);
-#undef ALLOC
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_n_active, 16, cudaHostAllocDefault);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        const std::string msg = std::string("allocation failed: ") + cudaGetErrorString(e);
-        delete p;
-        return fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, msg);
-    }
     auto ck = [&](cudaError_t c, const char* what) -> sdd_status {
         if (c == cudaSuccess) return SDD_OK;
         return fail(SDD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(c));
     };
     sdd_status s = SDD_OK;
-    if (s == SDD_OK) s = ck(cudaMemsetAsync(p->vec, 0, N * 4 * 2 * rs, p->stream), "memset");
     if (s == SDD_OK) s = ck(cudaMemcpyAsync(p->x, x0, N * 8, cudaMemcpyDefault, p->stream), "copy x0");
     if (s == SDD_OK) s = ck(cudaMemcpyAsync(p->y, y0, N * 8, cudaMemcpyDefault, p->stream), "copy y0");
-    if (s == SDD_OK && M > 0)
-        s = ck(cudaMemcpyAsync(p->nodes, p->ij.data(), M * sizeof(int2), cudaMemcpyHostToDevice, p->stream),
-               "copy nodes");
     // default monitor: omega = 1 everywhere
     if (s == SDD_OK) {
         std::vector<double> ones(N, 1.0);
@@ -448,14 +529,6 @@ sdd_status sdd_create_problem(const sdd_params* params, const double* x0, const 
         if (s == SDD_OK) s = ck(cudaStreamSynchronize(p->stream), "sync");
     }
     if (s != SDD_OK) return bail(s);
-    int dev = 0, nsm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = p->fp64 ? mc_max_blocks_per_sm<double>(p->acc_mode, false, false)
-                               : mc_max_blocks_per_sm<float>(p->acc_mode, false, false);
-    p->mc_grid = nsm * per_sm;
-    p->stats.M = p->M;
-    p->stats.t = params->t0;
     *out = p;
     return SDD_OK;
 }

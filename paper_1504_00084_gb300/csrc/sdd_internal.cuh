@@ -119,6 +119,11 @@ struct PlanParams {
     int32_t* n_active;
     int32_t* task_counter;
     int32_t* host_n_active;    // mapped pinned host word
+    // optional planning order: M positions taken from n_ranges pool ranges in list order
+    const int32_t* range_off;  // first node of each range (null: positions are node ids)
+    const int32_t* range_pre;  // exclusive prefix of the range lengths (n_ranges + 1)
+    int n_ranges;
+    int64_t max_tasks;         // > 0: cap on the round's tasks (nodes in planning order)
 };
 
 struct ReduceParams {

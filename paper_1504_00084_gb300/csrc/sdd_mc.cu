@@ -570,6 +570,22 @@ __device__ V block_exclusive_scan(V v, V* warp_tot, V& total)
     return res;
 }
 
+// Node of planning position v: v itself, or (ranges given) position v of the concatenation of
+// the ranges [range_off[r], range_off[r] + range_pre[r+1] - range_pre[r]) in list order.
+__device__ __forceinline__ int plan_node(const PlanParams& P, int v)
+{
+    if (!P.range_off) return v;
+    int lo = 0, hi = P.n_ranges - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.range_pre[mid] <= v) lo = mid; else hi = mid - 1;
+    }
+    return P.range_off[lo] + (v - P.range_pre[lo]);
+}
+
+// With max_tasks > 0 the round takes nodes in planning order while the tasks before them number
+// fewer than max_tasks (at least the first pending node); later nodes keep their chunk for a
+// later round.  A node's chunks, and hence its results, do not depend on the cap.
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
 {
     __shared__ int64_t s_tasks[33];
@@ -577,19 +593,25 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
     int64_t task_base = 0;
     int act_base = 0;
     for (int base = 0; base < P.M; base += kPlanThreads) {
-        const int m = base + threadIdx.x;
+        const int v = base + threadIdx.x;
+        const int m = v < P.M ? plan_node(P, v) : 0;
         int64_t cnt = 0;
-        if (m < P.M) {
+        if (v < P.M) {
             cnt = P.next_total[m] - P.n_done[m];
             if (cnt > kMaxChunkPerRound) cnt = kMaxChunkPerRound;
             if (cnt < 0) cnt = 0;
         }
-        const int act = cnt > 0 ? 1 : 0;
-        const int64_t tasks = act ? (cnt + kPathsPerTask - 1) / kPathsPerTask : 0;
-        int act_tot;
+        const int64_t tasks = cnt > 0 ? (cnt + kPathsPerTask - 1) / kPathsPerTask : 0;
         int64_t task_tot;
-        const int a_ex = block_exclusive_scan<int>(act, s_act, act_tot);
         const int64_t t_ex = block_exclusive_scan<int64_t>(tasks, s_tasks, task_tot);
+        // the cap excludes a suffix of this block's nodes, so t_ex is also the prefix over the
+        // nodes that stay
+        const bool fits = P.max_tasks <= 0 || task_base + t_ex < P.max_tasks;
+        const int act = (cnt > 0 && fits) ? 1 : 0;
+        int act_tot;
+        const int a_ex = block_exclusive_scan<int>(act, s_act, act_tot);
+        int64_t kept_tot;
+        (void)block_exclusive_scan<int64_t>(act ? tasks : 0, s_tasks, kept_tot);
         if (act) {
             const int a = act_base + a_ex;
             P.node_of[a] = m;
@@ -598,7 +620,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
             P.task_off[a] = task_base + t_ex;
         }
         act_base += act_tot;
-        task_base += task_tot;
+        task_base += kept_tot;
+        if (P.max_tasks > 0 && task_base >= P.max_tasks) break;
     }
     if (threadIdx.x == 0) {
         P.task_off[act_base] = task_base;

@@ -50,6 +50,7 @@ struct sdd_problem {
     int32_t* h_n_active = nullptr;  // pinned
     sdd_stats stats{};
     std::vector<void*> allocs;
+    size_t dev_bytes = 0;          // device bytes held (allocation granularity included)
     std::vector<cudaEvent_t> ev;  // start/stop pairs around path-kernel launches
     int64_t launches = 0;         // kernels launched since creation
 
@@ -74,6 +75,19 @@ struct sdd_problem {
 
 // Sets the calling thread's sdd_last_error message and returns s.
 sdd_status sdd_fail(sdd_status s, const char* msg);
+
+// Parameter checks of sdd_create_problem (sets the last error).
+sdd_status sdd_validate_params(const sdd_params* P);
+// Interface nodes (i, j) of a grid split, in node-id order (as sdd_interface_layout).
+void sdd_layout(int nx, int ny, int px, int py, int periodic, std::vector<int32_t>& ij);
+// Device bytes sdd_alloc_problem takes for these parameters.
+size_t sdd_problem_device_bytes(const sdd_params& prm, bool with_mc);
+// Allocates a problem's device arrays (with_mc: also its own interface MC state), uploads its
+// interface nodes and zeroes the solver vectors, all on `stream` (synchronised).  The mesh and
+// monitor are left for the caller to fill.
+sdd_status sdd_alloc_problem(const sdd_params& prm, cudaStream_t stream, bool with_mc, sdd_problem** out);
+// Host check of a Dirichlet mesh's boundary: (Lx xi, Ly eta) within 1e-12 (Lx + Ly).
+bool sdd_boundary_ok(const sdd_params& prm, const double* hx, const double* hy);
 
 // Path-kernel record of a problem at its current step.
 template <typename T>
