@@ -149,7 +149,9 @@ sdd_status sdd_set_monitor_analytic(sdd_problem* p, int32_t kind, const double* 
  * (k, p, m, n) and key = seed, estimate x^{n+1} and y^{n+1} by the arithmetic mean.
  * Outputs (nullable): est_xy, se_xy: M x 2 doubles (node-major, x then y);
  * paths_used: M int64.  Does not advance time.  Returns SDD_ERR_SE_NOT_REACHED (outputs
- * still written) when an adaptive node hit max_paths_per_node. */
+ * still written) when an adaptive node hit max_paths_per_node, and SDD_ERR_INVALID_ARG (no
+ * outputs) when the monitor is not finite and > 0 at every node or the mesh is not finite
+ * (checked on the device during the call). */
 sdd_status sdd_interface_mc(sdd_problem* p, double* est_xy, double* se_xy, int64_t* paths_used);
 
 /* Subdomain solves (Sec. 3.5): Dirichlet data = iface_xy (M x 2, nullable = the last
@@ -159,7 +161,9 @@ sdd_status sdd_interface_mc(sdd_problem* p, double* est_xy, double* se_xy, int64
 sdd_status sdd_subdomain_solve(sdd_problem* p, const double* iface_xy, double* x_out, double* y_out);
 
 /* One alternating step t^n -> t^{n+1} (Sec. 3.6): monitor on x^n at t^n (analytic kinds),
- * interface MC, subdomain solves, then x^n <- x^{n+1}, n <- n + 1.  x_out, y_out nullable. */
+ * interface MC, subdomain solves, then x^n <- x^{n+1}, n <- n + 1.  x_out, y_out nullable.
+ * On an invalid monitor or mesh (as sdd_interface_mc) returns SDD_ERR_INVALID_ARG and takes no
+ * step. */
 sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out);
 
 /* Counters of the last calls (see sdd_stats). */
@@ -186,6 +190,20 @@ int64_t sdd_adaptive_next_total(int64_t n_done, double se, double target, int64_
  * square cell (Sec. 3.7).  q_cells: (nx-1)*(ny-1) doubles, row-major (nullable); *q_max and
  * *q_mean (nullable): the maximum and mean over the cells.  Returns when written. */
 sdd_status sdd_mesh_quality(sdd_problem* p, double* q_cells, double* q_max, double* q_mean);
+
+/* Checkpoint of a problem (no counterpart in the paper; the method has no hidden state beyond
+ * what is saved, because the Philox counter is the time-step index): parameters, time-step
+ * index, monitor (kind, parameters, nodal values) and the current mesh, written to the file
+ * `path` in this layout (little-endian): 8 bytes "SDDCKPT1", int32 sizeof(sdd_params), the
+ * sdd_params record, int64 step index, int32 monitor kind, int32 parameter count, 64 doubles
+ * of monitor parameters, then nx*ny doubles each of x, y and the nodal monitor.  Returns
+ * SDD_ERR_INVALID_ARG if the file cannot be written. */
+sdd_status sdd_save(sdd_problem* p, const char* path);
+
+/* Resume a problem from a checkpoint written by sdd_save, with its work on `stream`: stepping
+ * it continues bit for bit as the saved problem would have.  Returns SDD_ERR_INVALID_ARG for a
+ * missing, truncated or foreign file (checked before any device work). */
+sdd_status sdd_load(const char* path, void* stream, sdd_problem** out);
 
 /* Test hook: the monitor as frozen for the next MC call (nx*ny each, FP64, nullable):
  * omega and its finite-difference gradient (Sec. 3.4). */
@@ -225,7 +243,8 @@ sdd_status sdd_batch_step(sdd_batch* b);
 /* Counters of the last batch step over all problems: M, path_steps, paths, mc_rounds,
  * nodes_not_reached, max_se, solve maxima, kernel_launches (since creation), and in
  * mc_kernel_ms the device time of the whole last step (CUDA events on the batch's stream).
- * Waits for the batch's stream. */
+ * Waits for the batch's stream.  Returns SDD_ERR_INVALID_ARG (counters still written) when a
+ * problem's monitor was not finite and > 0 at every node or its mesh not finite in that step. */
 sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out);
 
 /* Release the batch (not its problems). */
@@ -312,7 +331,9 @@ sdd_status sdd_server_poll(sdd_server* s, int64_t* ids, int32_t cap, int32_t* n)
  * 1, t, path_steps, paths, mc_rounds = rounds launched while it had pending nodes,
  * nodes_not_reached, max_se, solve maxima).  Host or device pointers, each nullable; returns when host outputs are written.
  * Releases the request (its id becomes invalid).  Returns the request's own status:
- * SDD_ERR_SE_NOT_REACHED or SDD_ERR_NOT_CONVERGED with outputs written, SDD_ERR_OOM without. */
+ * SDD_ERR_SE_NOT_REACHED or SDD_ERR_NOT_CONVERGED with outputs written; without outputs,
+ * SDD_ERR_INVALID_ARG when its monitor was not finite and > 0 at every node or its mesh not
+ * finite (found after its first round; no subdomain solve is run), and SDD_ERR_OOM. */
 sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, double* est_xy, double* se_xy,
                              sdd_stats* st);
 

@@ -84,6 +84,7 @@ EXPORTS = [
     "sdd_mesh_quality",
     "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
     "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
+    "sdd_save", "sdd_load",
 ]
 
 
@@ -125,6 +126,8 @@ def _load():
         "sdd_server_result": ([P, I64, P, P, P, P, ctypes.POINTER(SddStats)], I32),
         "sdd_server_get_stats": ([P, ctypes.POINTER(SddServerStats)], I32),
         "sdd_server_destroy": ([P], None),
+        "sdd_save": ([P, ctypes.c_char_p], I32),
+        "sdd_load": ([ctypes.c_char_p, P, ctypes.POINTER(P)], I32),
         "sdd_status_string": ([I32], ctypes.c_char_p),
         "sdd_last_error": ([], ctypes.c_char_p),
     }
@@ -304,6 +307,23 @@ class SddProblem:
                                     np.ascontiguousarray(y0, dtype=np.float64)
                                     if isinstance(y0, np.ndarray) else y0, stream)
         self.M = len(sdd_get_interface_nodes(self.h))
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "SddProblem":
+        """Resume from a checkpoint written by save() (sdd_load)."""
+        self = cls.__new__(cls)
+        self.h = 0
+        h = sdd_load(path, stream)
+        with open(path, "rb") as f:
+            head = f.read(12 + ctypes.sizeof(SddParams))
+        self.params = SddParams.from_buffer_copy(head[12:])
+        self.nx, self.ny = self.params.nx, self.params.ny
+        self.h = h
+        self.M = len(sdd_get_interface_nodes(self.h))
+        return self
+
+    def save(self, path: str) -> None:
+        sdd_save(self.h, path)
 
     def close(self):
         if self.h:
@@ -532,3 +552,17 @@ class SddServer:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------------------
+# Checkpoint / resume.
+# --------------------------------------------------------------------------------------
+
+def sdd_save(h: int, path: str) -> None:
+    _check(lib.sdd_save(h, os.fsencode(path)), "sdd_save")
+
+
+def sdd_load(path: str, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib.sdd_load(os.fsencode(path), _stream_handle(stream), ctypes.byref(h)), "sdd_load")
+    return h.value

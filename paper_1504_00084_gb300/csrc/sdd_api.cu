@@ -51,6 +51,7 @@ namespace {
 constexpr int64_t kMaxChunk = int64_t(1) << 19;  // paths per node per launch (see plan kernel)
 constexpr int kSlotsPerNode = (int)(kMaxChunk / kPathsPerTask);
 constexpr int kMaxAdaptiveRounds = 4096;
+const char kCkptMagic[8] = {'S', 'D', 'D', 'C', 'K', 'P', 'T', '1'};
 
 void layout(int nx, int ny, int px, int py, int periodic, std::vector<int32_t>& ij)
 {
@@ -160,7 +161,8 @@ sdd_status run_prep(sdd_problem* p)
     P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
     memcpy(P.params, p->mon_params, sizeof(P.params));
     P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64;
-    P.mon = p->mon; P.disp = p->disp;
+    P.mon = p->mon; P.disp = p->disp; P.bad = p->bad;
+    SDD_CK(cudaMemsetAsync(p->bad, 0, 4, p->stream));
     SDD_CK(launch_prep(P, p->stream));
     p->launches += 2;
     if (p->M > 0) {
@@ -222,6 +224,9 @@ sdd_status run_mc(sdd_problem* p)
     p->stats.nodes_not_reached = 0;
     p->stats.max_se = 0.0;
     if (M == 0) {
+        SDD_CK(cudaMemcpyAsync(p->h_n_active + 1, p->bad, 4, cudaMemcpyDeviceToHost, p->stream));
+        SDD_CK(cudaStreamSynchronize(p->stream));
+        if (p->h_n_active[1]) return fail(SDD_ERR_INVALID_ARG, "monitor must be finite and > 0, mesh finite");
         p->have_est = true;
         return SDD_OK;
     }
@@ -273,7 +278,9 @@ sdd_status run_mc(sdd_problem* p)
     SDD_CK(cudaMemcpyAsync(st.data(), p->steps, 8 * (size_t)M, cudaMemcpyDeviceToHost, p->stream));
     SDD_CK(cudaMemcpyAsync(np.data(), p->paths_run, 8 * (size_t)M, cudaMemcpyDeviceToHost, p->stream));
     SDD_CK(cudaMemcpyAsync(se.data(), p->se, 16 * (size_t)M, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(p->h_n_active + 1, p->bad, 4, cudaMemcpyDeviceToHost, p->stream));
     SDD_CK(cudaStreamSynchronize(p->stream));
+    if (p->h_n_active[1]) return fail(SDD_ERR_INVALID_ARG, "monitor must be finite and > 0, mesh finite");
     p->stats.mc_kernel_ms = 0.0;
     p->stats.mc_kernel_launches = n_timed;
     for (int k = 0; k < n_timed; ++k) {
@@ -365,6 +372,7 @@ void problem_arrays(sdd_problem* p, bool with_mc, F&& f)
     f((void**)&p->st_ok, (size_t)ns * 4); f((void**)&p->st_res, (size_t)ns * 8);
     f((void**)&p->quality, (N + 2) * 8);
     f((void**)&p->mg, p->mg_stride * ns);
+    f((void**)&p->bad, 16);
 }
 
 // Problem shell: parameters, interface layout, sizes; no device memory yet.
@@ -664,6 +672,72 @@ sdd_status sdd_get_interface_nodes(const sdd_problem* p, int32_t* ij, int32_t* M
     if (!p || !M) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
     *M = p->M;
     if (ij && p->M > 0) memcpy(ij, p->ij.data(), p->ij.size() * sizeof(int32_t));
+    return SDD_OK;
+}
+
+sdd_status sdd_save(sdd_problem* p, const char* path)
+{
+    if (!p || !path) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    std::vector<double> buf(3 * N);
+    SDD_CK(cudaMemcpyAsync(buf.data(), p->x, N * 8, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(buf.data() + N, p->y, N * 8, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaMemcpyAsync(buf.data() + 2 * N, p->omega_nodal, N * 8, cudaMemcpyDeviceToHost, p->stream));
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(SDD_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    const int32_t rec = (int32_t)sizeof(sdd_params);
+    const int64_t step = p->step;
+    const int32_t kind = p->mon_kind, np = p->n_params;
+    bool ok = fwrite(kCkptMagic, 1, 8, f) == 8 && fwrite(&rec, 4, 1, f) == 1 &&
+              fwrite(&p->prm, sizeof(sdd_params), 1, f) == 1 && fwrite(&step, 8, 1, f) == 1 &&
+              fwrite(&kind, 4, 1, f) == 1 && fwrite(&np, 4, 1, f) == 1 &&
+              fwrite(p->mon_params, 8, 64, f) == 64 && fwrite(buf.data(), 8, 3 * N, f) == 3 * N;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) return fail(SDD_ERR_INVALID_ARG, std::string("short write to ") + path);
+    return SDD_OK;
+}
+
+sdd_status sdd_load(const char* path, void* stream, sdd_problem** out)
+{
+    if (!path || !out) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(SDD_ERR_INVALID_ARG, std::string("cannot read ") + path);
+    char magic[8];
+    int32_t rec = 0, kind = 0, np = 0;
+    int64_t step = 0;
+    sdd_params prm{};
+    double mp[64];
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kCkptMagic, 8) == 0 && fread(&rec, 4, 1, f) == 1 &&
+              rec == (int32_t)sizeof(sdd_params) && fread(&prm, sizeof(sdd_params), 1, f) == 1 &&
+              fread(&step, 8, 1, f) == 1 && fread(&kind, 4, 1, f) == 1 && fread(&np, 4, 1, f) == 1 &&
+              fread(mp, 8, 64, f) == 64;
+    std::vector<double> buf;
+    if (ok) ok = validate(&prm) == SDD_OK && step >= 0 && step < ((int64_t)1 << 32) && kind >= SDD_MONITOR_NODAL &&
+                 kind <= SDD_MONITOR_RINGS && np >= 0 && np <= 64;
+    if (ok) {
+        const size_t N = (size_t)prm.nx * prm.ny;
+        buf.resize(3 * N);
+        ok = fread(buf.data(), 8, 3 * N, f) == 3 * N && fgetc(f) == EOF;
+    }
+    fclose(f);
+    if (!ok) return fail(SDD_ERR_INVALID_ARG, std::string("not a valid checkpoint: ") + path);
+    const size_t N = (size_t)prm.nx * prm.ny;
+    sdd_problem* p = nullptr;
+    SDD_TRY(sdd_create_problem(&prm, buf.data(), buf.data() + N, stream, &p));
+    sdd_status s = SDD_OK;
+    if (kind == SDD_MONITOR_NODAL) s = sdd_set_monitor(p, buf.data() + 2 * N);
+    else s = sdd_set_monitor_analytic(p, kind, mp, np);
+    if (s == SDD_OK && cudaStreamSynchronize(p->stream) != cudaSuccess) s = fail(SDD_ERR_CUDA, "sync");
+    if (s != SDD_OK) {
+        delete p;
+        return s;
+    }
+    p->step = step;
+    p->stats.step_index = (int32_t)step;
+    p->stats.t = prm.t0 + (double)step * prm.dt;
+    *out = p;
     return SDD_OK;
 }
 

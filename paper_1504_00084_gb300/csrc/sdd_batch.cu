@@ -179,6 +179,8 @@ sdd_status record_step(sdd_batch* b)
         P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
         memcpy(P.params, p->mon_params, sizeof(P.params));
         P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
+        P.bad = p->bad;
+        B_CK(cudaMemsetAsync(p->bad, 0, 4, b->stream));
         B_CK(launch_prep(P, b->stream));
         launches += 2;
         if (p->M > 0) {
@@ -413,7 +415,11 @@ sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out)
             if (target > 0 && v > target) s.nodes_not_reached += 1;
         }
     }
+    int invalid = 0;
     for (sdd_problem* p : b->probs) {
+        int32_t flag = 0;
+        B_CK(cudaMemcpy(&flag, p->bad, 4, cudaMemcpyDeviceToHost));
+        invalid += flag ? 1 : 0;
         const int ns = p->prm.px * p->prm.py;
         std::vector<int32_t> it(ns), ou(ns);
         std::vector<double> rs(ns);
@@ -427,6 +433,7 @@ sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out)
         }
     }
     *out = s;
+    if (invalid) return sdd_fail(SDD_ERR_INVALID_ARG, "a problem's monitor is not finite and > 0 (or its mesh not finite)");
     return SDD_OK;
 }
 

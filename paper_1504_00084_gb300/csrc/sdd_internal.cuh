@@ -155,6 +155,7 @@ struct PrepParams {
     double* weta64;
     void* mon;                 // out: Mon4<T>
     void* disp;                // out: Disp2<T>
+    int32_t* bad;              // out (nullable): set to 1 if omega <= 0 or anything is not finite
 };
 
 struct SolveParams {

@@ -276,18 +276,17 @@ template <typename T>
 __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, uint32_t p, int k,
                                              T& xi, T& eta, T& vx, T& vy, int& side)
 {
+    // the monitor gather first: its loads are in flight while Philox runs
+    T wv, wx, we;
+    monitor_at(P, xi, eta, wv, wx, we);
     const U4 w = philox4x32_10(U4{(uint32_t)k, p, m, P.tstep}, P.key0, P.key1);
     const T u1 = uniform_open(w.x, T()), u2 = uniform_open(w.y, T()), ub = uniform_open(w.z, T());
-    const T r = dsqrt((T)-2 * dlog(u1));
+    const T lgu = dlog(u1);
     T sn, cs;
     if constexpr (sizeof(T) == 4)
         sincos_2pi(u2, &sn, &cs);  // FP32: polynomial form (below 0.75 ulp)
     else
         sincos(Consts<T>::two_pi * u2, &sn, &cs);
-    const T z1 = r * cs, z2 = r * sn;
-
-    T wv, wx, we;
-    monitor_at(P, xi, eta, wv, wx, we);
     T q, bx, by;  // q = D ds, (bx, by) = drift * ds
     if (P.form == 0) {
         q = wv * P.cb;
@@ -298,9 +297,12 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
         bx = wx / wv * P.cb;
         by = we / wv * P.cb;
     }
+    // Eq. 7: increment sqrt(2 q) z with the Box-Muller normals z = sqrt(-2 ln u1) (cos, sin)(2 pi u2),
+    // in the oracle's order of operations
+    const T r = dsqrt((T)-2 * lgu);
     const T sd = dsqrt(2 * q);
-    const T xn = xi + bx + sd * z1;
-    const T en = eta + by + sd * z2;
+    const T xn = xi + bx + sd * (r * cs);
+    const T en = eta + by + sd * (r * sn);
 
     if (!P.periodic) {
         // deepest violation of the unit square; ties keep the lower side index
@@ -463,24 +465,26 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
                 }
             }
         }
-        const unsigned sm = __ballot_sync(kFull, st == 2);
-        if (st == 2) {
-            const int pos = qn + __popc(sm & lt);
-            q_xi[pos] = xi;
-            q_eta[pos] = eta;
-            q_path[pos] = path;
-        }
-        qn += __popc(sm);
         const unsigned dm = __ballot_sync(kFull, st != 0);
-        if (st != 0) {
-            path = next + __popc(dm & lt);
-            live = path < pend;
-            xi = xi0;
-            eta = eta0;
-            k = 0;
+        if (dm) {  // some lane's path ended: queue survivors, hand out the next path indices
+            const unsigned sm = __ballot_sync(kFull, st == 2);
+            if (st == 2) {
+                const int pos = qn + __popc(sm & lt);
+                q_xi[pos] = xi;
+                q_eta[pos] = eta;
+                q_path[pos] = path;
+            }
+            qn += __popc(sm);
+            if (st != 0) {
+                path = next + __popc(dm & lt);
+                live = path < pend;
+                xi = xi0;
+                eta = eta0;
+                k = 0;
+            }
+            next += __popc(dm);
+            if (qn >= 32) drain(32);
         }
-        next += __popc(dm);
-        if (qn >= 32) drain(32);
     }
     if (qn > 0) drain(qn);
     double a, b, c, d;

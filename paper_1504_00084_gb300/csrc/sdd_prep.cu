@@ -122,6 +122,9 @@ __global__ void prep_pack_kernel(const PrepParams P)
         const double X = __dsub_rn(P.x[c], __dmul_rn(P.Lx, xi));
         const double Y = __dsub_rn(P.y[c], __dmul_rn(P.Ly, eta));
         disp[id] = Disp2<T>{(T)X, (T)Y};
+        // the monitor must be positive and everything finite (Sec. 2: omega > 0)
+        if (P.bad && !(w > 0.0 && isfinite(w) && isfinite(wx) && isfinite(we) && isfinite(X) && isfinite(Y)))
+            atomicOr(P.bad, 1);
     }
 }
 

@@ -46,8 +46,9 @@ struct sdd_problem {
     int32_t *st_iters = nullptr, *st_outer = nullptr, *st_ok = nullptr;
     double* st_res = nullptr;
     double* quality = nullptr;      // (nx-1)(ny-1) cell qualities + 2 stats
+    int32_t* bad = nullptr;         // set by the monitor preparation on invalid monitor or mesh
     // host
-    int32_t* h_n_active = nullptr;  // pinned
+    int32_t* h_n_active = nullptr;  // pinned: [0] active nodes, [1] invalid-input flag
     sdd_stats stats{};
     std::vector<void*> allocs;
     size_t dev_bytes = 0;          // device bytes held (allocation granularity included)

@@ -105,12 +105,14 @@ struct sdd_server {
     int2* slot_range = nullptr;
     int32_t* pending = nullptr;
     int32_t *range_off = nullptr, *range_pre = nullptr;  // planning order of the running ranges
+    int32_t* slot_bad = nullptr;     // per slot: invalid monitor or mesh found by the preparation
     void* records = nullptr;         // McProblem<T> per slot (device)
     // pinned host mirrors
     void* h_records = nullptr;
     int2* h_slot_range = nullptr;
     int32_t* h_pending = nullptr;    // [max_resident + 1]: pending per slot, then n_active
     int32_t *h_range_off = nullptr, *h_range_pre = nullptr;
+    int32_t* h_bad = nullptr;
     // host bookkeeping
     std::map<int64_t, int64_t> free_ranges;  // offset -> length
     std::vector<int> free_slots;
@@ -334,6 +336,8 @@ sdd_status admit(sdd_server* s, Request* r)
     P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
     memcpy(P.params, r->mon_params, sizeof(P.params));
     P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
+    P.bad = s->slot_bad + r->slot;
+    S_CK(cudaMemsetAsync(P.bad, 0, 4, s->stream));
     S_CK(launch_prep(P, s->stream));
     s->st.kernel_launches += 2;
     if (r->M > 0) {
@@ -476,9 +480,9 @@ sdd_status sdd_server_create(const sdd_server_params* params, void* stream, sdd_
     ALLOC(s->task_off, (M + 1) * 8); ALLOC(s->node_of, M * 4); ALLOC(s->n_active, 16);
     ALLOC(s->task_counter, 16); ALLOC(s->slots, M * kSlotsPerNode * sizeof(TaskSlot));
     ALLOC(s->slot_range, R * sizeof(int2)); ALLOC(s->pending, (R + 1) * 4); ALLOC(s->records, rec * R);
-    ALLOC(s->range_off, (R + 1) * 4); ALLOC(s->range_pre, (R + 1) * 4);
+    ALLOC(s->range_off, (R + 1) * 4); ALLOC(s->range_pre, (R + 1) * 4); ALLOC(s->slot_bad, R * 4);
     HALLOC(s->h_records, rec * R); HALLOC(s->h_slot_range, R * sizeof(int2)); HALLOC(s->h_pending, (R + 2) * 4);
-    HALLOC(s->h_range_off, (R + 1) * 4); HALLOC(s->h_range_pre, (R + 1) * 4);
+    HALLOC(s->h_range_off, (R + 1) * 4); HALLOC(s->h_range_pre, (R + 1) * 4); HALLOC(s->h_bad, R * 4);
 #undef ALLOC
 #undef HALLOC
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->up, cudaStreamNonBlocking);
@@ -628,6 +632,7 @@ sdd_status sdd_server_progress(sdd_server* s, int32_t* n_running, int32_t* n_que
             S_CK(cudaMemcpyAsync(s->h_pending + R, s->n_active, 4, cudaMemcpyDeviceToHost, s->stream));
             s->st.kernel_launches += 2;
         }
+        S_CK(cudaMemcpyAsync(s->h_bad, s->slot_bad, (size_t)R * 4, cudaMemcpyDeviceToHost, s->stream));
         S_CK(cudaStreamSynchronize(s->stream));
         if (s->round_timed) {
             float ms = 0.f;
@@ -636,9 +641,16 @@ sdd_status sdd_server_progress(sdd_server* s, int32_t* n_running, int32_t* n_que
             s->round_timed = false;
         }
         const int n_active = hw > 0 ? s->h_pending[R] : 0;
-        // 4. finish requests whose nodes are all done
+        // 4. finish requests whose nodes are all done; drop requests with invalid input (their
+        //    nodes leave the plan; a round already launched may still sample them)
         for (auto it = s->running.begin(); it != s->running.end();) {
             Request* r = *it;
+            if (s->h_bad[r->slot]) {
+                r->status = SDD_ERR_INVALID_ARG;
+                complete(s, r);
+                it = s->running.erase(it);
+                continue;
+            }
             if (r->M > 0 && s->h_pending[r->slot] > 0) {
                 r->rounds += 1;
                 ++it;
@@ -680,7 +692,9 @@ sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, do
     Request* r = it->second;
     if (r->state != kDone) return sdd_fail(SDD_ERR_INVALID_ARG, "request not completed");
     sdd_status status = r->status;
-    if (r->p) {
+    if (r->p && status == SDD_ERR_INVALID_ARG) {
+        if (st) *st = sdd_stats{};
+    } else if (r->p) {
         sdd_problem* p = r->p;
         const size_t N = (size_t)r->prm.nx * r->prm.ny;
         const int64_t o = r->off;
@@ -727,6 +741,11 @@ sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, do
         if (st) *st = o_;
         if (o_.nodes_not_reached) status = SDD_ERR_SE_NOT_REACHED;
         else if (bad) status = SDD_ERR_NOT_CONVERGED;
+    } else if (st) {
+        *st = sdd_stats{};
+    }
+    if (r->p) {
+        sdd_problem* p = r->p;
         // release: state to the shape cache, pool range, slot
         s->h_slot_range[r->slot] = int2{0, 0};
         S_CK(cudaMemcpyAsync(s->slot_range + r->slot, s->h_slot_range + r->slot, sizeof(int2),
@@ -735,8 +754,6 @@ sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, do
         s->free_slots.push_back(r->slot);
         release_problem(s, p);
         r->p = nullptr;
-    } else if (st) {
-        *st = sdd_stats{};
     }
     if (r->up_ev) cudaEventDestroy(r->up_ev);
     if (r->done_ev) cudaEventDestroy(r->done_ev);
@@ -744,6 +761,7 @@ sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, do
     delete r;
     s->st.collected += 1;
     if (status == SDD_ERR_OOM) return sdd_fail(SDD_ERR_OOM, "request state does not fit the memory budget");
+    if (status == SDD_ERR_INVALID_ARG) return sdd_fail(status, "monitor must be finite and > 0, mesh finite");
     if (status == SDD_ERR_SE_NOT_REACHED) return sdd_fail(status, "max_paths_per_node reached before se_target");
     if (status == SDD_ERR_NOT_CONVERGED) return sdd_fail(status, "a subdomain solve reached solve_max_iter");
     return status;

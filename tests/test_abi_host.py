@@ -91,3 +91,19 @@ def test_adaptive_cap_validated(sdd):
 def test_status_strings(sdd):
     for s in range(7):
         assert len(sdd.lib.sdd_status_string(s)) > 0
+
+
+def test_checkpoint_load_rejects_bad_files_before_device_work(sdd, tmp_path):
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "none.ckpt").encode()
+    assert sdd.lib.sdd_load(missing, None, ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"NOTACKPT" + bytes(100))
+    assert sdd.lib.sdd_load(str(bad).encode(), None, ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
+    # right magic and record size, parameters that fail validation
+    p = sdd.SddParams()
+    body = b"SDDCKPT1" + ctypes.sizeof(p).to_bytes(4, "little") + bytes(p)
+    short = tmp_path / "short.ckpt"
+    short.write_bytes(body + bytes(8))
+    assert sdd.lib.sdd_load(str(short).encode(), None, ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
+    assert sdd.lib.sdd_save(None, str(short).encode()) == sdd.SDD_ERR_INVALID_ARG
