@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--paths", type=int, default=100000)
     ap.add_argument("--max-paths", type=int, default=1 << 25)
     ap.add_argument("--periodic", type=int, default=0)
+    ap.add_argument("--iface-stride", type=int, default=0,
+                    help="Monte Carlo at every k-th interface node, the rest interpolated (0: all)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -83,7 +85,8 @@ def workload(args, rank=0):
     prec = {"fp32": W.PREC_FP32_ACC64, "fp64": W.PREC_FP64, "kahan": W.PREC_FP32_KAHAN}[args.precision]
     p = W.c1_front(prec, periodic=args.periodic)
     return p.replace(se_target=args.se_target, paths_per_node=args.paths,
-                     max_paths_per_node=max(args.max_paths, args.paths), seed=p.seed + rank)
+                     max_paths_per_node=max(args.max_paths, args.paths), seed=p.seed + rank,
+                     iface_stride=args.iface_stride)
 
 
 def config_of(p, M):
@@ -93,7 +96,8 @@ def config_of(p, M):
             "periodic": p.periodic, "se_target": p.se_target, "paths_first_chunk": p.paths_per_node,
             "max_paths_per_node": p.max_paths_per_node, "substeps": p.substeps, "tau": p.tau, "dt": p.dt,
             "path_precision": {0: "fp64", 1: "fp32 (fp64 sums)", 2: "fp32 (kahan fp32 sums)"}[p.precision],
-            "l2": "256 MiB buffer written between timed steps (inputs are ~1 MB)"}
+            "l2": "256 MiB buffer written between timed steps (inputs are ~1 MB)",
+            **({"iface_stride": p.iface_stride} if p.iface_stride > 1 else {})}
 
 
 def reduce_over_ranks(dist, T, path_steps, estimates, device):

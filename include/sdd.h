@@ -81,7 +81,13 @@ typedef struct {
     int32_t bb_test;         /* 1: Brownian-bridge crossing test between substeps (Sec. 3.4)       */
     int32_t substeps;        /* K in [1, 2^20]: Euler-Maruyama substeps per step, ds = dt / K (Eq. 7) */
     int32_t solve_max_iter;  /* PCG iteration cap per subdomain solve, >= 1                       */
-    int32_t reserved0;       /* must be 0                                                          */
+    int32_t iface_stride;    /* 0 or 1: Monte Carlo at every interface node; k in [2, 2^16]: at
+                                every k-th node of each interface line (index along the line a
+                                multiple of k) and at line crossings, the other nodes linearly
+                                interpolated along their line between the nearest sampled nodes
+                                or the line's end (Sec. 3.6: "a sample can be evaluated with the
+                                rest obtained by interpolation").  Sampled nodes keep their node
+                                ids, so their estimates equal those of k = 1.                  */
     double Lx, Ly;           /* physical rectangle [0, Lx] x [0, Ly], > 0                           */
     double tau;              /* relaxation time of the generator, > 0                              */
     double dt;               /* mesh time step, > 0                                                */
@@ -166,6 +172,16 @@ sdd_status sdd_subdomain_solve(sdd_problem* p, const double* iface_xy, double* x
  * step. */
 sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out);
 
+/* M^kP step (Sec. 5): t^n -> t^{n+1} as K mesh sub-steps of dt/K.  Before each sub-step the
+ * monitor is evaluated on the current sub-mesh at the time t^n of the step (analytic kinds; the
+ * paper interpolates rho^n onto the sub-mesh, the analytic monitor is evaluated there exactly;
+ * nodal values stay with their nodes), then interface MC and subdomain solves with dt/K.
+ * Sub-step k of step n uses n K + k as the fourth Philox counter word, so K = 1 is sdd_step.
+ * K in [1, 2^16] with (n + 1) K <= 2^32.  Counters (sdd_get_stats) sum over the sub-steps.  On
+ * an error other than SDD_ERR_SE_NOT_REACHED / SDD_ERR_NOT_CONVERGED the problem keeps the last
+ * completed sub-mesh and the step index n. */
+sdd_status sdd_step_mkp(sdd_problem* p, int32_t K, double* x_out, double* y_out);
+
 /* Counters of the last calls (see sdd_stats). */
 sdd_status sdd_get_stats(const sdd_problem* p, sdd_stats* out);
 
@@ -179,6 +195,11 @@ sdd_status sdd_get_interface_nodes(const sdd_problem* p, int32_t* ij, int32_t* M
  * periodic lines: I = 0..px-1, j = 0..ny-2.  ij may be NULL to query *M.  Sec. 3.1, 3.5. */
 sdd_status sdd_interface_layout(int32_t nx, int32_t ny, int32_t px, int32_t py, int32_t periodic,
                                 int32_t* ij, int32_t* M);
+
+/* Host-only (no GPU needed): which interface nodes params->iface_stride leaves to Monte Carlo:
+ * sampled (M int32, node-id order, nullable) receives 1 for a sampled node and 0 for an
+ * interpolated one; *M the node count.  Validates params as sdd_create_problem does. */
+sdd_status sdd_interface_sampling(const sdd_params* params, int32_t* sampled, int32_t* M);
 
 /* Host-only: adaptive path total of a node after n_done paths with standard error se
  * (max of both components): n_done when se <= target or n_done >= max_paths, else

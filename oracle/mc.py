@@ -128,12 +128,34 @@ def interface_mc(prob, x, y, omega, nodes, tstep: int, real=np.float64):
     Fixed N (prob.se_target == 0): paths 0..N-1 of every node.  Adaptive (se_target > 0):
     every node starts with N = prob.paths_per_node paths and draws further chunks, path
     indices continuing, until max(SE_x, SE_y) <= se_target or max_paths_per_node is reached.
+    With prob.iface_stride > 1 only the sampled nodes of oracle.layout.interface_sampling are
+    estimated (with their own node ids) and the others are interpolated along their lines;
+    their se, n_used and steps are 0.
     Returns (est (M,2), se (M,2), n_used (M,), steps (M,)).
     """
-    inp = prepare(prob, x, y, omega, tstep, real)
+    stride = int(getattr(prob, "iface_stride", 0))
+    if stride > 1:
+        from .layout import interface_sampling
+        sampled, fill = interface_sampling(prob.nx, prob.ny, prob.px, prob.py, prob.periodic, stride,
+                                           prob.Lx, prob.Ly)
+        nodes = np.asarray(nodes, dtype=np.int32)
+        sub = _interface_mc_ids(prob, x, y, omega, nodes, np.nonzero(sampled)[0].astype(np.int32), tstep, real)
+        M = len(nodes)
+        est = np.full((M, 2), np.nan)
+        se = np.zeros((M, 2))
+        n_used = np.zeros(M, dtype=np.int64)
+        steps = np.zeros(M, dtype=np.int64)
+        est[sampled], se[sampled], n_used[sampled], steps[sampled] = sub
+        return fill(est), se, n_used, steps
     nodes = np.asarray(nodes, dtype=np.int32)
+    return _interface_mc_ids(prob, x, y, omega, nodes, np.arange(len(nodes), dtype=np.int32), tstep, real)
+
+
+def _interface_mc_ids(prob, x, y, omega, all_nodes, ids, tstep, real):
+    """interface_mc over the nodes all_nodes[ids], each with its own node id in the counter."""
+    inp = prepare(prob, x, y, omega, tstep, real)
+    nodes = all_nodes[ids]
     M = len(nodes)
-    ids = np.arange(M, dtype=np.int32)
     shift = np.stack([x[nodes[:, 1], nodes[:, 0]], y[nodes[:, 1], nodes[:, 0]]], axis=1)
     n0 = int(prob.paths_per_node)
     sums, steps = interface_sums(inp, ids, nodes, np.zeros(M, np.int64), np.full(M, n0, np.int64),

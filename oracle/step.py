@@ -78,3 +78,16 @@ def step(prob, x, y, t, tstep, omega_nodal=None, real=np.float64):
     xn1, yn1 = subdomain_solves(prob, omega, bx, by, x, y)
     return dict(x=xn1, y=yn1, est=est, se=se, n_used=n_used, steps=steps, omega=omega,
                 nodes=nodes)
+
+
+def mkp_step(prob, x, y, t, tstep, K, omega_nodal=None, real=np.float64):
+    """M^kP step (Sec. 5): x^n -> x^{n+1} through K sub-meshes, each a step of dt/K with the
+    monitor evaluated on the current sub-mesh at the step's time t (the analytic monitor at the
+    sub-mesh positions in place of the paper's interpolant of rho^n); sub-step k uses the
+    counter word tstep K + k.  Returns the last sub-step's dict (new mesh in x, y)."""
+    sub = prob.replace(dt=prob.dt / K)
+    r = None
+    for k in range(K):
+        r = step(sub, x, y, t, tstep * K + k, omega_nodal, real)
+        x, y = r["x"], r["y"]
+    return r

@@ -35,7 +35,7 @@ class SddParams(ctypes.Structure):
                 ("py", ctypes.c_int32), ("periodic", ctypes.c_int32), ("form", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("bicubic", ctypes.c_int32), ("bb_test", ctypes.c_int32),
                 ("substeps", ctypes.c_int32), ("solve_max_iter", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("iface_stride", ctypes.c_int32), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
                 ("tau", ctypes.c_double), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("paths_per_node", ctypes.c_int64), ("max_paths_per_node", ctypes.c_int64),
                 ("se_target", ctypes.c_double), ("solve_rtol", ctypes.c_double), ("t0", ctypes.c_double)]
@@ -84,7 +84,7 @@ EXPORTS = [
     "sdd_mesh_quality",
     "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
     "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
-    "sdd_save", "sdd_load",
+    "sdd_save", "sdd_load", "sdd_interface_sampling", "sdd_step_mkp",
 ]
 
 
@@ -127,6 +127,8 @@ def _load():
         "sdd_server_get_stats": ([P, ctypes.POINTER(SddServerStats)], I32),
         "sdd_server_destroy": ([P], None),
         "sdd_save": ([P, ctypes.c_char_p], I32),
+        "sdd_step_mkp": ([P, I32, P, P], I32),
+        "sdd_interface_sampling": ([ctypes.POINTER(SddParams), P, ctypes.POINTER(I32)], I32),
         "sdd_load": ([ctypes.c_char_p, P, ctypes.POINTER(P)], I32),
         "sdd_status_string": ([I32], ctypes.c_char_p),
         "sdd_last_error": ([], ctypes.c_char_p),
@@ -182,8 +184,6 @@ def params_from(prob, **overrides) -> SddParams:
     """sdd_params from a workloads.Problem-like object (attributes of the same names)."""
     p = SddParams()
     for name, _ in SddParams._fields_:
-        if name == "reserved0":
-            continue
         if hasattr(prob, name):
             setattr(p, name, getattr(prob, name))
     if getattr(prob, "max_paths_per_node", 0) <= 0:
@@ -245,6 +245,11 @@ def sdd_step(h: int, x_out=None, y_out=None, allow_se_not_reached=True) -> int:
     return _check(lib.sdd_step(h, _ptr(x_out), _ptr(y_out)), "sdd_step", ok)
 
 
+def sdd_step_mkp(h: int, K: int, x_out=None, y_out=None, allow_se_not_reached=True) -> int:
+    ok = (SDD_OK, SDD_ERR_NOT_CONVERGED) + ((SDD_ERR_SE_NOT_REACHED,) if allow_se_not_reached else ())
+    return _check(lib.sdd_step_mkp(h, K, _ptr(x_out), _ptr(y_out)), "sdd_step_mkp", ok=ok)
+
+
 def sdd_get_stats(h: int) -> dict:
     s = SddStats()
     _check(lib.sdd_get_stats(h, ctypes.byref(s)), "sdd_get_stats")
@@ -268,6 +273,16 @@ def sdd_interface_layout(nx: int, ny: int, px: int, py: int, periodic: int) -> n
         _check(lib.sdd_interface_layout(nx, ny, px, py, periodic, ij.ctypes.data, ctypes.byref(M)),
                "sdd_interface_layout")
     return ij
+
+
+def sdd_interface_sampling(params: SddParams) -> np.ndarray:
+    """bool array over the interface nodes: True where Monte Carlo runs (params.iface_stride)."""
+    M = ctypes.c_int32()
+    _check(lib.sdd_interface_sampling(ctypes.byref(params), None, ctypes.byref(M)), "sdd_interface_sampling")
+    out = np.zeros(max(M.value, 1), dtype=np.int32)
+    _check(lib.sdd_interface_sampling(ctypes.byref(params), out.ctypes.data, ctypes.byref(M)),
+           "sdd_interface_sampling")
+    return out[:M.value].astype(bool)
 
 
 def sdd_adaptive_next_total(n_done: int, se: float, target: float, max_paths: int) -> int:
@@ -367,6 +382,12 @@ class SddProblem:
         x = np.zeros((self.ny, self.nx))
         y = np.zeros((self.ny, self.nx))
         status = sdd_step(self.h, x, y)
+        return x, y, status
+
+    def step_mkp(self, K: int):
+        x = np.zeros((self.ny, self.nx))
+        y = np.zeros((self.ny, self.nx))
+        status = sdd_step_mkp(self.h, K, x, y)
         return x, y, status
 
     def mesh(self):

@@ -76,6 +76,65 @@ void layout(int nx, int ny, int px, int py, int periodic, std::vector<int32_t>& 
             if (!on_v[i]) { ij.push_back(i); ij.push_back(j); }
 }
 
+// Interface sampling (Sec. 3.6): along every interface line the nodes whose index along the line
+// is a multiple of k, and the crossings with lines of the other direction, are estimated; every
+// other node is the linear interpolation, in its index along the line, between the nearest
+// sampled positions on either side, where a line's end stands for a sample: the identity
+// boundary node on a Dirichlet domain, the line's first node one period on when periodic.
+void sampling_table(const sdd_params& q, const std::vector<int32_t>& ij, std::vector<int32_t>& role,
+                    std::vector<InterpRule>& rules)
+{
+    const int M = (int)(ij.size() / 2);
+    role.assign(M, -1);
+    rules.clear();
+    const int k = q.iface_stride;
+    if (k <= 1 || M == 0) return;
+    const int nx = q.nx, ny = q.ny, sx = (nx - 1) / q.px, sy = (ny - 1) / q.py;
+    std::vector<int32_t> id((size_t)nx * ny, -1);
+    for (int m = 0; m < M; ++m) id[(size_t)ij[2 * m + 1] * nx + ij[2 * m]] = m;
+    std::vector<char> is_vl(nx, 0), is_hl(ny, 0);
+    std::vector<int> vl, hl;
+    for (int I = q.periodic ? 0 : 1; I < q.px; ++I) { vl.push_back(I * sx); is_vl[I * sx] = 1; }
+    for (int J = q.periodic ? 0 : 1; J < q.py; ++J) { hl.push_back(J * sy); is_hl[J * sy] = 1; }
+    struct Anchor { int t; int32_t node; double ox, oy; };
+    auto line = [&](bool vertical, int c) {
+        const int L = vertical ? ny - 1 : nx - 1;
+        std::vector<Anchor> an;
+        for (int t = 0; t <= L; ++t) {
+            const int i = vertical ? c : t, j = vertical ? t : c;
+            const bool end = t == 0 || t == L;
+            if (end && !q.periodic) {
+                an.push_back({t, -1, q.Lx * ((double)i / (double)(nx - 1)), q.Ly * ((double)j / (double)(ny - 1))});
+            } else if (end && t == L) {
+                const int32_t first = vertical ? id[(size_t)c] : id[(size_t)c * nx];
+                an.push_back({t, first, vertical ? 0.0 : q.Lx, vertical ? q.Ly : 0.0});
+            } else if (t % k == 0 || (vertical ? is_hl[j] : is_vl[i])) {
+                an.push_back({t, id[(size_t)j * nx + i], 0.0, 0.0});
+            }
+        }
+        size_t a = 0;
+        for (int t = 1; t < L; ++t) {
+            while (a + 1 < an.size() && an[a + 1].t <= t) ++a;
+            if (an[a].t == t) continue;  // sampled
+            const int i = vertical ? c : t, j = vertical ? t : c;
+            const int32_t m = id[(size_t)j * nx + i];
+            if (m < 0) continue;
+            const Anchor& A0 = an[a];
+            const Anchor& B0 = an[a + 1];
+            InterpRule r{};
+            r.m = m;
+            r.a = A0.node;
+            r.b = B0.node;
+            r.w = (double)(B0.t - t) / (double)(B0.t - A0.t);
+            r.oax = A0.ox; r.oay = A0.oy; r.obx = B0.ox; r.oby = B0.oy;
+            role[m] = (int32_t)rules.size();
+            rules.push_back(r);
+        }
+    };
+    for (int i : vl) line(true, i);
+    for (int j : hl) line(false, j);
+}
+
 bool is_device_ptr(const void* ptr)
 {
     cudaPointerAttributes a;
@@ -106,7 +165,7 @@ sdd_status validate(const sdd_params* P)
     if (P->bb_test != 0 && P->bb_test != 1) return fail(SDD_ERR_INVALID_ARG, "bb_test must be 0 or 1");
     if (P->substeps < 1 || P->substeps > (1 << 20)) return fail(SDD_ERR_INVALID_ARG, "substeps must be in [1, 2^20]");
     if (P->solve_max_iter < 1) return fail(SDD_ERR_INVALID_ARG, "solve_max_iter must be >= 1");
-    if (P->reserved0 != 0) return fail(SDD_ERR_INVALID_ARG, "reserved0 must be 0");
+    if (P->iface_stride < 0 || P->iface_stride > (1 << 16)) return fail(SDD_ERR_INVALID_ARG, "iface_stride must be in [0, 2^16]");
     if (!(P->Lx > 0) || !(P->Ly > 0) || !(P->tau > 0) || !(P->dt > 0))
         return fail(SDD_ERR_INVALID_ARG, "Lx, Ly, tau, dt must be > 0");
     if (!isfinite(P->Lx) || !isfinite(P->Ly) || !isfinite(P->tau) || !isfinite(P->dt) || !isfinite(P->t0))
@@ -157,7 +216,7 @@ sdd_status run_prep(sdd_problem* p)
     P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic;
     P.kind = p->mon_kind; P.n_params = p->n_params; P.precision = p->prm.precision;
     P.Lx = p->prm.Lx; P.Ly = p->prm.Ly;
-    P.t = p->prm.t0 + (double)p->step * p->prm.dt;
+    P.t = p->monitor_time_fixed ? p->t_monitor : p->prm.t0 + (double)p->step * p->prm.dt;
     P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
     memcpy(P.params, p->mon_params, sizeof(P.params));
     P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64;
@@ -233,7 +292,8 @@ sdd_status run_mc(sdd_problem* p)
     const bool adaptive = p->prm.se_target > 0;
     const int64_t n0 = p->prm.paths_per_node;
     const int64_t maxp = adaptive ? p->prm.max_paths_per_node : n0;
-    SDD_CK(launch_mc_init(M, n0, maxp, p->acc, p->n_done, p->steps, p->paths_run, p->next_total, p->stream));
+    SDD_CK(launch_mc_init(M, n0, maxp, p->acc, p->n_done, p->steps, p->paths_run, p->next_total, p->stream,
+                          p->n_interp > 0 ? p->iface_role : nullptr));
     p->launches += 1;
     int n_timed = 0;
     PlanParams PP{};
@@ -272,6 +332,10 @@ sdd_status run_mc(sdd_problem* p)
     }
     SDD_CK(launch_output(M, p->acc, p->n_done, p->shift, p->est, p->se, p->stream));
     p->launches += 1;
+    if (p->n_interp > 0) {
+        SDD_CK(launch_interp(p->interp, p->n_interp, p->est, p->se, p->stream));
+        p->launches += 1;
+    }
     // counters (small copies)
     std::vector<int64_t> st(M), np(M);
     std::vector<double> se((size_t)2 * M);
@@ -357,6 +421,8 @@ void problem_arrays(sdd_problem* p, bool with_mc, F&& f)
     f((void**)&p->omega_nodal, N * 8);
     f((void**)&p->mon, N * 4 * rs); f((void**)&p->disp, N * 2 * rs);
     f((void**)&p->nodes, (M + 1) * sizeof(int2));
+    f((void**)&p->iface_role, (M + 1) * 4);
+    f((void**)&p->interp, (size_t)(p->n_interp > 0 ? p->n_interp : 1) * sizeof(InterpRule));
     if (with_mc) {
         f((void**)&p->shift, (M + 1) * 16);
         f((void**)&p->acc, (M + 1) * 32); f((void**)&p->n_done, (M + 1) * 8); f((void**)&p->steps, (M + 1) * 8);
@@ -385,6 +451,8 @@ sdd_problem* problem_shell(const sdd_params& prm, cudaStream_t stream)
     p->acc_mode = prm.precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
     layout(prm.nx, prm.ny, prm.px, prm.py, prm.periodic, p->ij);
     p->M = (int)(p->ij.size() / 2);
+    sampling_table(prm, p->ij, p->h_role, p->h_interp);
+    p->n_interp = (int)p->h_interp.size();
     p->slot_cap = (int64_t)(p->M > 0 ? p->M : 1) * kSlotsPerNode;
     const size_t rs = p->fp64 ? 8 : 4;
     p->mg_stride = mg_bytes((prm.nx - 1) / prm.px - 1, (prm.ny - 1) / prm.py - 1, rs);
@@ -434,6 +502,11 @@ sdd_status sdd_alloc_problem(const sdd_params& prm, cudaStream_t stream, bool wi
     e = cudaMemsetAsync(p->vec, 0, N * 4 * 2 * rs, p->stream);
     if (e == cudaSuccess && p->M > 0)
         e = cudaMemcpyAsync(p->nodes, p->ij.data(), (size_t)p->M * sizeof(int2), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && p->M > 0)
+        e = cudaMemcpyAsync(p->iface_role, p->h_role.data(), (size_t)p->M * 4, cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && p->n_interp > 0)
+        e = cudaMemcpyAsync(p->interp, p->h_interp.data(), (size_t)p->n_interp * sizeof(InterpRule),
+                            cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // p->ij is pageable host memory
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -495,6 +568,20 @@ sdd_status sdd_interface_layout(int32_t nx, int32_t ny, int32_t px, int32_t py, 
     layout(nx, ny, px, py, periodic, v);
     *M = (int32_t)(v.size() / 2);
     if (ij && !v.empty()) memcpy(ij, v.data(), v.size() * sizeof(int32_t));
+    return SDD_OK;
+}
+
+sdd_status sdd_interface_sampling(const sdd_params* params, int32_t* sampled, int32_t* M)
+{
+    if (!M) return fail(SDD_ERR_INVALID_ARG, "M is NULL");
+    SDD_TRY(validate(params));
+    std::vector<int32_t> ij, role;
+    std::vector<InterpRule> rules;
+    layout(params->nx, params->ny, params->px, params->py, params->periodic, ij);
+    sampling_table(*params, ij, role, rules);
+    *M = (int32_t)role.size();
+    if (sampled)
+        for (size_t m = 0; m < role.size(); ++m) sampled[m] = role[m] < 0 ? 1 : 0;
     return SDD_OK;
 }
 
@@ -654,6 +741,73 @@ sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out)
     SDD_TRY(copy_out(p, y_out, p->y, N * 8));
     if (s_mc != SDD_OK) return fail(s_mc, "max_paths_per_node reached before se_target");
     return s_sv;
+}
+
+sdd_status sdd_step_mkp(sdd_problem* p, int32_t K, double* x_out, double* y_out)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    if (K < 1 || K > (1 << 16)) return fail(SDD_ERR_INVALID_ARG, "K must be in [1, 2^16]");
+    const int64_t n = p->step;
+    if ((n + 1) * (int64_t)K > ((int64_t)1 << 32))
+        return fail(SDD_ERR_INVALID_ARG, "time-step word n K + k exceeds 32 bits");
+    const sdd_params saved = p->prm;
+    p->prm.dt = saved.dt / (double)K;
+    p->t_monitor = saved.t0 + (double)n * saved.dt;
+    p->monitor_time_fixed = true;
+    sdd_status hard = SDD_OK, soft = SDD_OK;
+    sdd_stats acc{};
+    int k = 0;
+    for (; k < K; ++k) {
+        p->step = n * K + k;
+        hard = run_prep(p);
+        if (hard != SDD_OK) break;
+        const sdd_status s_mc = run_mc(p);
+        if (s_mc != SDD_OK && s_mc != SDD_ERR_SE_NOT_REACHED) { hard = s_mc; break; }
+        const sdd_status s_sv = run_solve(p);
+        if (s_sv != SDD_OK && s_sv != SDD_ERR_NOT_CONVERGED) { hard = s_sv; break; }
+        if (soft == SDD_OK) soft = s_mc != SDD_OK ? s_mc : s_sv;
+        double* t;
+        t = p->x; p->x = p->xn; p->xn = t;
+        t = p->y; p->y = p->yn; p->yn = t;
+        acc.path_steps += p->stats.path_steps;
+        acc.paths += p->stats.paths;
+        acc.mc_rounds += p->stats.mc_rounds;
+        acc.mc_kernel_ms += p->stats.mc_kernel_ms;
+        acc.mc_kernel_launches += p->stats.mc_kernel_launches;
+        acc.nodes_not_reached += p->stats.nodes_not_reached;
+        if (p->stats.max_se > acc.max_se) acc.max_se = p->stats.max_se;
+        if (p->stats.solve_iters_max > acc.solve_iters_max) acc.solve_iters_max = p->stats.solve_iters_max;
+        if (p->stats.solve_outer_max > acc.solve_outer_max) acc.solve_outer_max = p->stats.solve_outer_max;
+        if (p->stats.solve_rel_residual > acc.solve_rel_residual) acc.solve_rel_residual = p->stats.solve_rel_residual;
+    }
+    p->prm = saved;
+    p->monitor_time_fixed = false;
+    p->have_est = false;
+    if (hard != SDD_OK) {
+        // the mesh is the last completed sub-mesh; the step index stays n
+        p->step = n;
+        p->stats.step_index = (int32_t)n;
+        return hard;
+    }
+    p->step = n + 1;
+    p->stats.path_steps = acc.path_steps;
+    p->stats.paths = acc.paths;
+    p->stats.mc_rounds = acc.mc_rounds;
+    p->stats.mc_kernel_ms = acc.mc_kernel_ms;
+    p->stats.mc_kernel_launches = acc.mc_kernel_launches;
+    p->stats.nodes_not_reached = acc.nodes_not_reached;
+    p->stats.max_se = acc.max_se;
+    p->stats.solve_iters_max = acc.solve_iters_max;
+    p->stats.solve_outer_max = acc.solve_outer_max;
+    p->stats.solve_rel_residual = acc.solve_rel_residual;
+    p->stats.step_index = (int32_t)p->step;
+    p->stats.t = p->prm.t0 + (double)p->step * p->prm.dt;
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_out(p, x_out, p->x, N * 8));
+    SDD_TRY(copy_out(p, y_out, p->y, N * 8));
+    if (soft == SDD_ERR_SE_NOT_REACHED) return fail(soft, "max_paths_per_node reached before se_target");
+    if (soft == SDD_ERR_NOT_CONVERGED) return fail(soft, "a subdomain solve reached solve_max_iter");
+    return SDD_OK;
 }
 
 sdd_status sdd_get_stats(const sdd_problem* p, sdd_stats* out)

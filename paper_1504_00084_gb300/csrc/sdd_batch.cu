@@ -48,6 +48,7 @@ struct sdd_batch {
     int mc_grid = 1;
     // device: concatenated node arrays and round plan
     int32_t* node_prob = nullptr;
+    int32_t* node_role = nullptr;    // concatenated sampling roles (null: every node by Monte Carlo)
     double *shift = nullptr, *acc = nullptr, *est = nullptr, *se = nullptr;
     int64_t *n_done = nullptr, *steps = nullptr, *paths_run = nullptr, *next_total = nullptr;
     int64_t *p_begin = nullptr, *p_count = nullptr, *task_off = nullptr;
@@ -195,7 +196,7 @@ sdd_status record_step(sdd_batch* b)
         const int64_t n0 = q.paths_per_node;
         const int64_t maxp = adaptive ? q.max_paths_per_node : n0;
         B_CK(launch_mc_init(b->M, n0, maxp, b->acc, b->n_done, b->steps, b->paths_run, b->next_total,
-                            b->stream));
+                            b->stream, b->node_role));
         launches += 1;
         PlanParams PP{};
         PP.M = b->M; PP.n_done = b->n_done; PP.next_total = b->next_total; PP.node_of = b->node_of;
@@ -234,6 +235,13 @@ sdd_status record_step(sdd_batch* b)
         b->rounds_last = rounds;
         B_CK(launch_output(b->M, b->acc, b->n_done, b->shift, b->est, b->se, b->stream));
         launches += 1;
+        for (int i = 0; i < b->n; ++i) {
+            sdd_problem* p = b->probs[i];
+            if (p->n_interp == 0) continue;
+            const size_t o = (size_t)b->node_off[i];
+            B_CK(launch_interp(p->interp, p->n_interp, b->est + 2 * o, b->se + 2 * o, b->stream));
+            launches += 1;
+        }
     }
     const bool fp64_inner = b->fp64;
     for (int i = 0; i < b->n; ++i) {
@@ -288,12 +296,15 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     b->fp64 = q.precision == SDD_FP64;
     b->acc_mode = q.precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
     b->use_graph = use_graph != 0;
-    std::vector<int32_t> node_prob;
+    std::vector<int32_t> node_prob, node_role;
+    bool sampled_any = false;
     b->sub_off.push_back(0);
     for (int i = 0; i < n; ++i) {
         b->node_off.push_back(b->M);
         b->M += problems[i]->M;
         node_prob.insert(node_prob.end(), problems[i]->M, i);
+        node_role.insert(node_role.end(), problems[i]->h_role.begin(), problems[i]->h_role.end());
+        sampled_any = sampled_any || problems[i]->n_interp > 0;
         b->total_subs += problems[i]->prm.px * problems[i]->prm.py;
         b->sub_off.push_back(b->total_subs);
     }
@@ -309,6 +320,7 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     ALLOC(b->task_counter, 16); ALLOC(b->slots, M * kSlotsPerNode * sizeof(TaskSlot));
     ALLOC(b->mcprob_dev, rec * n); ALLOC(b->solve_dev, sizeof(SolveParams) * n); ALLOC(b->t_dev, 8 * n);
     ALLOC(b->sub_off_dev, 4 * (n + 1));
+    if (sampled_any) ALLOC(b->node_role, M * 4);
     HALLOC(b->mcprob_host, rec * n); HALLOC(b->solve_host, sizeof(SolveParams) * n); HALLOC(b->t_host, 8 * n);
     HALLOC(b->h_n_active, 16);
 #undef ALLOC
@@ -319,6 +331,8 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
         e = cudaMemcpy(b->node_prob, node_prob.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->sub_off_dev, b->sub_off.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && sampled_any && b->M > 0)
+        e = cudaMemcpy(b->node_role, node_role.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         cudaGetLastError();
         const std::string m = std::string("batch allocation failed: ") + cudaGetErrorString(e);

@@ -208,6 +208,14 @@ __host__ __device__ inline size_t mg_bytes(int n, int m, size_t real_bytes)
     return total;
 }
 
+// Interpolated interface node (interface sampling, Sec. 3.6): est[m] = w va + (1 - w) vb with
+// v = (node >= 0 ? est[node] : 0) + offset for each of the two anchors a, b.
+struct InterpRule {
+    int32_t m, a, b, pad;
+    double w;
+    double oax, oay, obx, oby;
+};
+
 // Launchers (return cudaGetLastError of the launch).
 cudaError_t launch_prep(const PrepParams& P, cudaStream_t s);
 cudaError_t launch_quality(int nx, int ny, const double* x, const double* y, double* q, double* stats,
@@ -216,8 +224,11 @@ cudaError_t launch_shift(const int2* nodes, int M, int nx, const double* x, cons
                          double* shift, cudaStream_t s);
 cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, const int2* nodes,
                            int M, const double* est, double* xnew, double* ynew, cudaStream_t s);
+// role (nullable): per node, -1 = estimated by Monte Carlo, >= 0 = interpolated (never planned)
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
-                           int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s);
+                           int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s,
+                           const int32_t* role = nullptr);
+cudaError_t launch_interp(const InterpRule* rules, int n, double* est, double* se, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& P, cudaStream_t s);
 template <typename T>
 cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s);

@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
 }
 
 __global__ void mc_init_kernel(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
-                               int64_t* steps, int64_t* paths_run, int64_t* next_total)
+                               int64_t* steps, int64_t* paths_run, int64_t* next_total, const int32_t* role)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
@@ -643,7 +643,26 @@ __global__ void mc_init_kernel(int M, int64_t n0, int64_t max_paths, double* acc
     n_done[m] = 0;
     steps[m] = 0;
     paths_run[m] = 0;
-    next_total[m] = n0 < max_paths ? n0 : max_paths;
+    const bool interpolated = role && role[m] >= 0;
+    next_total[m] = interpolated ? 0 : (n0 < max_paths ? n0 : max_paths);
+}
+
+// Interface sampling (Sec. 3.6): interpolated nodes from the estimates of their anchors, in the
+// order w va + (1 - w) vb without fused multiply-add; their standard error is 0.
+__global__ void interp_kernel(const InterpRule* rules, int n, double* est, double* se)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const InterpRule r = rules[k];
+    const double ax = __dadd_rn(r.a >= 0 ? est[2 * r.a] : 0.0, r.oax);
+    const double ay = __dadd_rn(r.a >= 0 ? est[2 * r.a + 1] : 0.0, r.oay);
+    const double bx = __dadd_rn(r.b >= 0 ? est[2 * r.b] : 0.0, r.obx);
+    const double by = __dadd_rn(r.b >= 0 ? est[2 * r.b + 1] : 0.0, r.oby);
+    const double wb = __dsub_rn(1.0, r.w);
+    est[2 * r.m] = __dadd_rn(__dmul_rn(r.w, ax), __dmul_rn(wb, bx));
+    est[2 * r.m + 1] = __dadd_rn(__dmul_rn(r.w, ay), __dmul_rn(wb, by));
+    se[2 * r.m] = 0.0;
+    se[2 * r.m + 1] = 0.0;
 }
 
 __device__ __forceinline__ void node_estimate(const double* s, double n, double sx, double sy,
@@ -778,10 +797,18 @@ template int mc_max_blocks_per_sm<float>(int, bool, bool);
 template int mc_max_blocks_per_sm<double>(int, bool, bool);
 
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
-                           int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s)
+                           int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s,
+                           const int32_t* role)
 {
     mc_init_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, n0, max_paths, acc, n_done, steps, paths_run,
-                                                   next_total);
+                                                   next_total, role);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_interp(const InterpRule* rules, int n, double* est, double* se, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    interp_kernel<<<(n + 255) / 256, 256, 0, s>>>(rules, n, est, se);
     return cudaGetLastError();
 }
 

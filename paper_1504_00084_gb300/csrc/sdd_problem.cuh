@@ -18,6 +18,8 @@ struct sdd_problem {
     bool fp64 = true;
     int acc_mode = sdd::kAcc64;
     int64_t step = 0;
+    double t_monitor = 0.0;         // monitor time when monitor_time_fixed (M^kP sub-steps)
+    bool monitor_time_fixed = false;
     bool have_est = false;
     // monitor
     int mon_kind = 0;
@@ -29,6 +31,12 @@ struct sdd_problem {
     void *mon = nullptr, *disp = nullptr;
     int2* nodes = nullptr;
     double* shift = nullptr;
+    // interface sampling (iface_stride > 1): per node -1 (Monte Carlo) or its rule index
+    std::vector<int32_t> h_role;
+    std::vector<sdd::InterpRule> h_interp;
+    int n_interp = 0;
+    int32_t* iface_role = nullptr;
+    sdd::InterpRule* interp = nullptr;
     // device: interface MC
     double* acc = nullptr;
     int64_t *n_done = nullptr, *steps = nullptr, *paths_run = nullptr, *next_total = nullptr;

@@ -62,7 +62,7 @@ __global__ void slot_pending_kernel(const int2* range, int n_slots, const int64_
 
 enum ReqState { kQueued, kRunning, kFinishing, kDone };
 
-typedef std::tuple<int, int, int, int, int> ShapeKey;  // nx, ny, px, py, periodic
+typedef std::tuple<int, int, int, int, int, int> ShapeKey;  // nx, ny, px, py, periodic, sampling stride
 
 struct Request {
     int64_t id = 0;
@@ -83,7 +83,10 @@ struct Request {
     cudaEvent_t done_ev = nullptr;  // finish work complete (finish stream)
 };
 
-ShapeKey shape_of(const sdd_params& q) { return ShapeKey(q.nx, q.ny, q.px, q.py, q.periodic); }
+ShapeKey shape_of(const sdd_params& q)
+{
+    return ShapeKey(q.nx, q.ny, q.px, q.py, q.periodic, q.iface_stride > 1 ? q.iface_stride : 1);
+}
 
 }  // namespace
 
@@ -349,7 +352,7 @@ sdd_status admit(sdd_server* s, Request* r)
         const int64_t n0 = s->prm.paths_per_node;
         const int64_t maxp = adaptive ? s->prm.max_paths_per_node : n0;
         S_CK(launch_mc_init(r->M, n0, maxp, s->acc + 4 * o, s->n_done + o, s->steps + o, s->paths_run + o,
-                            s->next_total + o, s->stream));
+                            s->next_total + o, s->stream, p->n_interp > 0 ? p->iface_role : nullptr));
         s->st.kernel_launches += 3;
     }
     if (s->fp64) write_record<double>(s, r); else write_record<float>(s, r);
@@ -372,7 +375,8 @@ sdd_status finish(sdd_server* s, Request* r)
     if (r->M > 0) {
         S_CK(launch_output(r->M, s->acc + 4 * o, s->n_done + o, s->shift + 2 * o, s->est + 2 * o, s->se + 2 * o,
                            s->fin));
-        s->st.kernel_launches += 1;
+        S_CK(launch_interp(p->interp, p->n_interp, s->est + 2 * o, s->se + 2 * o, s->fin));
+        s->st.kernel_launches += 1 + (p->n_interp > 0 ? 1 : 0);
     }
     S_CK(launch_scatter(r->prm.nx, r->prm.ny, r->prm.periodic, r->prm.Lx, r->prm.Ly, p->nodes, r->M,
                         s->est + 2 * o, p->xn, p->yn, s->fin));

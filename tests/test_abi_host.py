@@ -64,7 +64,7 @@ def base_params(sdd, **kw):
 
 
 @pytest.mark.parametrize("field,value", [("nx", 2), ("px", 3), ("py", 0), ("substeps", 0),
-                                         ("paths_per_node", 1), ("reserved0", 1), ("tau", 0.0),
+                                         ("paths_per_node", 1), ("iface_stride", -1), ("tau", 0.0),
                                          ("precision", 7), ("form", 2), ("solve_rtol", 0.0),
                                          ("periodic", 2), ("se_target", -1.0)])
 def test_invalid_params_rejected_before_any_device_work(sdd, field, value):
@@ -107,3 +107,16 @@ def test_checkpoint_load_rejects_bad_files_before_device_work(sdd, tmp_path):
     short.write_bytes(body + bytes(8))
     assert sdd.lib.sdd_load(str(short).encode(), None, ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
     assert sdd.lib.sdd_save(None, str(short).encode()) == sdd.SDD_ERR_INVALID_ARG
+
+
+
+@pytest.mark.parametrize("periodic", [0, 1])
+@pytest.mark.parametrize("shape", [(33, 33, 4, 4), (41, 25, 5, 3), (65, 65, 8, 2), (9, 17, 1, 2)])
+@pytest.mark.parametrize("stride", [0, 1, 2, 3, 4, 7, 40])
+def test_interface_sampling_matches_oracle(sdd, periodic, shape, stride):
+    from oracle.layout import interface_sampling
+    nx, ny, px, py = shape
+    p = base_params(sdd, nx=nx, ny=ny, px=px, py=py, periodic=periodic, iface_stride=stride)
+    got = sdd.sdd_interface_sampling(p)
+    want, _ = interface_sampling(nx, ny, px, py, periodic, stride)
+    assert np.array_equal(got, want)

@@ -61,3 +61,70 @@ def test_subdomain_rims_are_interface_or_boundary():
     for j in range(1, ny - 1):
         for i in range(1, nx - 1):
             assert covered[j, i] == (0 if (i, j) in nodes else 1)
+
+
+
+@pytest.mark.parametrize("periodic", [0, 1])
+@pytest.mark.parametrize("stride", [1, 2, 3, 5, 7])
+def test_interface_sampling_reproduces_fields_linear_along_lines(periodic, stride):
+    from oracle.layout import interface_sampling
+    nx, ny, px, py, Lx, Ly = 33, 41, 4, 5, 2.0, 1.5
+    sampled, fill = interface_sampling(nx, ny, px, py, periodic, stride, Lx, Ly)
+    nodes = interface_nodes(nx, ny, px, py, periodic)
+    # the identity mesh is linear along every line (with the period offset across the seam)
+    est = np.stack([Lx * nodes[:, 0] / (nx - 1), Ly * nodes[:, 1] / (ny - 1)], 1)
+    blank = est.copy()
+    blank[~sampled] = np.nan
+    assert np.allclose(fill(blank), est, atol=1e-14, rtol=0)
+    if stride == 1:
+        assert sampled.all()
+    else:
+        assert 0 < sampled.sum() < len(nodes)
+
+
+def test_interface_sampling_counts_closed_form():
+    from oracle.layout import interface_sampling
+    # 33 x 33 split 4 x 4, stride 2: 3 vertical lines x 15 even rows (crossings are even) and
+    # 3 horizontal lines x (15 even columns - 3 crossing columns)
+    sampled, _ = interface_sampling(33, 33, 4, 4, 0, 2)
+    assert sampled.sum() == 3 * 15 + 3 * 12
+    # stride 3: rows 3, 6, .., 30 (10) plus the crossings 8 and 16 (24 is a multiple of 3) on
+    # each vertical line; columns 3..30 step 3 (10) on each horizontal line, less the crossing
+    # column 24 (crossings are listed on the vertical lines)
+    sampled, _ = interface_sampling(33, 33, 4, 4, 0, 3)
+    assert sampled.sum() == 3 * 12 + 3 * 9
+
+
+def test_interface_sampling_brute_force_neighbours():
+    """Every interpolated node equals the linear interpolation between the nearest sampled node
+    (or boundary node) found by walking along its line in both directions."""
+    from oracle.layout import interface_sampling
+    nx, ny, px, py = 25, 17, 3, 2
+    rng = np.random.default_rng(5)
+    nodes = interface_nodes(nx, ny, px, py, 0)
+    sampled, fill = interface_sampling(nx, ny, px, py, 0, 4)
+    est = rng.normal(size=(len(nodes), 2))
+    out = fill(est)
+    ident = {(int(i), int(j)): m for m, (i, j) in enumerate(nodes)}
+    vcols = {8, 16}
+    for m, (i, j) in enumerate(nodes):
+        if sampled[m]:
+            assert np.array_equal(out[m], est[m])
+            continue
+        vertical = i in vcols
+        def value(ii, jj):
+            if (ii, jj) in ident and sampled[ident[(ii, jj)]]:
+                return est[ident[(ii, jj)]]
+            if ii in (0, nx - 1) or jj in (0, ny - 1):
+                return np.array([ii / (nx - 1), jj / (ny - 1)])
+            return None
+        step = (0, 1) if vertical else (1, 0)
+        lo, hi = 1, 1
+        while value(i - lo * step[0], j - lo * step[1]) is None:
+            lo += 1
+        while value(i + hi * step[0], j + hi * step[1]) is None:
+            hi += 1
+        a = value(i - lo * step[0], j - lo * step[1])
+        b = value(i + hi * step[0], j + hi * step[1])
+        want = (hi * a + lo * b) / (lo + hi)
+        assert np.allclose(out[m], want, atol=1e-14)

@@ -55,6 +55,7 @@ class Problem:
     max_paths_per_node: int = 0
     solve_rtol: float = 1e-12
     solve_max_iter: int = 20000
+    iface_stride: int = 0          # > 1: Monte Carlo at every k-th node of each interface line
     monitor_kind: int = MONITOR_GAUSS
     monitor_params: List[float] = field(default_factory=list)
     steps: int = 1
