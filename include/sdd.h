@@ -70,8 +70,10 @@ enum {
 };
 
 typedef struct {
-    int32_t nx, ny;          /* grid nodes per direction, >= 3; (nx-1) % px == 0, (ny-1) % py == 0  */
-    int32_t px, py;          /* subdomains per direction, >= 1 (px * py >= 2 for an interface)     */
+    int32_t nx, ny;          /* grid nodes per direction, >= 3                                      */
+    int32_t px, py;          /* subdomains per direction, 1 <= px <= nx - 1, 1 <= py <= ny - 1;
+                                subdomain I spans node columns floor(I (nx-1)/px) ..
+                                floor((I+1)(nx-1)/px) (equal when px divides nx - 1), likewise J */
     int32_t periodic;        /* 0: Dirichlet, boundary mesh fixed at (Lx xi, Ly eta) (Sec. 2);
                                 1: doubly periodic, x(xi+1) = x(xi) + Lx, y(eta+1) = y(eta) + Ly    */
     int32_t form;            /* SDD_FORM_DIV or SDD_FORM_WINSLOW                                   */
@@ -285,7 +287,7 @@ void sdd_batch_destroy(sdd_batch* b);
  * requests and a device-memory budget; with round_paths set, each round's paths also go to
  * the oldest running requests first, so requests complete close to arrival order instead of
  * all together.  The device state of collected requests is kept per
- * grid shape (nx, ny, px, py, periodic) and reused, so steady-state serving allocates no
+ * grid shape (nx, ny, px, py, periodic, iface_stride) and reused, so steady-state serving allocates no
  * device memory; cached state is freed (oldest first) only when a new shape needs room.
  * The paper has no serving layer: this is the system around its method. */
 typedef struct sdd_server sdd_server;

@@ -9,26 +9,29 @@ from __future__ import annotations
 import numpy as np
 
 
+def split_line(I, n, P):
+    """Node index of the line that ends part I of an n-node direction split into P parts
+    (part I spans split_line(I) .. split_line(I + 1); equal parts when P divides n - 1)."""
+    return (I * (n - 1)) // P
+
+
 def interface_nodes(nx, ny, px, py, periodic=0):
     """(M, 2) int array of (i, j) interface nodes in the canonical order.
 
     Vertical lines first (by increasing i, then j), then horizontal lines (by increasing j,
     then i), skipping nodes already listed on a vertical line.  Dirichlet: lines at
-    i = I (nx-1)/px for I = 1..px-1, nodes j = 1..ny-2 (and the mirror for horizontal
+    i = floor(I (nx-1)/px) for I = 1..px-1, nodes j = 1..ny-2 (and the mirror for horizontal
     lines).  Periodic: lines at I = 0..px-1 (the line i = 0 is also i = nx-1), nodes
     j = 0..ny-2.  The position in this list is the node id used in the Philox counter.
     """
-    if (nx - 1) % px or (ny - 1) % py:
-        raise ValueError("grid intervals must divide evenly into subdomains")
-    sx, sy = (nx - 1) // px, (ny - 1) // py
+    if px > nx - 1 or py > ny - 1:
+        raise ValueError("every subdomain must span at least one cell")
+    vl = [split_line(I, nx, px) for I in (range(px) if periodic else range(1, px))]
+    hl = [split_line(J, ny, py) for J in (range(py) if periodic else range(1, py))]
     if periodic:
-        vl = [I * sx for I in range(px)]
-        hl = [J * sy for J in range(py)]
         jr = range(0, ny - 1)
         ir = range(0, nx - 1)
     else:
-        vl = [I * sx for I in range(1, px)]
-        hl = [J * sy for J in range(1, py)]
         jr = range(1, ny - 1)
         ir = range(1, nx - 1)
     out = []
@@ -45,8 +48,8 @@ def interface_nodes(nx, ny, px, py, periodic=0):
 
 def subdomains(nx, ny, px, py):
     """List of (i0, i1, j0, j1): subdomain (I, J) spans nodes i0..i1, j0..j1 (rims included)."""
-    sx, sy = (nx - 1) // px, (ny - 1) // py
-    return [(I * sx, (I + 1) * sx, J * sy, (J + 1) * sy) for J in range(py) for I in range(px)]
+    return [(split_line(I, nx, px), split_line(I + 1, nx, px), split_line(J, ny, py), split_line(J + 1, ny, py))
+            for J in range(py) for I in range(px)]
 
 
 def interface_sampling(nx, ny, px, py, periodic=0, stride=1, Lx=1.0, Ly=1.0):
@@ -69,9 +72,8 @@ def interface_sampling(nx, ny, px, py, periodic=0, stride=1, Lx=1.0, Ly=1.0):
     if stride <= 1:
         return np.ones(M, dtype=bool), lambda est: np.array(est, dtype=np.float64, copy=True)
     ident = {(int(i), int(j)): m for m, (i, j) in enumerate(nodes)}
-    sx, sy = (nx - 1) // px, (ny - 1) // py
-    vl = [I * sx for I in (range(px) if periodic else range(1, px))]
-    hl = [J * sy for J in (range(py) if periodic else range(1, py))]
+    vl = [split_line(I, nx, px) for I in (range(px) if periodic else range(1, px))]
+    hl = [split_line(J, ny, py) for J in (range(py) if periodic else range(1, py))]
     sampled = np.zeros(M, dtype=bool)
     rules = []   # (m, weight of a, anchor a, anchor b); anchor = (node id or None, offset x, offset y)
 

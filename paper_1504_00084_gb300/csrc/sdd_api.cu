@@ -56,15 +56,9 @@ const char kCkptMagic[8] = {'S', 'D', 'D', 'C', 'K', 'P', 'T', '1'};
 void layout(int nx, int ny, int px, int py, int periodic, std::vector<int32_t>& ij)
 {
     ij.clear();
-    const int sx = (nx - 1) / px, sy = (ny - 1) / py;
     std::vector<int> vl, hl;
-    if (periodic) {
-        for (int I = 0; I < px; ++I) vl.push_back(I * sx);
-        for (int J = 0; J < py; ++J) hl.push_back(J * sy);
-    } else {
-        for (int I = 1; I < px; ++I) vl.push_back(I * sx);
-        for (int J = 1; J < py; ++J) hl.push_back(J * sy);
-    }
+    for (int I = periodic ? 0 : 1; I < px; ++I) vl.push_back(split_line(I, nx, px));
+    for (int J = periodic ? 0 : 1; J < py; ++J) hl.push_back(split_line(J, ny, py));
     const int jlo = periodic ? 0 : 1, jhi = periodic ? ny - 2 : ny - 2;
     const int ilo = periodic ? 0 : 1, ihi = periodic ? nx - 2 : nx - 2;
     std::vector<char> on_v(nx, 0);
@@ -89,13 +83,19 @@ void sampling_table(const sdd_params& q, const std::vector<int32_t>& ij, std::ve
     rules.clear();
     const int k = q.iface_stride;
     if (k <= 1 || M == 0) return;
-    const int nx = q.nx, ny = q.ny, sx = (nx - 1) / q.px, sy = (ny - 1) / q.py;
+    const int nx = q.nx, ny = q.ny;
     std::vector<int32_t> id((size_t)nx * ny, -1);
     for (int m = 0; m < M; ++m) id[(size_t)ij[2 * m + 1] * nx + ij[2 * m]] = m;
     std::vector<char> is_vl(nx, 0), is_hl(ny, 0);
     std::vector<int> vl, hl;
-    for (int I = q.periodic ? 0 : 1; I < q.px; ++I) { vl.push_back(I * sx); is_vl[I * sx] = 1; }
-    for (int J = q.periodic ? 0 : 1; J < q.py; ++J) { hl.push_back(J * sy); is_hl[J * sy] = 1; }
+    for (int I = q.periodic ? 0 : 1; I < q.px; ++I) {
+        vl.push_back(split_line(I, nx, q.px));
+        is_vl[vl.back()] = 1;
+    }
+    for (int J = q.periodic ? 0 : 1; J < q.py; ++J) {
+        hl.push_back(split_line(J, ny, q.py));
+        is_hl[hl.back()] = 1;
+    }
     struct Anchor { int t; int32_t node; double ox, oy; };
     auto line = [&](bool vertical, int c) {
         const int L = vertical ? ny - 1 : nx - 1;
@@ -155,8 +155,8 @@ sdd_status validate(const sdd_params* P)
     if (P->nx < 3 || P->ny < 3) return fail(SDD_ERR_INVALID_ARG, "nx, ny must be >= 3");
     if ((int64_t)P->nx * P->ny > (int64_t)1 << 28) return fail(SDD_ERR_INVALID_ARG, "grid too large");
     if (P->px < 1 || P->py < 1) return fail(SDD_ERR_INVALID_ARG, "px, py must be >= 1");
-    if ((P->nx - 1) % P->px || (P->ny - 1) % P->py)
-        return fail(SDD_ERR_INVALID_ARG, "(nx-1) % px and (ny-1) % py must be 0");
+    if (P->px > P->nx - 1 || P->py > P->ny - 1)
+        return fail(SDD_ERR_INVALID_ARG, "px <= nx - 1 and py <= ny - 1 (every subdomain spans a cell)");
     if (P->periodic != 0 && P->periodic != 1) return fail(SDD_ERR_INVALID_ARG, "periodic must be 0 or 1");
     if (P->form != SDD_FORM_DIV && P->form != SDD_FORM_WINSLOW) return fail(SDD_ERR_INVALID_ARG, "bad form");
     if (P->precision < SDD_FP64 || P->precision > SDD_FP32_KAHAN)
@@ -455,7 +455,16 @@ sdd_problem* problem_shell(const sdd_params& prm, cudaStream_t stream)
     p->n_interp = (int)p->h_interp.size();
     p->slot_cap = (int64_t)(p->M > 0 ? p->M : 1) * kSlotsPerNode;
     const size_t rs = p->fp64 ? 8 : 4;
-    p->mg_stride = mg_bytes((prm.nx - 1) / prm.px - 1, (prm.ny - 1) / prm.py - 1, rs);
+    // workspace slot per subdomain: the largest hierarchy over the subdomain widths, which are
+    // floor((n-1)/P) or that plus one in each direction
+    size_t mg = 0;
+    const int wx = (prm.nx - 1) / prm.px, wy = (prm.ny - 1) / prm.py;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) {
+            const size_t m = mg_bytes(wx + a - 1, wy + b - 1, rs);
+            if (m > mg) mg = m;
+        }
+    p->mg_stride = mg;
     p->stats.M = p->M;
     p->stats.t = prm.t0;
     return p;
@@ -562,7 +571,7 @@ sdd_status sdd_interface_layout(int32_t nx, int32_t ny, int32_t px, int32_t py, 
                                 int32_t* ij, int32_t* M)
 {
     if (!M) return fail(SDD_ERR_INVALID_ARG, "M is NULL");
-    if (nx < 3 || ny < 3 || px < 1 || py < 1 || (nx - 1) % px || (ny - 1) % py || (periodic != 0 && periodic != 1))
+    if (nx < 3 || ny < 3 || px < 1 || py < 1 || px > nx - 1 || py > ny - 1 || (periodic != 0 && periodic != 1))
         return fail(SDD_ERR_INVALID_ARG, "bad grid or split");
     std::vector<int32_t> v;
     layout(nx, ny, px, py, periodic, v);

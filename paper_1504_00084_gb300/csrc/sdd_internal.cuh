@@ -181,6 +181,13 @@ struct SolveParams {
     double* stat_res;          // per subdomain: final relative residual (max of x, y)
 };
 
+// Subdomain lines of an n-node direction split into P parts: part I spans nodes
+// split_line(I) .. split_line(I + 1) (equal parts when P divides n - 1).
+__host__ __device__ inline int split_line(int I, int n, int P)
+{
+    return (int)(((int64_t)I * (int64_t)(n - 1)) / (int64_t)P);
+}
+
 // Multigrid hierarchy of an n x m subdomain interior: levels while both sizes stay odd and
 // >= 3 (n -> (n-1)/2), and the bytes of its per-level arrays (x, b, t pairs; faces; identity).
 __host__ __device__ inline int mg_levels(int n, int m)

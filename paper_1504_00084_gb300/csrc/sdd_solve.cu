@@ -300,10 +300,10 @@ template <typename TI>
 __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double* sh)
 {
     const int nx = P.nx, ny = P.ny;
-    const int sx = (nx - 1) / P.px, sy = (ny - 1) / P.py;
     const int I = sub % P.px, J = sub / P.px;
-    const int i0 = I * sx, j0 = J * sy;
-    const int ni = sx - 1, nj = sy - 1;
+    const int i0 = split_line(I, nx, P.px), i1 = split_line(I + 1, nx, P.px);
+    const int j0 = split_line(J, ny, P.py), j1 = split_line(J + 1, ny, P.py);
+    const int ni = i1 - i0 - 1, nj = j1 - j0 - 1;
     const int nint = ni * nj;
     const long N = (long)nx * ny;
     Pair<TI>* e = static_cast<Pair<TI>*>(P.vec);
@@ -330,9 +330,9 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
         const double d = dP(id);
         double bx = d * P.xcur[id], by = d * P.ycur[id];
         if (i - 1 == i0) { bx += P.ce64[id - 1] * P.xnew[id - 1]; by += P.ce64[id - 1] * P.ynew[id - 1]; }
-        if (i + 1 == i0 + sx) { bx += P.ce64[id] * P.xnew[id + 1]; by += P.ce64[id] * P.ynew[id + 1]; }
+        if (i + 1 == i1) { bx += P.ce64[id] * P.xnew[id + 1]; by += P.ce64[id] * P.ynew[id + 1]; }
         if (j - 1 == j0) { bx += P.cn64[id - nx] * P.xnew[id - nx]; by += P.cn64[id - nx] * P.ynew[id - nx]; }
-        if (j + 1 == j0 + sy) { bx += P.cn64[id] * P.xnew[id + nx]; by += P.cn64[id] * P.ynew[id + nx]; }
+        if (j + 1 == j1) { bx += P.cn64[id] * P.xnew[id + nx]; by += P.cn64[id] * P.ynew[id + nx]; }
         bn[0] += bx * bx;
         bn[1] += by * by;
     }

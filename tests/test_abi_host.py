@@ -37,7 +37,8 @@ def test_every_declared_symbol_is_exported(sdd):
 
 @pytest.mark.parametrize("nx,ny,px,py,per", [(33, 33, 2, 2, 0), (257, 257, 4, 4, 0), (257, 257, 4, 4, 1),
                                              (65, 129, 8, 2, 0), (9, 9, 1, 1, 0), (9, 9, 1, 1, 1),
-                                             (3, 3, 2, 2, 0), (17, 33, 4, 2, 1)])
+                                             (3, 3, 2, 2, 0), (17, 33, 4, 2, 1), (41, 41, 3, 3, 0),
+                                             (41, 41, 3, 3, 1), (100, 37, 7, 5, 0), (50, 50, 13, 6, 1)])
 def test_interface_layout_matches_oracle(sdd, nx, ny, px, py, per):
     from oracle.layout import interface_nodes
     got = sdd.sdd_interface_layout(nx, ny, px, py, per)
@@ -63,7 +64,7 @@ def base_params(sdd, **kw):
     return sdd.params_from(W.c0_small_fp64(), **kw)
 
 
-@pytest.mark.parametrize("field,value", [("nx", 2), ("px", 3), ("py", 0), ("substeps", 0),
+@pytest.mark.parametrize("field,value", [("nx", 2), ("px", 40), ("py", 0), ("substeps", 0),
                                          ("paths_per_node", 1), ("iface_stride", -1), ("tau", 0.0),
                                          ("precision", 7), ("form", 2), ("solve_rtol", 0.0),
                                          ("periodic", 2), ("se_target", -1.0)])
@@ -111,7 +112,8 @@ def test_checkpoint_load_rejects_bad_files_before_device_work(sdd, tmp_path):
 
 
 @pytest.mark.parametrize("periodic", [0, 1])
-@pytest.mark.parametrize("shape", [(33, 33, 4, 4), (41, 25, 5, 3), (65, 65, 8, 2), (9, 17, 1, 2)])
+@pytest.mark.parametrize("shape", [(33, 33, 4, 4), (41, 25, 5, 3), (65, 65, 8, 2), (9, 17, 1, 2), (41, 41, 3, 3),
+                                   (50, 37, 7, 4)])
 @pytest.mark.parametrize("stride", [0, 1, 2, 3, 4, 7, 40])
 def test_interface_sampling_matches_oracle(sdd, periodic, shape, stride):
     from oracle.layout import interface_sampling

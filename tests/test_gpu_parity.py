@@ -156,13 +156,18 @@ def _mesh_tolerance(prob, om, rims_x, rims_y, xn, yn, est_tol):
     return est_tol + worst + 1e-12
 
 
-@pytest.mark.parametrize("variant", ["c0", "periodic", "winslow"])
+@pytest.mark.parametrize("variant", ["c0", "periodic", "winslow", "uneven", "uneven_periodic"])
 def test_full_step_fp64(S, variant):
     prob = W.c0_small_fp64()
     if variant == "periodic":
         prob = prob.replace(periodic=1, monitor_params=[6.0, 40.0, 0.3, 0.6])
     elif variant == "winslow":
         prob = prob.replace(form=W.FORM_WINSLOW, tau=1.0)
+    elif variant == "uneven":
+        # 32 cells in 3 and 5 parts: subdomains of 10/11/11 and 6/6/7/6/7 cells
+        prob = prob.replace(px=3, py=5)
+    elif variant == "uneven_periodic":
+        prob = prob.replace(px=3, py=3, periodic=1, monitor_params=[6.0, 40.0, 0.3, 0.6])
     x, y = W.identity_mesh(prob)
     h = gpu_problem(prob, x, y)
     gx, gy, status = h.step()

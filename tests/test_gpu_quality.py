@@ -61,7 +61,7 @@ def _five_ring(px, substeps):
     return r
 
 
-@pytest.mark.parametrize("px", [2, 4])
+@pytest.mark.parametrize("px", [2, 3, 4])
 @pytest.mark.parametrize("substeps", [1, 16])
 def test_five_ring_quality_ratio(px, substeps):
     """Paper's setting is one Euler-Maruyama substep per step.  The rings are resolved by about

@@ -128,3 +128,25 @@ def test_interface_sampling_brute_force_neighbours():
         b = value(i + hi * step[0], j + hi * step[1])
         want = (hi * a + lo * b) / (lo + hi)
         assert np.allclose(out[m], want, atol=1e-14)
+
+
+def test_uneven_split_lines_and_tiling():
+    """41 nodes in 3 parts: lines at floor(40 I / 3) = 13, 26, parts of 13, 13 and 14 cells; the
+    counts keep their closed forms and the subdomain interiors still tile the grid once."""
+    from oracle.layout import split_line
+    assert [split_line(I, 41, 3) for I in range(4)] == [0, 13, 26, 40]
+    nodes = interface_nodes(41, 41, 3, 3, 0)
+    assert len(nodes) == 2 * 39 + 2 * 39 - 4
+    assert {int(i) for i, j in nodes[:2 * 39]} == {13, 26}
+    per = interface_nodes(41, 41, 3, 3, 1)
+    assert len(per) == 3 * 40 + 3 * 40 - 9
+    subs = subdomains(41, 41, 3, 3)
+    covered = np.zeros((41, 41), int)
+    for (i0, i1, j0, j1) in subs:
+        covered[j0 + 1:j1, i0 + 1:i1] += 1
+    on_line = np.zeros((41, 41), bool)
+    on_line[:, [0, 13, 26, 40]] = True
+    on_line[[0, 13, 26, 40], :] = True
+    assert np.array_equal(covered, (~on_line).astype(int))
+    with pytest.raises(ValueError):
+        interface_nodes(5, 5, 5, 1, 0)
