@@ -100,6 +100,13 @@ typedef struct {
                                 at every node; 0: fixed N                                           */
     double solve_rtol;       /* subdomain solves stop at ||b - A x||_2 <= solve_rtol ||b||_2, > 0   */
     double t0;               /* time of the initial mesh                                           */
+    int32_t subdomain_scheme; /* 0: backward Euler (default, any step size); 1: forward Euler, the
+                                paper's local solver (Sec. 3.5), in S = ceil(max_P sum_nb c_nb/d_P)
+                                explicit substeps (every substep a convex combination: discrete
+                                maximum principle) with the rim values interpolated linearly in
+                                time between the previous mesh and the new Dirichlet data      */
+    int32_t fe_max_substeps; /* forward Euler: a subdomain needing more substeps is not solved
+                                (SDD_ERR_NOT_CONVERGED, interior left at x^n); 0 means 2^16     */
 } sdd_params;
 
 typedef struct {
@@ -287,7 +294,7 @@ void sdd_batch_destroy(sdd_batch* b);
  * requests and a device-memory budget; with round_paths set, each round's paths also go to
  * the oldest running requests first, so requests complete close to arrival order instead of
  * all together.  The device state of collected requests is kept per
- * grid shape (nx, ny, px, py, periodic, iface_stride) and reused, so steady-state serving allocates no
+ * grid shape (nx, ny, px, py, periodic, iface_stride, subdomain_scheme) and reused, so steady-state serving allocates no
  * device memory; cached state is freed (oldest first) only when a new shape needs room.
  * The paper has no serving layer: this is the system around its method. */
 typedef struct sdd_server sdd_server;

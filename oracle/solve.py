@@ -13,8 +13,16 @@ step solves, for every interior node P with neighbours E, W, N, S,
 
 with r = dt / tau, a_E = (omega_P + omega_E)/2 / h_xi^2 (face average), a_N the same with
 h_eta.  The system is symmetric positive definite; the oracle solves it directly (SuperLU).
+
+The paper's own local solver is forward Euler (Sec. 3.5), offered as an option: the same
+operator applied explicitly in S substeps of dt / S, with S = ceil(max_P sum_nb r a_nb / d_P) --
+the smallest count for which every substep is a convex combination of the node and its
+neighbours (discrete maximum principle) -- and the rim values interpolated linearly in time
+between the previous mesh and the new Dirichlet data.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -143,4 +151,89 @@ def periodic_single_domain_step(omega, xn, yn, dt, tau, form, Lx=1.0, Ly=1.0):
             P = idx(i, j)
             out_x[j, i] = sx[P] + Lx * (i // mx)
             out_y[j, i] = sy[P] + Ly * (j // my)
+    return out_x, out_y
+
+
+def fe_substeps(c_sum_over_d):
+    """Forward-Euler substeps for the largest sum_nb c_nb / d_P of a box: S = ceil(that), >= 1."""
+    return max(1, int(math.ceil(c_sum_over_d)))
+
+
+def solve_box_fe(omega, rim_x, rim_y, xn, yn, i0, i1, j0, j1, dt, tau, form):
+    """Forward-Euler update of the interior of one node box (the paper's local solver, Sec. 3.5).
+
+    rim_x, rim_y hold the new Dirichlet values on the box rim, xn, yn the previous mesh.  Every
+    substep m = 0..S-1 moves each interior node by (1 / (S d_P)) sum_nb c_nb (x_nb - x_P), with
+    rim neighbours at xn + (m / S)(rim - xn).  Returns (x_int, y_int, order, S) as solve_box."""
+    ny, nx = omega.shape
+    hx2 = float(nx - 1) ** 2
+    hy2 = float(ny - 1) ** 2
+    r = dt / tau
+    ii = np.arange(i0 + 1, i1)
+    jj = np.arange(j0 + 1, j1)
+    order = [(i, j) for j in jj for i in ii]
+    if len(order) == 0:
+        return np.zeros(0), np.zeros(0), order, 1
+    J, I = np.meshgrid(jj, ii, indexing="ij")
+    w = omega[J, I]
+    cE = r * (0.5 * (w + omega[J, I + 1]) * hx2)
+    cW = r * (0.5 * (w + omega[J, I - 1]) * hx2)
+    cN = r * (0.5 * (w + omega[J + 1, I]) * hy2)
+    cS = r * (0.5 * (w + omega[J - 1, I]) * hy2)
+    d = w if form == 1 else np.ones_like(w)
+    S = fe_substeps(float(((cE + cW + cN + cS) / d).max()))
+    ax = xn[j0:j1 + 1, i0:i1 + 1].astype(np.float64).copy()
+    ay = yn[j0:j1 + 1, i0:i1 + 1].astype(np.float64).copy()
+    px, py = xn[j0:j1 + 1, i0:i1 + 1], yn[j0:j1 + 1, i0:i1 + 1]
+    qx, qy = rim_x[j0:j1 + 1, i0:i1 + 1], rim_y[j0:j1 + 1, i0:i1 + 1]
+    rim = np.ones(ax.shape, bool)
+    rim[1:-1, 1:-1] = False
+    for m in range(S):
+        f = m / S
+        for a, p, q in ((ax, px, qx), (ay, py, qy)):
+            a[rim] = p[rim] + f * (q[rim] - p[rim])
+        for a in (ax, ay):
+            c = a[1:-1, 1:-1]
+            s_ = (cE * (a[1:-1, 2:] - c) + cW * (a[1:-1, :-2] - c)) + cN * (a[2:, 1:-1] - c) + cS * (a[:-2, 1:-1] - c)
+            a[1:-1, 1:-1] = c + s_ / (S * d)
+    return ax[1:-1, 1:-1].ravel(), ay[1:-1, 1:-1].ravel(), order, S
+
+
+def periodic_single_domain_step_fe(omega, xn, yn, dt, tau, form, Lx=1.0, Ly=1.0):
+    """Forward-Euler counterpart of periodic_single_domain_step: S substeps of the same
+    operator on the doubly periodic grid (neighbours across a seam carry the period offset)."""
+    ny, nx = omega.shape
+    mx, my = nx - 1, ny - 1
+    hx2 = float(nx - 1) ** 2
+    hy2 = float(ny - 1) ** 2
+    r = dt / tau
+    w = omega[:my, :mx]
+    wE, wW = np.roll(w, -1, axis=1), np.roll(w, 1, axis=1)
+    wN, wS = np.roll(w, -1, axis=0), np.roll(w, 1, axis=0)
+    cE = r * (0.5 * (w + wE) * hx2)
+    cW = r * (0.5 * (w + wW) * hx2)
+    cN = r * (0.5 * (w + wN) * hy2)
+    cS = r * (0.5 * (w + wS) * hy2)
+    d = w if form == 1 else np.ones_like(w)
+    S = fe_substeps(float(((cE + cW + cN + cS) / d).max()))
+    x = xn[:my, :mx].astype(np.float64).copy()
+    y = yn[:my, :mx].astype(np.float64).copy()
+    for _ in range(S):
+        xE = np.roll(x, -1, axis=1); xE[:, -1] += Lx
+        xW = np.roll(x, 1, axis=1); xW[:, 0] -= Lx
+        x_new = x + ((cE * (xE - x) + cW * (xW - x)) + cN * (np.roll(x, -1, axis=0) - x) +
+                     cS * (np.roll(x, 1, axis=0) - x)) / (S * d)
+        yN = np.roll(y, -1, axis=0); yN[-1, :] += Ly
+        yS = np.roll(y, 1, axis=0); yS[0, :] -= Ly
+        y_new = y + ((cE * (np.roll(y, -1, axis=1) - y) + cW * (np.roll(y, 1, axis=1) - y)) + cN * (yN - y) +
+                     cS * (yS - y)) / (S * d)
+        x, y = x_new, y_new
+    out_x = np.empty((ny, nx))
+    out_y = np.empty((ny, nx))
+    out_x[:my, :mx] = x
+    out_y[:my, :mx] = y
+    out_x[:my, mx] = x[:, 0] + Lx
+    out_y[:my, mx] = y[:, 0]
+    out_x[my, :] = out_x[0, :]
+    out_y[my, :] = out_y[0, :] + Ly
     return out_x, out_y

@@ -13,7 +13,7 @@ from workloads import MONITOR_NODAL
 from .layout import interface_nodes, subdomains
 from .mc import interface_mc
 from .monitor import monitor_on_grid, wrap_copy
-from .solve import solve_box
+from .solve import solve_box, solve_box_fe
 
 
 def monitor_on_mesh(prob, x, y, t, omega_nodal=None):
@@ -58,11 +58,17 @@ def scatter(prob, nodes, est):
 
 
 def subdomain_solves(prob, omega, bx, by, xn, yn):
-    """Fill every subdomain interior of (bx, by) by its backward-Euler solve (Sec. 3.5)."""
+    """Fill every subdomain interior of (bx, by) by its backward-Euler solve (Sec. 3.5), or by
+    forward-Euler substeps when prob.subdomain_scheme == 1 (the paper's local solver)."""
     out_x, out_y = bx.copy(), by.copy()
+    fe = int(getattr(prob, "subdomain_scheme", 0)) == 1
     for (i0, i1, j0, j1) in subdomains(prob.nx, prob.ny, prob.px, prob.py):
-        xs, ys, order = solve_box(omega, bx, by, xn, yn, i0, i1, j0, j1, prob.dt, prob.tau,
-                                  prob.form)
+        if fe:
+            xs, ys, order, _ = solve_box_fe(omega, bx, by, xn, yn, i0, i1, j0, j1, prob.dt, prob.tau,
+                                            prob.form)
+        else:
+            xs, ys, order = solve_box(omega, bx, by, xn, yn, i0, i1, j0, j1, prob.dt, prob.tau,
+                                      prob.form)
         for P, (i, j) in enumerate(order):
             out_x[j, i] = xs[P]
             out_y[j, i] = ys[P]

@@ -176,6 +176,9 @@ sdd_status validate(const sdd_params* P)
     if (cap < P->paths_per_node || cap > ((int64_t)1 << 31))
         return fail(SDD_ERR_INVALID_ARG, "max_paths_per_node must be in [paths_per_node, 2^31]");
     if (!(P->solve_rtol > 0)) return fail(SDD_ERR_INVALID_ARG, "solve_rtol must be > 0");
+    if (P->subdomain_scheme != 0 && P->subdomain_scheme != 1)
+        return fail(SDD_ERR_INVALID_ARG, "subdomain_scheme must be 0 or 1");
+    if (P->fe_max_substeps < 0) return fail(SDD_ERR_INVALID_ARG, "fe_max_substeps must be >= 0");
     return SDD_OK;
 }
 
@@ -372,6 +375,8 @@ sdd_status run_solve(sdd_problem* p)
     SolveParams S{};
     S.nx = p->prm.nx; S.ny = p->prm.ny; S.px = p->prm.px; S.py = p->prm.py; S.form = p->prm.form;
     S.r = p->prm.dt / p->prm.tau; S.rtol = p->prm.solve_rtol; S.max_iter = p->prm.solve_max_iter;
+    S.scheme = p->prm.subdomain_scheme;
+    S.fe_max_substeps = p->prm.fe_max_substeps > 0 ? p->prm.fe_max_substeps : (1 << 16);
     S.om64 = p->om64; S.xcur = p->x; S.ycur = p->y; S.xnew = p->xn; S.ynew = p->yn;
     S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
     S.mg = p->mg; S.mg_stride = p->mg_stride;

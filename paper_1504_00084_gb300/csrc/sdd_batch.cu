@@ -123,6 +123,8 @@ SolveParams solve_params(const sdd_problem* p)
     SolveParams S{};
     S.nx = p->prm.nx; S.ny = p->prm.ny; S.px = p->prm.px; S.py = p->prm.py; S.form = p->prm.form;
     S.r = p->prm.dt / p->prm.tau; S.rtol = p->prm.solve_rtol; S.max_iter = p->prm.solve_max_iter;
+    S.scheme = p->prm.subdomain_scheme;
+    S.fe_max_substeps = p->prm.fe_max_substeps > 0 ? p->prm.fe_max_substeps : (1 << 16);
     S.om64 = p->om64; S.xcur = p->x; S.ycur = p->y; S.xnew = p->xn; S.ynew = p->yn;
     S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
     S.mg = p->mg; S.mg_stride = p->mg_stride;
@@ -252,8 +254,14 @@ sdd_status record_step(sdd_batch* b)
         B_CK(launch_faces(b->solve_host[i], fp64_inner, b->stream));
         launches += 1;
     }
-    B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream));
-    launches += 1;
+    bool any_be = false, any_fe = false;
+    for (const sdd_problem* p : b->probs) {
+        any_be = any_be || p->prm.subdomain_scheme == 0;
+        any_fe = any_fe || p->prm.subdomain_scheme == 1;
+    }
+    B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream, any_be,
+                            any_fe));
+    launches += (any_be ? 1 : 0) + (any_fe ? 1 : 0);
     for (int i = 0; i < b->n; ++i) {
         sdd_problem* p = b->probs[i];
         const size_t bytes = (size_t)p->prm.nx * p->prm.ny * 8;

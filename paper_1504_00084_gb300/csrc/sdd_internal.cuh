@@ -160,6 +160,8 @@ struct PrepParams {
 
 struct SolveParams {
     int nx, ny, px, py, form;
+    int scheme;                // 0 backward Euler, 1 forward Euler substeps
+    int fe_max_substeps;
     double r;                  // dt / tau
     double rtol;
     int max_iter;
@@ -246,7 +248,7 @@ cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const
 cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s);
 cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s);
 cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
-                               bool fp64_inner, cudaStream_t s);
+                               bool fp64_inner, cudaStream_t s, bool any_be = true, bool any_fe = false);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                           cudaStream_t s);
 

@@ -62,7 +62,9 @@ __global__ void slot_pending_kernel(const int2* range, int n_slots, const int64_
 
 enum ReqState { kQueued, kRunning, kFinishing, kDone };
 
-typedef std::tuple<int, int, int, int, int, int> ShapeKey;  // nx, ny, px, py, periodic, sampling stride
+// nx, ny, px, py, periodic, sampling stride, subdomain scheme (the schemes use the solver
+// vectors differently, so state is reused only within a scheme)
+typedef std::tuple<int, int, int, int, int, int, int> ShapeKey;
 
 struct Request {
     int64_t id = 0;
@@ -85,7 +87,7 @@ struct Request {
 
 ShapeKey shape_of(const sdd_params& q)
 {
-    return ShapeKey(q.nx, q.ny, q.px, q.py, q.periodic, q.iface_stride > 1 ? q.iface_stride : 1);
+    return ShapeKey(q.nx, q.ny, q.px, q.py, q.periodic, q.iface_stride > 1 ? q.iface_stride : 1, q.subdomain_scheme);
 }
 
 }  // namespace
@@ -384,6 +386,8 @@ sdd_status finish(sdd_server* s, Request* r)
     SolveParams S{};
     S.nx = r->prm.nx; S.ny = r->prm.ny; S.px = r->prm.px; S.py = r->prm.py; S.form = r->prm.form;
     S.r = r->prm.dt / r->prm.tau; S.rtol = r->prm.solve_rtol; S.max_iter = r->prm.solve_max_iter;
+    S.scheme = r->prm.subdomain_scheme;
+    S.fe_max_substeps = r->prm.fe_max_substeps > 0 ? r->prm.fe_max_substeps : (1 << 16);
     S.om64 = p->om64; S.xcur = p->x; S.ycur = p->y; S.xnew = p->xn; S.ynew = p->yn;
     S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
     S.mg = p->mg; S.mg_stride = p->mg_stride;

@@ -295,6 +295,106 @@ __device__ void mg_vcycle(void* base, int nx0, int ny0, int levels)
     }
 }
 
+// Largest value of v over the block; every thread receives it.
+__device__ __forceinline__ double block_max(double v, double* sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, off));
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        double t = lane < nw ? sh[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t = fmax(t, __shfl_xor_sync(kFull, t, off));
+        if (lane == 0) sh[32] = t;
+    }
+    __syncthreads();
+    const double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Forward Euler (the paper's local solver, Sec. 3.5) for subdomain `sub`, in FP64: S substeps of
+//   x_P <- x_P + (1 / (S d_P)) sum_nb c_nb (x_nb - x_P),   S = ceil(max_P sum_nb c_nb / d_P),
+// so every substep is a convex combination (discrete maximum principle); a rim neighbour takes
+// x^n + (m / S)(x^{n+1} - x^n) at substep m.  Two full-grid FP64 pair buffers in P.vec hold the
+// interior iterates (the inner-vector storage, unused by this scheme).
+__device__ void fe_body(const SolveParams& P, int sub, double* sh)
+{
+    const int nx = P.nx, ny = P.ny;
+    const int I = sub % P.px, J = sub / P.px;
+    const int i0 = split_line(I, nx, P.px), i1 = split_line(I + 1, nx, P.px);
+    const int j0 = split_line(J, ny, P.py), j1 = split_line(J + 1, ny, P.py);
+    const int ni = i1 - i0 - 1, nj = j1 - j0 - 1;
+    const int nint = ni * nj;
+    const long N = (long)nx * ny;
+    double2* A = static_cast<double2*>(P.vec);
+    double2* B = A + N;
+    auto node = [&](int t) -> long { return (long)(j0 + 1 + t / ni) * nx + (i0 + 1 + t % ni); };
+    auto dP = [&](long id) -> double { return P.form == 0 ? 1.0 : P.om64[id]; };
+    double cmax = 0.0;
+    for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+        const long id = node(t);
+        const double c = __dadd_rn(__dadd_rn(__dadd_rn(P.ce64[id], P.ce64[id - 1]), P.cn64[id]), P.cn64[id - nx]);
+        cmax = fmax(cmax, __ddiv_rn(c, dP(id)));
+    }
+    cmax = block_max(cmax, sh);
+    const double Sd = ceil(cmax) < 1.0 ? 1.0 : ceil(cmax);
+    if (!(Sd <= (double)P.fe_max_substeps)) {
+        for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+            const long id = node(t);
+            P.xnew[id] = P.xcur[id];
+            P.ynew[id] = P.ycur[id];
+        }
+        if (threadIdx.x == 0) {
+            P.stat_iters[sub] = 0; P.stat_outer[sub] = 0; P.stat_ok[sub] = 0; P.stat_res[sub] = 0.0;
+        }
+        return;
+    }
+    const int S = (int)Sd;
+    for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+        const long id = node(t);
+        A[id] = make_double2(P.xcur[id], P.ycur[id]);
+    }
+    __syncthreads();
+    for (int m = 0; m < S; ++m) {
+        const double f = __ddiv_rn((double)m, Sd);
+        for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+            const long id = node(t);
+            const int i = (int)(id % nx), j = (int)(id / nx);
+            auto val = [&](long nb, bool rim) -> double2 {
+                if (!rim) return A[nb];
+                const double px = P.xcur[nb], py = P.ycur[nb];
+                return make_double2(__dadd_rn(px, __dmul_rn(f, __dsub_rn(P.xnew[nb], px))),
+                                    __dadd_rn(py, __dmul_rn(f, __dsub_rn(P.ynew[nb], py))));
+            };
+            const double2 c = A[id];
+            const double2 vE = val(id + 1, i + 1 == i1), vW = val(id - 1, i - 1 == i0);
+            const double2 vN = val(id + nx, j + 1 == j1), vS = val(id - nx, j - 1 == j0);
+            const double cE = P.ce64[id], cW = P.ce64[id - 1], cN = P.cn64[id], cS = P.cn64[id - nx];
+            const double sx = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(cE, __dsub_rn(vE.x, c.x)), __dmul_rn(cW, __dsub_rn(vW.x, c.x))),
+                                                  __dmul_rn(cN, __dsub_rn(vN.x, c.x))), __dmul_rn(cS, __dsub_rn(vS.x, c.x)));
+            const double sy = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(cE, __dsub_rn(vE.y, c.y)), __dmul_rn(cW, __dsub_rn(vW.y, c.y))),
+                                                  __dmul_rn(cN, __dsub_rn(vN.y, c.y))), __dmul_rn(cS, __dsub_rn(vS.y, c.y)));
+            const double den = __dmul_rn(Sd, dP(id));
+            B[id] = make_double2(__dadd_rn(c.x, __ddiv_rn(sx, den)), __dadd_rn(c.y, __ddiv_rn(sy, den)));
+        }
+        __syncthreads();
+        double2* tmp = A;
+        A = B;
+        B = tmp;
+    }
+    for (int t = threadIdx.x; t < nint; t += blockDim.x) {
+        const long id = node(t);
+        P.xnew[id] = A[id].x;
+        P.ynew[id] = A[id].y;
+    }
+    if (threadIdx.x == 0) {
+        P.stat_iters[sub] = S; P.stat_outer[sub] = 0; P.stat_ok[sub] = 1; P.stat_res[sub] = 0.0;
+    }
+}
+
 // Subdomain `sub` of the problem described by P, solved by the calling CTA.
 template <typename TI>
 __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double* sh)
@@ -489,6 +589,37 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_const
     solve_body<TI>(P, blockIdx.x, sh);
 }
 
+__global__ void __launch_bounds__(kSolveThreads) fe_kernel(const __grid_constant__ SolveParams P)
+{
+    __shared__ double sh[40];
+    fe_body(P, blockIdx.x, sh);
+}
+
+// Batched problem record of CTA b: problem p with sub_off[p] <= b < sub_off[p + 1].
+__device__ __forceinline__ void batch_lookup(const SolveParams* probs, const int32_t* sub_off, int n,
+                                             SolveParams& sp, int& sub)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sub_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    sp = probs[lo];
+    sub = (int)blockIdx.x - sub_off[lo];
+}
+
+// Batched forward-Euler subdomains (CTAs of backward-Euler problems return at once).
+__global__ void __launch_bounds__(kSolveThreads) fe_batch_kernel(const SolveParams* probs, const int32_t* sub_off,
+                                                                 int n)
+{
+    __shared__ double sh[40];
+    __shared__ SolveParams sp;
+    __shared__ int sub;
+    if (threadIdx.x == 0) batch_lookup(probs, sub_off, n, sp, sub);
+    __syncthreads();
+    if (sp.scheme == 1) fe_body(sp, sub, sh);
+}
+
 // Batched: CTA b solves subdomain b - sub_off[p] of problem p, sub_off[p] <= b < sub_off[p + 1].
 template <typename TI>
 __global__ void __launch_bounds__(kSolveThreads) solve_batch_kernel(const SolveParams* probs,
@@ -497,17 +628,9 @@ __global__ void __launch_bounds__(kSolveThreads) solve_batch_kernel(const SolveP
     __shared__ double sh[32 * 8 + 8];
     __shared__ SolveParams sp;
     __shared__ int sub;
-    if (threadIdx.x == 0) {
-        int lo = 0, hi = n - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (sub_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
-        }
-        sp = probs[lo];
-        sub = (int)blockIdx.x - sub_off[lo];
-    }
+    if (threadIdx.x == 0) batch_lookup(probs, sub_off, n, sp, sub);
     __syncthreads();
-    solve_body<TI>(sp, sub, sh);
+    if (sp.scheme == 0) solve_body<TI>(sp, sub, sh);  // forward-Euler problems: fe_batch_kernel
 }
 
 }  // namespace
@@ -520,13 +643,16 @@ cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s)
 }
 
 cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
-                               bool fp64_inner, cudaStream_t s)
+                               bool fp64_inner, cudaStream_t s, bool any_be, bool any_fe)
 {
     if (total_subs <= 0) return cudaSuccess;
-    if (fp64_inner)
-        solve_batch_kernel<double><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
-    else
-        solve_batch_kernel<float><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+    if (any_be) {
+        if (fp64_inner)
+            solve_batch_kernel<double><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+        else
+            solve_batch_kernel<float><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+    }
+    if (any_fe) fe_batch_kernel<<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
     return cudaGetLastError();
 }
 
@@ -535,7 +661,9 @@ cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s)
     const long n = (long)P.nx * P.ny;
     faces_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(P, fp64_inner ? 1 : 0);
     const int nsub = P.px * P.py;
-    if (fp64_inner)
+    if (P.scheme == 1)
+        fe_kernel<<<nsub, kSolveThreads, 0, s>>>(P);
+    else if (fp64_inner)
         solve_kernel<double><<<nsub, kSolveThreads, 0, s>>>(P);
     else
         solve_kernel<float><<<nsub, kSolveThreads, 0, s>>>(P);

@@ -94,3 +94,21 @@ def test_batch_rejects_mixed_settings():
     with pytest.raises(S.SddError):
         S.SddBatch([a], stream=None, use_graph=True)   # graph mode needs a stream
     a.close(); b.close()
+
+
+def test_batch_mixing_subdomain_schemes_equals_alone():
+    """Forward-Euler problems (the paper's local solver) and backward-Euler ones in one batch."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    probs = [p.replace(subdomain_scheme=k % 2) for k, p in enumerate(small_mix(W.PREC_FP32_KAHAN, paths=2048, n=4))]
+    ref = meshes_alone(probs, 1)
+    hs = [gpu_problem(p) for p in probs]
+    with S.SddBatch(hs, stream=torch.cuda.Stream()) as b:
+        b.step()
+        st = b.stats()
+    assert st["solve_iters_max"] >= 1
+    for h, (rx, ry) in zip(hs, ref):
+        gx, gy = h.mesh()
+        assert np.array_equal(gx, rx) and np.array_equal(gy, ry)
+        h.close()

@@ -156,9 +156,15 @@ def _mesh_tolerance(prob, om, rims_x, rims_y, xn, yn, est_tol):
     return est_tol + worst + 1e-12
 
 
-@pytest.mark.parametrize("variant", ["c0", "periodic", "winslow", "uneven", "uneven_periodic"])
+@pytest.mark.parametrize("variant", ["c0", "periodic", "winslow", "uneven", "uneven_periodic",
+                                     "forward_euler", "forward_euler_winslow_periodic"])
 def test_full_step_fp64(S, variant):
     prob = W.c0_small_fp64()
+    if variant.startswith("forward_euler"):
+        # the paper's local solver: r = dt / tau = 1e-3 keeps the substep count near 15
+        prob = prob.replace(subdomain_scheme=1, tau=1.0, dt=1e-3)
+        if variant.endswith("periodic"):
+            prob = prob.replace(form=W.FORM_WINSLOW, periodic=1, px=3, py=2, monitor_params=[6.0, 40.0, 0.3, 0.6])
     if variant == "periodic":
         prob = prob.replace(periodic=1, monitor_params=[6.0, 40.0, 0.3, 0.6])
     elif variant == "winslow":
@@ -279,4 +285,20 @@ def test_front257_full_size_sampled_nodes(S, precision):
         close = np.abs(gv - ov).max(axis=1) <= (FP64_VAL if fp64 else FP32_VAL)
         assert same.mean() >= (0.999 if fp64 else 0.99)
         assert close.mean() >= (0.9 if fp64 else 0.9)
+    h.close()
+
+
+
+def test_forward_euler_substep_cap_leaves_interiors(S):
+    """A subdomain needing more forward-Euler substeps than fe_max_substeps is not solved: the step
+    reports SDD_ERR_NOT_CONVERGED and its interior keeps the previous mesh."""
+    prob = W.c0_small_fp64().replace(subdomain_scheme=1, fe_max_substeps=100)  # r = 1 needs ~1e4
+    x, y = W.sine_mode_mesh(prob, amp=0.02)
+    h = gpu_problem(prob, x, y)
+    gx = np.zeros_like(x)
+    gy = np.zeros_like(y)
+    status = S.lib.sdd_step(h.h, gx.ctypes.data, gy.ctypes.data)
+    assert status == S.SDD_ERR_NOT_CONVERGED
+    for (i0, i1, j0, j1) in subdomains(prob.nx, prob.ny, prob.px, prob.py):
+        assert np.array_equal(gx[j0 + 1:j1, i0 + 1:i1], x[j0 + 1:j1, i0 + 1:i1])
     h.close()

@@ -148,3 +148,57 @@ def test_periodic_scatter_applies_period_offsets():
         for j in range(j0, j1 + 1):
             for i in (i0, i1):
                 assert not np.isnan(bx[j, i])
+
+
+def test_forward_euler_periodic_mode_decay_closed_form():
+    """Constant omega on the periodic grid: the mode sin(2 pi xi) sin(2 pi eta) is an eigenvector of
+    the operator with eigenvalue r w mu, mu = 2 (4/h^2) sin^2(pi h); each of the S substeps
+    multiplies it by 1 - r w mu / S, S = ceil(4 r w / h^2) (the largest sum of coefficients)."""
+    import math
+    from oracle.solve import periodic_single_domain_step_fe
+    nx = 17
+    Lx, Ly = 2.0, 1.5
+    xi = np.arange(nx) / (nx - 1)
+    X, Y = np.meshgrid(xi, xi)
+    w0, dt, tau = 2.0, 1e-3, 1e-2
+    om = np.full((nx, nx), w0)
+    x1, y1 = periodic_single_domain_step_fe(om, Lx * X, Ly * Y, dt, tau, 0, Lx, Ly)
+    assert np.allclose(x1, Lx * X, atol=1e-13) and np.allclose(y1, Ly * Y, atol=1e-13)
+    A = 0.01
+    mode = np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y)
+    x1, y1 = periodic_single_domain_step_fe(om, Lx * X + A * mode, Ly * Y + A * mode, dt, tau, 0, Lx, Ly)
+    h = 1.0 / (nx - 1)
+    r = dt / tau
+    S = math.ceil(4 * r * w0 / h ** 2)
+    lam = r * w0 * 2 * (4 / h ** 2) * math.sin(math.pi * h) ** 2
+    fac = (1 - lam / S) ** S
+    assert np.allclose(x1, Lx * X + A * fac * mode, atol=1e-13)
+    assert np.allclose(y1, Ly * Y + A * fac * mode, atol=1e-13)
+
+
+def test_forward_euler_box_keeps_linear_meshes_and_counts_substeps():
+    from oracle.solve import solve_box_fe
+    nx = 17
+    xi = np.arange(nx) / (nx - 1)
+    X, Y = np.meshgrid(xi, xi)
+    om = np.full((nx, nx), 3.0)
+    xs, ys, order, S = solve_box_fe(om, X, Y, X, Y, 0, 8, 4, 16, 1e-3, 1e-2, 0)
+    want = np.array([X[j, i] for i, j in order]), np.array([Y[j, i] for i, j in order])
+    assert np.allclose(xs, want[0], atol=1e-14) and np.allclose(ys, want[1], atol=1e-14)
+    assert S == int(np.ceil(4 * 0.1 * 3.0 * 256 - 1e-9))
+
+
+def test_forward_euler_agrees_with_backward_euler_to_second_order():
+    """Both are first-order steps of the same linear ODE: FE - BE = O(r^2) on a smooth mesh."""
+    from oracle.solve import solve_box, solve_box_fe
+    nx = 17
+    xi = np.arange(nx) / (nx - 1)
+    X, Y = np.meshgrid(xi, xi)
+    om = 1.0 + 0.5 * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    xm = X + 0.02 * np.sin(np.pi * X) * np.sin(np.pi * Y)
+    errs = []
+    for dt in (1e-4, 5e-5):
+        fx, _, order, _ = solve_box_fe(om, X, Y, xm, Y, 0, 16, 0, 16, dt, 1.0, 0)
+        bx, _, _ = solve_box(om, X, Y, xm, Y, 0, 16, 0, 16, dt, 1.0, 0)
+        errs.append(np.abs(fx - bx).max())
+    assert errs[1] < errs[0] / 3.0   # second order in dt: halving dt quarters the gap

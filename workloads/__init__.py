@@ -56,6 +56,8 @@ class Problem:
     solve_rtol: float = 1e-12
     solve_max_iter: int = 20000
     iface_stride: int = 0          # > 1: Monte Carlo at every k-th node of each interface line
+    subdomain_scheme: int = 0      # 0 backward Euler, 1 forward Euler (the paper's, Sec. 3.5)
+    fe_max_substeps: int = 0       # forward Euler: refuse more substeps than this (0: 2^16)
     monitor_kind: int = MONITOR_GAUSS
     monitor_params: List[float] = field(default_factory=list)
     steps: int = 1
