@@ -107,6 +107,12 @@ typedef struct {
                                 time between the previous mesh and the new Dirichlet data      */
     int32_t fe_max_substeps; /* forward Euler: a subdomain needing more substeps is not solved
                                 (SDD_ERR_NOT_CONVERGED, interior left at x^n); 0 means 2^16     */
+    int32_t moving_boundary; /* 0: boundary mesh fixed at (Lx xi, Ly eta); 1 (Dirichlet only): the
+                                tangential components -- x along eta = 0, 1 and y along xi = 0, 1 --
+                                take one backward-Euler step of the 1-D generator along their side
+                                before the interface Monte Carlo (Sec. 2); exiting paths then take
+                                the new boundary mesh, linearly interpolated along the exit side.
+                                The normal components and the corners stay fixed.            */
 } sdd_params;
 
 typedef struct {
@@ -380,7 +386,9 @@ void sdd_server_destroy(sdd_server* s);
  * sdd_interface_mc in fixed-N mode (same Philox streams, same node ids, same estimates) for
  * the nodal monitor `omega` on the mesh (x, y) at time-step index `step_index`, and allocates
  * nothing: no cudaMalloc, no cudaFree, no allocating library routine.
- *   params : as for sdd_create_problem, with se_target == 0 (fixed paths_per_node).
+ *   params : as for sdd_create_problem, with se_target == 0 (fixed paths_per_node), every
+ *            interface node sampled (iface_stride <= 1), a fixed boundary (moving_boundary ==
+ *            0) and an equal split ((nx-1) % px == 0, (ny-1) % py == 0).
  *   x, y, omega : nx*ny doubles in DEVICE memory (read); est_xy, se_xy : M x 2 doubles in
  *            DEVICE memory (written, same layout as sdd_interface_mc).
  *   stream : cudaStream_t for all work (NULL = legacy default stream); the call returns

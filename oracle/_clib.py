@@ -40,7 +40,7 @@ def _problem_struct(real):
                                             "bb_test", "tstep")]
     fields += [("key0", ctypes.c_uint32), ("key1", ctypes.c_uint32)]
     fields += [(n, ctypes.c_double) for n in ("Lx", "Ly", "tau", "dt")]
-    fields += [(n, ctypes.POINTER(real)) for n in ("w", "w_xi", "w_eta", "X", "Y")]
+    fields += [(n, ctypes.POINTER(real)) for n in ("w", "w_xi", "w_eta", "X", "Y", "bnd")]
 
     class OracleProblem(ctypes.Structure):
         _fields_ = fields

@@ -28,11 +28,12 @@ class PathInputs:
     keep: tuple  # arrays referenced by the struct
 
 
-def prepare(prob, x, y, omega, tstep: int, real=np.float64) -> PathInputs:
+def prepare(prob, x, y, omega, tstep: int, real=np.float64, bnd=None) -> PathInputs:
     """Pack the frozen monitor, its FD gradient and the mesh displacement for the C core.
 
     The monitor and its gradient are computed in FP64 and rounded once to the working
-    precision; so is the displacement X = x - Lx xi, Y = y - Ly eta of the previous mesh.
+    precision; so is the displacement X = x - Lx xi, Y = y - Ly eta of the previous mesh, and
+    the new boundary mesh bnd of a moving boundary (oracle.boundary layout; None: identity).
     """
     real = np.dtype(real).type
     wxi, weta = fd_gradient(omega, prob.periodic)
@@ -41,6 +42,8 @@ def prepare(prob, x, y, omega, tstep: int, real=np.float64) -> PathInputs:
     X = np.asarray(x, dtype=np.float64) - prob.Lx * xi[None, :]
     Y = np.asarray(y, dtype=np.float64) - prob.Ly * eta[:, None]
     arrs = tuple(np.ascontiguousarray(a, dtype=real) for a in (omega, wxi, weta, X, Y))
+    if bnd is not None:
+        arrs = arrs + (np.ascontiguousarray(bnd, dtype=real),)
     ct = _clib.ctypes.c_float if real is np.float32 else _clib.ctypes.c_double
     S = _clib.ProblemF32 if real is np.float32 else _clib.ProblemF64
     seed = int(prob.seed) & 0xFFFFFFFFFFFFFFFF
@@ -48,7 +51,7 @@ def prepare(prob, x, y, omega, tstep: int, real=np.float64) -> PathInputs:
           bicubic=prob.bicubic, bb_test=prob.bb_test, tstep=int(tstep),
           key0=seed & 0xFFFFFFFF, key1=seed >> 32, Lx=prob.Lx, Ly=prob.Ly, tau=prob.tau,
           dt=prob.dt)
-    for name, a in zip(("w", "w_xi", "w_eta", "X", "Y"), arrs):
+    for name, a in zip(("w", "w_xi", "w_eta", "X", "Y", "bnd"), arrs):
         setattr(s, name, a.ctypes.data_as(_clib.ctypes.POINTER(ct)))
     return PathInputs(real=real, struct=s, keep=arrs)
 
@@ -122,7 +125,7 @@ def next_total(n_done: int, se: float, target: float, max_paths: int) -> int:
     return int(min(total, max_paths))
 
 
-def interface_mc(prob, x, y, omega, nodes, tstep: int, real=np.float64):
+def interface_mc(prob, x, y, omega, nodes, tstep: int, real=np.float64, bnd=None):
     """Estimates at all interface nodes for one step.
 
     Fixed N (prob.se_target == 0): paths 0..N-1 of every node.  Adaptive (se_target > 0):
@@ -139,7 +142,7 @@ def interface_mc(prob, x, y, omega, nodes, tstep: int, real=np.float64):
         sampled, fill = interface_sampling(prob.nx, prob.ny, prob.px, prob.py, prob.periodic, stride,
                                            prob.Lx, prob.Ly)
         nodes = np.asarray(nodes, dtype=np.int32)
-        sub = _interface_mc_ids(prob, x, y, omega, nodes, np.nonzero(sampled)[0].astype(np.int32), tstep, real)
+        sub = _interface_mc_ids(prob, x, y, omega, nodes, np.nonzero(sampled)[0].astype(np.int32), tstep, real, bnd)
         M = len(nodes)
         est = np.full((M, 2), np.nan)
         se = np.zeros((M, 2))
@@ -148,12 +151,12 @@ def interface_mc(prob, x, y, omega, nodes, tstep: int, real=np.float64):
         est[sampled], se[sampled], n_used[sampled], steps[sampled] = sub
         return fill(est), se, n_used, steps
     nodes = np.asarray(nodes, dtype=np.int32)
-    return _interface_mc_ids(prob, x, y, omega, nodes, np.arange(len(nodes), dtype=np.int32), tstep, real)
+    return _interface_mc_ids(prob, x, y, omega, nodes, np.arange(len(nodes), dtype=np.int32), tstep, real, bnd)
 
 
-def _interface_mc_ids(prob, x, y, omega, all_nodes, ids, tstep, real):
+def _interface_mc_ids(prob, x, y, omega, all_nodes, ids, tstep, real, bnd=None):
     """interface_mc over the nodes all_nodes[ids], each with its own node id in the counter."""
-    inp = prepare(prob, x, y, omega, tstep, real)
+    inp = prepare(prob, x, y, omega, tstep, real, bnd)
     nodes = all_nodes[ids]
     M = len(nodes)
     shift = np.stack([x[nodes[:, 1], nodes[:, 0]], y[nodes[:, 1], nodes[:, 0]]], axis=1)

@@ -53,7 +53,22 @@ typedef struct {
     const REAL* w_eta;   /* d omega / d eta at the nodes                                         */
     const REAL* X;       /* previous mesh displacement x - Lx xi at the nodes                    */
     const REAL* Y;       /* previous mesh displacement y - Ly eta at the nodes                   */
+    const REAL* bnd;     /* moving boundary (NULL: the identity): tangential coordinate of the
+                            new boundary mesh, x on eta = 0 (nx values) and eta = 1 (nx), then y
+                            on xi = 0 (ny) and xi = 1 (ny)                                      */
 } NAME(oracle_problem);
+
+/* Linear interpolation of the n values b (nodes s = k / (n - 1)) at s in [0, 1]. */
+static REAL NAME(side_lerp)(const REAL* b, int n, REAL s)
+{
+    REAL u = s * (REAL)(n - 1);
+    REAL fl = R_FLOOR(u);
+    long c = (long)fl;
+    if (c < 0) c = 0;
+    if (c > n - 2) c = n - 2;
+    REAL f = u - (REAL)c;
+    return ((REAL)1 - f) * b[c] + f * b[c + 1];
+}
 
 /* Uniform deviate in (0, 1) from one 32-bit Philox word, formed without rounding:
  * FP64: (w + 1/2) 2^-32;  FP32: (floor(w / 2^9) + 1/2) 2^-23 (24 significant bits). */
@@ -214,7 +229,8 @@ static double NAME(gap4)(const REAL v[4], int s)
  *     crosses side s with probability exp(-d0_s d1_s / (D ds)); the path exits if the
  *     uniform exceeds prod_s (1 - p_s), through the side of largest p_s, at the point on
  *     that side that keeps phi''s other coordinate.
- * The exit value is the boundary mesh at the exit point, (Lx xi_e, Ly eta_e).  A path that
+ * The exit value is the boundary mesh at the exit point: (Lx xi_e, Ly eta_e), or with a
+ * moving boundary (Sec. 2) the new boundary mesh linearly interpolated along the exit side.  A path that
  * completes K substeps takes the previous mesh at its final point: (Lx xi_K + X(phi_K),
  * Ly eta_K + Y(phi_K)) with X, Y interpolated (periodic: indices wrap, the linear part
  * carries the period offset).
@@ -295,8 +311,19 @@ void NAME(oracle_path)(const NAME(oracle_problem)* P, uint32_t m, int i0, int j0
                 if (s == 1) xe = 1;
                 if (s == 2) ee = 0;
                 if (s == 3) ee = 1;
-                *vx = (double)(Lx * xe);
-                *vy = (double)(Ly * ee);
+                if (P->bnd) {   /* the new boundary mesh along the exit side */
+                    const REAL* b = P->bnd;
+                    REAL bx, by;
+                    if (s == 0) { bx = 0; by = NAME(side_lerp)(b + 2 * nx, ny, ee); }
+                    else if (s == 1) { bx = Lx; by = NAME(side_lerp)(b + 2 * nx + ny, ny, ee); }
+                    else if (s == 2) { bx = NAME(side_lerp)(b, nx, xe); by = 0; }
+                    else { bx = NAME(side_lerp)(b + nx, nx, xe); by = Ly; }
+                    *vx = (double)bx;
+                    *vy = (double)by;
+                } else {
+                    *vx = (double)(Lx * xe);
+                    *vy = (double)(Ly * ee);
+                }
                 *steps = k + 1;
                 *side = s;
                 *margin = mg;

@@ -26,7 +26,7 @@ def monitor_on_mesh(prob, x, y, t, omega_nodal=None):
                             prob.Lx, prob.Ly)
 
 
-def scatter(prob, nodes, est):
+def scatter(prob, nodes, est, bnd=None):
     """New-mesh arrays holding the Dirichlet data of every subdomain rim.
 
     Dirichlet: the physical boundary keeps the identity mesh (Lx xi, Ly eta); interface
@@ -37,7 +37,10 @@ def scatter(prob, nodes, est):
     nx, ny = prob.nx, prob.ny
     bx = np.full((ny, nx), np.nan)
     by = np.full((ny, nx), np.nan)
-    if not prob.periodic:
+    if bnd is not None:           # moving boundary: the new boundary mesh (oracle.boundary)
+        from .boundary import boundary_arrays
+        bx, by = boundary_arrays(prob, bnd)
+    elif not prob.periodic:
         xi = np.arange(nx) / (nx - 1)
         eta = np.arange(ny) / (ny - 1)
         bx[0, :] = prob.Lx * xi; bx[-1, :] = prob.Lx * xi
@@ -79,11 +82,15 @@ def step(prob, x, y, t, tstep, omega_nodal=None, real=np.float64):
     """x^n -> x^{n+1}.  Returns dict with the new mesh, interface estimates, SE, paths, steps."""
     omega = monitor_on_mesh(prob, x, y, t, omega_nodal)
     nodes = interface_nodes(prob.nx, prob.ny, prob.px, prob.py, prob.periodic)
-    est, se, n_used, steps = interface_mc(prob, x, y, omega, nodes, tstep, real)
-    bx, by = scatter(prob, nodes, est)
+    bnd = None
+    if int(getattr(prob, "moving_boundary", 0)):
+        from .boundary import boundary_mesh_step
+        bnd = boundary_mesh_step(prob, omega, x, y)   # the boundary first (Sec. 2), then the interfaces
+    est, se, n_used, steps = interface_mc(prob, x, y, omega, nodes, tstep, real, bnd)
+    bx, by = scatter(prob, nodes, est, bnd)
     xn1, yn1 = subdomain_solves(prob, omega, bx, by, x, y)
     return dict(x=xn1, y=yn1, est=est, se=se, n_used=n_used, steps=steps, omega=omega,
-                nodes=nodes)
+                nodes=nodes, bnd=bnd)
 
 
 def mkp_step(prob, x, y, t, tstep, K, omega_nodal=None, real=np.float64):

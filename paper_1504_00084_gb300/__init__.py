@@ -39,7 +39,8 @@ class SddParams(ctypes.Structure):
                 ("tau", ctypes.c_double), ("dt", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("paths_per_node", ctypes.c_int64), ("max_paths_per_node", ctypes.c_int64),
                 ("se_target", ctypes.c_double), ("solve_rtol", ctypes.c_double), ("t0", ctypes.c_double),
-                ("subdomain_scheme", ctypes.c_int32), ("fe_max_substeps", ctypes.c_int32)]
+                ("subdomain_scheme", ctypes.c_int32), ("fe_max_substeps", ctypes.c_int32),
+                ("moving_boundary", ctypes.c_int32)]
 
 
 class SddStats(ctypes.Structure):

@@ -179,6 +179,9 @@ sdd_status validate(const sdd_params* P)
     if (P->subdomain_scheme != 0 && P->subdomain_scheme != 1)
         return fail(SDD_ERR_INVALID_ARG, "subdomain_scheme must be 0 or 1");
     if (P->fe_max_substeps < 0) return fail(SDD_ERR_INVALID_ARG, "fe_max_substeps must be >= 0");
+    if (P->moving_boundary != 0 && P->moving_boundary != 1)
+        return fail(SDD_ERR_INVALID_ARG, "moving_boundary must be 0 or 1");
+    if (P->moving_boundary && P->periodic) return fail(SDD_ERR_INVALID_ARG, "a periodic domain has no boundary to move");
     return SDD_OK;
 }
 
@@ -208,7 +211,9 @@ sdd_status check_boundary(const sdd_problem* p, const double* x, const double* y
         return fail(SDD_ERR_INVALID_ARG, "mesh pointers are not readable");
     }
     if (!sdd_boundary_ok(p->prm, hx.data(), hy.data()))
-        return fail(SDD_ERR_INVALID_ARG, "Dirichlet mesh must equal (Lx xi, Ly eta) on the boundary");
+        return fail(SDD_ERR_INVALID_ARG, p->prm.moving_boundary
+                                             ? "boundary mesh must have x = 0, Lx on xi = 0, 1 and y = 0, Ly on eta = 0, 1"
+                                             : "Dirichlet mesh must equal (Lx xi, Ly eta) on the boundary");
     return SDD_OK;
 }
 
@@ -224,6 +229,8 @@ sdd_status run_prep(sdd_problem* p)
     memcpy(P.params, p->mon_params, sizeof(P.params));
     P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64;
     P.mon = p->mon; P.disp = p->disp; P.bad = p->bad;
+    P.moving_boundary = p->prm.moving_boundary; P.form = p->prm.form; P.r = p->prm.dt / p->prm.tau;
+    P.bnd64 = p->bnd64; P.bnd = p->bnd; P.bnd_scratch = p->bnd_scratch;
     SDD_CK(cudaMemsetAsync(p->bad, 0, 4, p->stream));
     SDD_CK(launch_prep(P, p->stream));
     p->launches += 2;
@@ -370,7 +377,7 @@ sdd_status run_mc(sdd_problem* p)
 sdd_status run_solve(sdd_problem* p)
 {
     SDD_CK(launch_scatter(p->prm.nx, p->prm.ny, p->prm.periodic, p->prm.Lx, p->prm.Ly, p->nodes, p->M,
-                          p->est, p->xn, p->yn, p->stream));
+                          p->est, p->xn, p->yn, p->stream, p->prm.moving_boundary ? p->bnd64 : nullptr));
     p->launches += (p->prm.periodic ? 0 : 1) + (p->M > 0 ? 1 : 0);
     SolveParams S{};
     S.nx = p->prm.nx; S.ny = p->prm.ny; S.px = p->prm.px; S.py = p->prm.py; S.form = p->prm.form;
@@ -444,6 +451,10 @@ void problem_arrays(sdd_problem* p, bool with_mc, F&& f)
     f((void**)&p->quality, (N + 2) * 8);
     f((void**)&p->mg, p->mg_stride * ns);
     f((void**)&p->bad, 16);
+    const size_t nb = 2 * (size_t)q.nx + 2 * (size_t)q.ny;
+    f((void**)&p->bnd64, nb * 8);
+    f((void**)&p->bnd, nb * rs);
+    f((void**)&p->bnd_scratch, 2 * nb * 8);
 }
 
 // Problem shell: parameters, interface layout, sizes; no device memory yet.
@@ -549,6 +560,11 @@ bool sdd_boundary_ok(const sdd_params& prm, const double* hx, const double* hy)
             const double bx = prm.Lx * ((double)i / (double)(nx - 1));
             const double by = prm.Ly * ((double)j / (double)(ny - 1));
             const size_t id = (size_t)j * nx + i;
+            if (prm.moving_boundary) {  // only the normal components are fixed
+                if ((i == 0 || i == nx - 1) && !(fabs(hx[id] - bx) <= tol)) return false;
+                if ((j == 0 || j == ny - 1) && !(fabs(hy[id] - by) <= tol)) return false;
+                continue;
+            }
             if (!(fabs(hx[id] - bx) <= tol) || !(fabs(hy[id] - by) <= tol)) return false;
         }
     return true;

@@ -183,6 +183,8 @@ sdd_status record_step(sdd_batch* b)
         memcpy(P.params, p->mon_params, sizeof(P.params));
         P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
         P.bad = p->bad;
+        P.moving_boundary = p->prm.moving_boundary; P.form = p->prm.form; P.r = p->prm.dt / p->prm.tau;
+        P.bnd64 = p->bnd64; P.bnd = p->bnd; P.bnd_scratch = p->bnd_scratch;
         B_CK(cudaMemsetAsync(p->bad, 0, 4, b->stream));
         B_CK(launch_prep(P, b->stream));
         launches += 2;
@@ -249,7 +251,8 @@ sdd_status record_step(sdd_batch* b)
     for (int i = 0; i < b->n; ++i) {
         sdd_problem* p = b->probs[i];
         B_CK(launch_scatter(p->prm.nx, p->prm.ny, p->prm.periodic, p->prm.Lx, p->prm.Ly, p->nodes, p->M,
-                            b->est + 2 * (size_t)b->node_off[i], p->xn, p->yn, b->stream));
+                            b->est + 2 * (size_t)b->node_off[i], p->xn, p->yn, b->stream,
+                            p->prm.moving_boundary ? p->bnd64 : nullptr));
         launches += (p->prm.periodic ? 0 : 1) + (p->M > 0 ? 1 : 0);
         B_CK(launch_faces(b->solve_host[i], fp64_inner, b->stream));
         launches += 1;

@@ -86,6 +86,7 @@ template <typename T> struct McProblem {
     T Lx, Ly;
     uint32_t key0, key1, tstep;
     int32_t node_offset;       // global index of the problem's node 0 in the launch's node arrays
+    const T* bnd;              // moving boundary: tangential boundary coordinates (null: identity)
 };
 
 template <typename T> struct McParams {
@@ -156,6 +157,12 @@ struct PrepParams {
     void* mon;                 // out: Mon4<T>
     void* disp;                // out: Disp2<T>
     int32_t* bad;              // out (nullable): set to 1 if omega <= 0 or anything is not finite
+    // moving boundary (Sec. 2): one backward-Euler step of the 1-D generator along each side
+    int moving_boundary, form;
+    double r;                  // dt / tau
+    double* bnd64;             // out: [x on eta=0 (nx), x on eta=1 (nx), y on xi=0 (ny), y on xi=1 (ny)]
+    void* bnd;                 // out: the same in the path precision
+    double* bnd_scratch;       // 2 (2 nx + 2 ny) doubles
 };
 
 struct SolveParams {
@@ -231,8 +238,10 @@ cudaError_t launch_quality(int nx, int ny, const double* x, const double* y, dou
                            cudaStream_t s);
 cudaError_t launch_shift(const int2* nodes, int M, int nx, const double* x, const double* y,
                          double* shift, cudaStream_t s);
+// bnd64 (nullable): the moving boundary's new tangential coordinates (PrepParams layout)
 cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, const int2* nodes,
-                           int M, const double* est, double* xnew, double* ynew, cudaStream_t s);
+                           int M, const double* est, double* xnew, double* ynew, cudaStream_t s,
+                           const double* bnd64 = nullptr);
 // role (nullable): per node, -1 = estimated by Monte Carlo, >= 0 = interpolated (never planned)
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
                            int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s,

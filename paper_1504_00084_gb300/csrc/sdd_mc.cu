@@ -250,6 +250,17 @@ __device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
 template <typename T>
 __device__ __forceinline__ T clamp01(T v) { return v < 0 ? (T)0 : (v > 1 ? (T)1 : v); }
 
+// Linear interpolation along one side of the n boundary values b (nodes s = k / (n - 1)).
+template <typename T>
+__device__ __forceinline__ T side_lerp(const T* b, int n, T s)
+{
+    const T u = s * (T)(n - 1);
+    int c = (int)dfloor(u);
+    c = c < 0 ? 0 : (c > n - 2 ? n - 2 : c);
+    const T f = u - (T)c;
+    return ((T)1 - f) * b[c] + f * b[c + 1];
+}
+
 // Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; zero
 // where the exponential is too small to change 1 - p (and then cannot be the largest p of an
 // exiting path).
@@ -335,8 +346,15 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
             if (s == 1) xe = 1;
             if (s == 2) ee = 0;
             if (s == 3) ee = 1;
-            vx = P.Lx * xe;
-            vy = P.Ly * ee;
+            if (P.bnd) {  // moving boundary: the new boundary mesh along the exit side
+                if (s == 0) { vx = (T)0; vy = side_lerp(P.bnd + 2 * P.nx, P.ny, ee); }
+                else if (s == 1) { vx = P.Lx; vy = side_lerp(P.bnd + 2 * P.nx + P.ny, P.ny, ee); }
+                else if (s == 2) { vx = side_lerp(P.bnd, P.nx, xe); vy = (T)0; }
+                else { vx = side_lerp(P.bnd + P.nx, P.nx, xe); vy = P.Ly; }
+            } else {
+                vx = P.Lx * xe;
+                vy = P.Ly * ee;
+            }
             side = s;
             return 1;
         }

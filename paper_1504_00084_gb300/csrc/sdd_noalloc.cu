@@ -202,7 +202,7 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
     if ((P->periodic != 0 && P->periodic != 1) || (P->form != SDD_FORM_DIV && P->form != SDD_FORM_WINSLOW) ||
         P->precision < SDD_FP64 || P->precision > SDD_FP32_KAHAN || (P->bicubic != 0 && P->bicubic != 1) ||
         (P->bb_test != 0 && P->bb_test != 1) || P->substeps < 1 || P->substeps > (1 << 20) ||
-        P->iface_stride > 1 || P->iface_stride < 0)
+        P->iface_stride > 1 || P->iface_stride < 0 || P->moving_boundary != 0)
         return SDD_ERR_INVALID_ARG;
     if (!(P->Lx > 0) || !(P->Ly > 0) || !(P->tau > 0) || !(P->dt > 0) || P->se_target != 0.0 ||
         P->paths_per_node < 2 || P->paths_per_node > (int64_t(1) << 31))

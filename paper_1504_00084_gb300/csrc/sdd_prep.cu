@@ -139,16 +139,69 @@ __global__ void shift_kernel(const int2* nodes, int M, int nx, const double* x, 
 }
 
 __global__ void scatter_boundary_kernel(int nx, int ny, double Lx, double Ly, double* xnew,
-                                        double* ynew)
+                                        double* ynew, const double* bnd)
 {
     const int n = nx * ny;
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
         const int i = id % nx, j = id / nx;
         if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
-            xnew[id] = Lx * ((double)i / (double)(nx - 1));
-            ynew[id] = Ly * ((double)j / (double)(ny - 1));
+            double vx = Lx * ((double)i / (double)(nx - 1));
+            double vy = Ly * ((double)j / (double)(ny - 1));
+            if (bnd) {  // moving boundary: tangential components from the 1-D step
+                if (j == 0) vx = bnd[i];
+                else if (j == ny - 1) vx = bnd[nx + i];
+                if (i == 0) vy = bnd[2 * nx + j];
+                else if (i == nx - 1) vy = bnd[2 * nx + ny + j];
+            }
+            xnew[id] = vx;
+            ynew[id] = vy;
         }
     }
+}
+
+// One backward-Euler step of the 1-D generator along each side of a Dirichlet domain (Sec. 2):
+// side s (thread s) carries the tangential coordinate b_k at its n nodes -- x along eta = 0
+// (s = 0) and eta = 1 (s = 1), y along xi = 0 (s = 2) and xi = 1 (s = 3) -- and solves
+//   d_k b_k + r sum_{nb = k +- 1} c_{k,nb} (b_k - b_nb) = d_k b^n_k,  k = 1 .. n-2,
+//   c_{k,k+1} = (omega_k + omega_{k+1}) / 2 / h^2,  d_k = 1 (form 0) or omega_k (form 1),
+// with the corner values fixed, by the tridiagonal (Thomas) sweeps; the system is a
+// diagonally dominant M-matrix.
+template <typename T>
+__global__ void boundary_kernel(const PrepParams P)
+{
+    const int s = threadIdx.x;
+    if (s >= 4) return;
+    const int nx = P.nx, ny = P.ny;
+    const int n = s < 2 ? nx : ny;
+    const long off = s == 0 ? 0 : s == 1 ? nx : s == 2 ? 2L * nx : 2L * nx + ny;
+    auto id = [&](int k) -> long {
+        return s == 0 ? k : s == 1 ? (long)(ny - 1) * nx + k : s == 2 ? (long)k * nx : (long)k * nx + nx - 1;
+    };
+    auto coord = [&](int k) -> double { return s < 2 ? P.x[id(k)] : P.y[id(k)]; };
+    double* b = P.bnd64 + off;
+    double* cp = P.bnd_scratch + 2 * off;
+    double* dp = cp + n;
+    const double h2 = (double)(n - 1) * (double)(n - 1);
+    b[0] = coord(0);
+    b[n - 1] = coord(n - 1);
+    for (int k = 1; k <= n - 2; ++k) {
+        const double w = P.om64[id(k)];
+        const double cw = __dmul_rn(P.r, __dmul_rn(__dmul_rn(0.5, __dadd_rn(w, P.om64[id(k - 1)])), h2));
+        const double ce = __dmul_rn(P.r, __dmul_rn(__dmul_rn(0.5, __dadd_rn(w, P.om64[id(k + 1)])), h2));
+        const double d = P.form == 1 ? w : 1.0;
+        const double diag = __dadd_rn(__dadd_rn(d, cw), ce);
+        double rhs = __dmul_rn(d, coord(k));
+        double lower = -cw, upper = -ce;
+        if (k == 1) { rhs = __dadd_rn(rhs, __dmul_rn(cw, b[0])); lower = 0.0; }
+        if (k == n - 2) { rhs = __dadd_rn(rhs, __dmul_rn(ce, b[n - 1])); upper = 0.0; }
+        const double m = k == 1 ? diag : __dsub_rn(diag, __dmul_rn(lower, cp[k - 1]));
+        cp[k] = __ddiv_rn(upper, m);
+        dp[k] = __ddiv_rn(k == 1 ? rhs : __dsub_rn(rhs, __dmul_rn(lower, dp[k - 1])), m);
+    }
+    if (n > 2) b[n - 2] = dp[n - 2];
+    for (int k = n - 3; k >= 1; --k) b[k] = __dsub_rn(dp[k], __dmul_rn(cp[k], b[k + 1]));
+    T* bt = static_cast<T*>(P.bnd) + off;
+    for (int k = 0; k < n; ++k) bt[k] = (T)b[k];
 }
 
 __global__ void scatter_iface_kernel(int nx, int ny, int periodic, double Lx, double Ly,
@@ -233,6 +286,12 @@ cudaError_t launch_prep(const PrepParams& P, cudaStream_t s)
         prep_pack_kernel<double><<<blocks, threads, 0, s>>>(P);
     else
         prep_pack_kernel<float><<<blocks, threads, 0, s>>>(P);
+    if (P.moving_boundary && !P.periodic) {
+        if (P.precision == 0)
+            boundary_kernel<double><<<1, 32, 0, s>>>(P);
+        else
+            boundary_kernel<float><<<1, 32, 0, s>>>(P);
+    }
     return cudaGetLastError();
 }
 
@@ -253,11 +312,12 @@ cudaError_t launch_shift(const int2* nodes, int M, int nx, const double* x, cons
 }
 
 cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, const int2* nodes,
-                           int M, const double* est, double* xnew, double* ynew, cudaStream_t s)
+                           int M, const double* est, double* xnew, double* ynew, cudaStream_t s,
+                           const double* bnd64)
 {
     if (!periodic)
         scatter_boundary_kernel<<<blocks_for((long)nx * ny, 256), 256, 0, s>>>(nx, ny, Lx, Ly, xnew,
-                                                                               ynew);
+                                                                               ynew, bnd64);
     if (M > 0)
         scatter_iface_kernel<<<blocks_for(M, 256), 256, 0, s>>>(nx, ny, periodic, Lx, Ly, nodes, M, est,
                                                                 xnew, ynew);

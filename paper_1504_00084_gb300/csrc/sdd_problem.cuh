@@ -55,6 +55,9 @@ struct sdd_problem {
     double* st_res = nullptr;
     double* quality = nullptr;      // (nx-1)(ny-1) cell qualities + 2 stats
     int32_t* bad = nullptr;         // set by the monitor preparation on invalid monitor or mesh
+    double* bnd64 = nullptr;        // moving boundary: new tangential boundary coordinates (FP64)
+    void* bnd = nullptr;            //   the same in the path precision
+    double* bnd_scratch = nullptr;  //   tridiagonal sweeps
     // host
     int32_t* h_n_active = nullptr;  // pinned: [0] active nodes, [1] invalid-input flag
     sdd_stats stats{};
@@ -115,6 +118,7 @@ inline sdd::McProblem<T> mc_problem(const sdd_problem* p)
     R.key1 = (uint32_t)(p->prm.seed >> 32);
     R.tstep = (uint32_t)p->step;
     R.node_offset = 0;
+    R.bnd = p->prm.moving_boundary ? static_cast<const T*>(p->bnd) : nullptr;
     return R;
 }
 

@@ -342,6 +342,8 @@ sdd_status admit(sdd_server* s, Request* r)
     memcpy(P.params, r->mon_params, sizeof(P.params));
     P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
     P.bad = s->slot_bad + r->slot;
+    P.moving_boundary = r->prm.moving_boundary; P.form = r->prm.form; P.r = r->prm.dt / r->prm.tau;
+    P.bnd64 = p->bnd64; P.bnd = p->bnd; P.bnd_scratch = p->bnd_scratch;
     S_CK(cudaMemsetAsync(P.bad, 0, 4, s->stream));
     S_CK(launch_prep(P, s->stream));
     s->st.kernel_launches += 2;
@@ -381,7 +383,7 @@ sdd_status finish(sdd_server* s, Request* r)
         s->st.kernel_launches += 1 + (p->n_interp > 0 ? 1 : 0);
     }
     S_CK(launch_scatter(r->prm.nx, r->prm.ny, r->prm.periodic, r->prm.Lx, r->prm.Ly, p->nodes, r->M,
-                        s->est + 2 * o, p->xn, p->yn, s->fin));
+                        s->est + 2 * o, p->xn, p->yn, s->fin, r->prm.moving_boundary ? p->bnd64 : nullptr));
     s->st.kernel_launches += (r->prm.periodic ? 0 : 1) + (r->M > 0 ? 1 : 0);
     SolveParams S{};
     S.nx = r->prm.nx; S.ny = r->prm.ny; S.px = r->prm.px; S.py = r->prm.py; S.form = r->prm.form;

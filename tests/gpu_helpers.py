@@ -27,7 +27,11 @@ def gpu_problem(prob, x=None, y=None, omega=None):
 
 def oracle_inputs(prob, x, y, t, tstep, omega=None):
     om = monitor_on_mesh(prob, x, y, t, omega)
-    inp = mc.prepare(prob, x, y, om, tstep, real_of(prob))
+    bnd = None
+    if getattr(prob, "moving_boundary", 0):
+        from oracle.boundary import boundary_mesh_step
+        bnd = boundary_mesh_step(prob, om, x, y)
+    inp = mc.prepare(prob, x, y, om, tstep, real_of(prob), bnd)
     nodes = interface_nodes(prob.nx, prob.ny, prob.px, prob.py, prob.periodic)
     return om, inp, nodes
 

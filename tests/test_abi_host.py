@@ -67,7 +67,9 @@ def base_params(sdd, **kw):
 @pytest.mark.parametrize("field,value", [("nx", 2), ("px", 40), ("py", 0), ("substeps", 0),
                                          ("paths_per_node", 1), ("iface_stride", -1), ("tau", 0.0),
                                          ("precision", 7), ("form", 2), ("solve_rtol", 0.0),
-                                         ("periodic", 2), ("se_target", -1.0)])
+                                         ("periodic", 2), ("se_target", -1.0),
+                                         ("moving_boundary", 2), ("subdomain_scheme", 3),
+                                         ("fe_max_substeps", -1)])
 def test_invalid_params_rejected_before_any_device_work(sdd, field, value):
     import workloads as W
     p = base_params(sdd)
@@ -122,3 +124,12 @@ def test_interface_sampling_matches_oracle(sdd, periodic, shape, stride):
     got = sdd.sdd_interface_sampling(p)
     want, _ = interface_sampling(nx, ny, px, py, periodic, stride)
     assert np.array_equal(got, want)
+
+
+
+def test_moving_boundary_needs_a_dirichlet_domain(sdd):
+    p = base_params(sdd, periodic=1, moving_boundary=1)
+    x = np.zeros((p.ny, p.nx))
+    h = ctypes.c_void_p()
+    assert sdd.lib.sdd_create_problem(ctypes.byref(p), x.ctypes.data, x.ctypes.data, None,
+                                      ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG

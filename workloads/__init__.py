@@ -58,6 +58,7 @@ class Problem:
     iface_stride: int = 0          # > 1: Monte Carlo at every k-th node of each interface line
     subdomain_scheme: int = 0      # 0 backward Euler, 1 forward Euler (the paper's, Sec. 3.5)
     fe_max_substeps: int = 0       # forward Euler: refuse more substeps than this (0: 2^16)
+    moving_boundary: int = 0       # 1: tangential boundary coordinates follow the 1-D generator
     monitor_kind: int = MONITOR_GAUSS
     monitor_params: List[float] = field(default_factory=list)
     steps: int = 1
