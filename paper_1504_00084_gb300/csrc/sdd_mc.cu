@@ -143,9 +143,9 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
     T fx, fy;
     locate(P.nx, P.periodic, xi, i, fx);
     locate(P.ny, P.periodic, eta, j, fy);
-    const Mon4<T>* r0 = P.mon + (long)j * P.nx + i;
-    const Mon4<T> a = load_mon(r0), b = load_mon(r0 + 1);
-    const Mon4<T> c = load_mon(r0 + P.nx), d = load_mon(r0 + P.nx + 1);
+    const int base = j * P.nx + i;  // grids hold at most 2^28 nodes
+    const Mon4<T> a = load_mon(P.mon + base), b = load_mon(P.mon + (base + 1));
+    const Mon4<T> c = load_mon(P.mon + (base + P.nx)), d = load_mon(P.mon + (base + P.nx + 1));
     const T gx = 1 - fx, gy = 1 - fy;
     const T w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
     w = w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w;
