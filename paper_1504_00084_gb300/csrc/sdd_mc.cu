@@ -146,11 +146,26 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
     const int base = j * P.nx + i;  // grids hold at most 2^28 nodes
     const Mon4<T> a = load_mon(P.mon + base), b = load_mon(P.mon + (base + 1));
     const Mon4<T> c = load_mon(P.mon + (base + P.nx)), d = load_mon(P.mon + (base + P.nx + 1));
-    const T gx = 1 - fx, gy = 1 - fy;
-    const T w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
-    w = w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w;
-    wx = w00 * a.wx + w10 * b.wx + w01 * c.wx + w11 * d.wx;
-    we = w00 * a.we + w10 * b.we + w01 * c.we + w11 * d.we;
+    if constexpr (sizeof(T) == 4) {
+        // paired FP32 arithmetic (one instruction for two lanes of work), operation for
+        // operation the contraction of the plain expressions below: bit-identical results
+        const float2 g = __fadd2_rn(make_float2(1.0f, 1.0f), make_float2(-fx, -fy));
+        const float2 wa = __fmul2_rn(make_float2(g.x, fx), make_float2(g.y, g.y));  // w00, w10
+        const float2 wb = __fmul2_rn(make_float2(g.x, fx), make_float2(fy, fy));    // w01, w11
+        float2 t = __fmul2_rn(make_float2(wa.y, wa.y), make_float2(b.w, b.wx));
+        t = __ffma2_rn(make_float2(wa.x, wa.x), make_float2(a.w, a.wx), t);
+        t = __ffma2_rn(make_float2(wb.x, wb.x), make_float2(c.w, c.wx), t);
+        t = __ffma2_rn(make_float2(wb.y, wb.y), make_float2(d.w, d.wx), t);
+        w = t.x;
+        wx = t.y;
+        we = fmaf(wb.y, d.we, fmaf(wb.x, c.we, fmaf(wa.x, a.we, wa.y * b.we)));
+    } else {
+        const T gx = 1 - fx, gy = 1 - fy;
+        const T w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
+        w = w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w;
+        wx = w00 * a.wx + w10 * b.wx + w01 * c.wx + w11 * d.wx;
+        we = w00 * a.we + w10 * b.we + w01 * c.we + w11 * d.we;
+    }
 }
 
 // Keys (1981) cubic-convolution kernel, a = -1/2.
