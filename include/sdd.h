@@ -218,7 +218,7 @@ sdd_status sdd_interface_sampling(const sdd_params* params, int32_t* sampled, in
 
 /* Host-only: adaptive path total of a node after n_done paths with standard error se
  * (max of both components): n_done when se <= target or n_done >= max_paths, else
- * min(max_paths, max(n_done + 1024, 1024 ceil(1.1 n_done (se/target)^2 / 1024))). */
+ * min(max_paths, max(n_done + 1024, 1024 ceil(1.03 n_done (se/target)^2 / 1024))). */
 int64_t sdd_adaptive_next_total(int64_t n_done, double se, double target, int64_t max_paths);
 
 /* Geometric mesh quality of the current mesh (Eq. 8): per cell Q = tr(J^T J) / (2 |det J|),

@@ -17,7 +17,7 @@ from . import _clib
 from .monitor import fd_gradient
 
 ADAPTIVE_GRANULE = 1024   # adaptive chunk totals are multiples of this many paths
-ADAPTIVE_SAFETY = 1.1     # over-provisioning factor of the next chunk
+ADAPTIVE_SAFETY = 1.03    # over-provisioning factor of the next chunk
 
 
 @dataclass
@@ -114,7 +114,7 @@ def next_total(n_done: int, se: float, target: float, max_paths: int) -> int:
     """Adaptive path count of a node after n_done paths with standard error se.
 
     Returns n_done when the node is finished (se <= target, or the cap is reached);
-    otherwise the new cumulative total: n_done (se/target)^2 times a 1.1 safety factor,
+    otherwise the new cumulative total: n_done (se/target)^2 times a 1.03 safety factor,
     rounded up to a multiple of 1024 paths, at least 1024 more than n_done, at most max_paths.
     """
     if se <= target or n_done >= max_paths:

@@ -278,7 +278,7 @@ __host__ __device__ inline int64_t adaptive_next_total(int64_t n_done, double se
 {
     if (se <= target || n_done >= max_paths) return n_done;
     const double r = se / target;
-    const double want = ((double)n_done * (r * r)) * 1.1;
+    const double want = ((double)n_done * (r * r)) * 1.03;
     double total = ceil(want / (double)kAdaptiveGranule) * (double)kAdaptiveGranule;
     const double floor_total = (double)(n_done + kAdaptiveGranule);
     if (total < floor_total) total = floor_total;

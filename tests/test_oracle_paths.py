@@ -228,7 +228,7 @@ def test_estimate_matches_numpy_moments():
 
 def test_next_total_schedule():
     assert mc.next_total(4096, 1e-4, 1e-4, 10 ** 7) == 4096
-    assert mc.next_total(4096, 2e-4, 1e-4, 10 ** 7) == int(math.ceil(4096 * 4 * 1.1 / 1024) * 1024)
+    assert mc.next_total(4096, 2e-4, 1e-4, 10 ** 7) == int(math.ceil(4096 * 4 * 1.03 / 1024) * 1024)
     assert mc.next_total(4096, 1.01e-4, 1e-4, 10 ** 7) == 4096 + 1024
     assert mc.next_total(4096, 1.0, 1e-4, 50000) == 50000
     assert mc.next_total(50000, 1.0, 1e-4, 50000) == 50000
