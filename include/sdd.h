@@ -49,7 +49,8 @@ typedef enum {
     SDD_ERR_CUDA = 3,            /* a CUDA runtime call failed (message in sdd_last_error)     */
     SDD_ERR_NOT_CONVERGED = 4,   /* a subdomain solve hit solve_max_iter; the best iterate is kept */
     SDD_ERR_SE_NOT_REACHED = 5,  /* adaptive MC hit max_paths_per_node before se_target at some node */
-    SDD_ERR_NO_DEVICE = 6        /* no CUDA device is visible                                  */
+    SDD_ERR_NO_DEVICE = 6,       /* no CUDA device is visible                                  */
+    SDD_ERR_CANCELLED = 7        /* a served request was cancelled before it was finished       */
 } sdd_status;
 
 enum { SDD_FORM_DIV = 0, SDD_FORM_WINSLOW = 1 };
@@ -372,6 +373,14 @@ sdd_status sdd_server_poll(sdd_server* s, int64_t* ids, int32_t cap, int32_t* n)
  * finite (found after its first round; no subdomain solve is run), and SDD_ERR_OOM. */
 sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, double* est_xy, double* se_xy,
                              sdd_stats* st);
+
+/* Cancel a request.  A queued request completes at once; a running one leaves the round plan
+ * at the next sdd_server_progress (a round already launched may still sample its nodes) and
+ * completes without a subdomain solve; either way sdd_server_result then returns
+ * SDD_ERR_CANCELLED without outputs.  A request whose finishing work has started completes
+ * normally (the call returns SDD_OK and does nothing).  Unknown or collected ids:
+ * SDD_ERR_INVALID_ARG. */
+sdd_status sdd_server_cancel(sdd_server* s, int64_t id);
 
 /* Counters of the server (waits for nothing). */
 sdd_status sdd_server_get_stats(sdd_server* s, sdd_server_stats* out);

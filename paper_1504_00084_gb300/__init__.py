@@ -24,6 +24,7 @@ SDD_ERR_CUDA = 3
 SDD_ERR_NOT_CONVERGED = 4
 SDD_ERR_SE_NOT_REACHED = 5
 SDD_ERR_NO_DEVICE = 6
+SDD_ERR_CANCELLED = 7
 
 SDD_FORM_DIV, SDD_FORM_WINSLOW = 0, 1
 SDD_FP64, SDD_FP32_ACC64, SDD_FP32_KAHAN = 0, 1, 2
@@ -86,7 +87,7 @@ EXPORTS = [
     "sdd_mesh_quality",
     "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
     "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
-    "sdd_save", "sdd_load", "sdd_interface_sampling", "sdd_step_mkp",
+    "sdd_save", "sdd_load", "sdd_interface_sampling", "sdd_step_mkp", "sdd_server_cancel",
 ]
 
 
@@ -128,6 +129,7 @@ def _load():
         "sdd_server_result": ([P, I64, P, P, P, P, ctypes.POINTER(SddStats)], I32),
         "sdd_server_get_stats": ([P, ctypes.POINTER(SddServerStats)], I32),
         "sdd_server_destroy": ([P], None),
+        "sdd_server_cancel": ([P, I64], I32),
         "sdd_save": ([P, ctypes.c_char_p], I32),
         "sdd_step_mkp": ([P, I32, P, P], I32),
         "sdd_interface_sampling": ([ctypes.POINTER(SddParams), P, ctypes.POINTER(I32)], I32),
@@ -517,6 +519,10 @@ def sdd_server_result(s: int, rid: int, x=None, y=None, est_xy=None, se_xy=None,
     return status, st.as_dict()
 
 
+def sdd_server_cancel(s: int, rid: int) -> None:
+    _check(lib.sdd_server_cancel(s, rid), "sdd_server_cancel")
+
+
 def sdd_server_get_stats(s: int) -> dict:
     o = SddServerStats()
     _check(lib.sdd_server_get_stats(s, ctypes.byref(o)), "sdd_server_get_stats")
@@ -555,6 +561,9 @@ class SddServer:
         se = np.empty((max(M, 1), 2))
         status, st = sdd_server_result(self.h, rid, x, y, est, se, ok=ok)
         return {"x": x, "y": y, "est": est[:M], "se": se[:M], "stats": st, "status": status}
+
+    def cancel(self, rid):
+        sdd_server_cancel(self.h, rid)
 
     def stats(self):
         return sdd_server_get_stats(self.h)

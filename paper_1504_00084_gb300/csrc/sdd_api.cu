@@ -582,6 +582,7 @@ const char* sdd_status_string(sdd_status s)
     case SDD_ERR_NOT_CONVERGED: return "subdomain solve not converged";
     case SDD_ERR_SE_NOT_REACHED: return "standard-error target not reached";
     case SDD_ERR_NO_DEVICE: return "no CUDA device";
+    case SDD_ERR_CANCELLED: return "request cancelled";
     }
     return "unknown status";
 }

@@ -81,6 +81,7 @@ struct Request {
     int slot = -1;
     int64_t off = 0;
     int32_t rounds = 0;
+    bool cancel = false;            // cancellation asked while running
     cudaEvent_t up_ev = nullptr;    // inputs uploaded (upload stream)
     cudaEvent_t done_ev = nullptr;  // finish work complete (finish stream)
 };
@@ -655,8 +656,8 @@ sdd_status sdd_server_progress(sdd_server* s, int32_t* n_running, int32_t* n_que
         //    nodes leave the plan; a round already launched may still sample them)
         for (auto it = s->running.begin(); it != s->running.end();) {
             Request* r = *it;
-            if (s->h_bad[r->slot]) {
-                r->status = SDD_ERR_INVALID_ARG;
+            if (s->h_bad[r->slot] || r->cancel) {
+                r->status = r->cancel ? SDD_ERR_CANCELLED : SDD_ERR_INVALID_ARG;
                 complete(s, r);
                 it = s->running.erase(it);
                 continue;
@@ -702,7 +703,7 @@ sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, do
     Request* r = it->second;
     if (r->state != kDone) return sdd_fail(SDD_ERR_INVALID_ARG, "request not completed");
     sdd_status status = r->status;
-    if (r->p && status == SDD_ERR_INVALID_ARG) {
+    if (r->p && (status == SDD_ERR_INVALID_ARG || status == SDD_ERR_CANCELLED)) {
         if (st) *st = sdd_stats{};
     } else if (r->p) {
         sdd_problem* p = r->p;
@@ -772,9 +773,30 @@ sdd_status sdd_server_result(sdd_server* s, int64_t id, double* x, double* y, do
     s->st.collected += 1;
     if (status == SDD_ERR_OOM) return sdd_fail(SDD_ERR_OOM, "request state does not fit the memory budget");
     if (status == SDD_ERR_INVALID_ARG) return sdd_fail(status, "monitor must be finite and > 0, mesh finite");
+    if (status == SDD_ERR_CANCELLED) return sdd_fail(status, "request cancelled");
     if (status == SDD_ERR_SE_NOT_REACHED) return sdd_fail(status, "max_paths_per_node reached before se_target");
     if (status == SDD_ERR_NOT_CONVERGED) return sdd_fail(status, "a subdomain solve reached solve_max_iter");
     return status;
+}
+
+sdd_status sdd_server_cancel(sdd_server* s, int64_t id)
+{
+    if (!s) return sdd_fail(SDD_ERR_INVALID_ARG, "server is NULL");
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return sdd_fail(SDD_ERR_INVALID_ARG, "unknown request id");
+    Request* r = it->second;
+    if (r->state == kQueued) {
+        for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+            if (*q == r) {
+                s->queue.erase(q);
+                break;
+            }
+        r->status = SDD_ERR_CANCELLED;
+        complete(s, r);
+    } else if (r->state == kRunning) {
+        r->cancel = true;
+    }
+    return SDD_OK;
 }
 
 sdd_status sdd_server_get_stats(sdd_server* s, sdd_server_stats* out)

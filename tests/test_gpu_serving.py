@@ -205,3 +205,40 @@ def test_server_rejections():
         rx, ry = h.mesh()
         h.close()
         assert np.array_equal(out["x"], rx) and np.array_equal(out["y"], ry)
+
+
+def test_server_cancellation():
+    """A cancelled queued request completes at once, a cancelled running one leaves the plan at
+    the next round; both report SDD_ERR_CANCELLED, and the other requests are unaffected."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    probs = small_mix(W.PREC_FP32_KAHAN, paths=2048, n=5, se_target=6e-3)
+    refs = {k: alone(probs[k]) for k in (0, 2, 4)}
+    stream = torch.cuda.Stream()
+    with S.SddServer(server_params(W.PREC_FP32_KAHAN, 2048, 6e-3, 1 << 16, max_resident=2), stream) as srv:
+        ids = [submit(srv, p) for p in probs]
+        srv.progress()                      # admits the first two and launches a round
+        assert srv.stats()["running"] == 2 and srv.stats()["queued"] == 3
+        srv.cancel(ids[1])                  # running
+        srv.cancel(ids[3])                  # queued
+        with pytest.raises(S.SddError):
+            srv.cancel(987654)
+        got = {}
+        for _ in range(100000):
+            srv.progress()
+            for rid in srv.poll():
+                k = ids.index(rid)
+                if k in (1, 3):
+                    with pytest.raises(S.SddError) as e:
+                        srv.result(rid)
+                    assert e.value.status == S.SDD_ERR_CANCELLED
+                    got[k] = None
+                else:
+                    got[k] = srv.result(rid)
+            if len(got) == 5:
+                break
+        assert len(got) == 5
+        for k, (rx, ry, rest, _) in refs.items():
+            assert np.array_equal(got[k]["x"], rx) and np.array_equal(got[k]["y"], ry)
+            assert np.array_equal(got[k]["est"], rest)
