@@ -326,3 +326,22 @@ def test_moving_boundary_two_steps_fp64(S):
     assert np.abs(gx - r2["x"]).max() <= 1e-9 and np.abs(gy - r2["y"]).max() <= 1e-9
     assert np.abs(gx[0, :] - x[0, :]).max() > 1e-4
     h.close()
+
+
+def test_adaptive_cap_reports_nodes_not_reached(S):
+    """A target the cap cannot reach: the call returns SDD_ERR_SE_NOT_REACHED with its outputs,
+    every node stops at the cap with the oracle's path count, and the estimates match (FP64)."""
+    prob = W.c0_small_fp64().replace(paths_per_node=1024, se_target=1e-5, max_paths_per_node=5000)
+    x, y = W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    est, se, n, status = h.interface_mc()
+    assert status == S.SDD_ERR_SE_NOT_REACHED
+    om = ostep.monitor_on_mesh(prob, x, y, prob.t0)
+    from oracle.layout import interface_nodes
+    nodes = interface_nodes(prob.nx, prob.ny, prob.px, prob.py, prob.periodic)
+    oest, ose, on, _ = mc.interface_mc(prob, x, y, om, nodes, 0)
+    assert np.array_equal(n, on) and np.all(n == 5000)
+    assert np.abs(est - oest).max() <= 1e-10
+    st = h.stats()
+    assert st["nodes_not_reached"] == int((ose.max(axis=1) > prob.se_target).sum()) == len(nodes)
+    h.close()
