@@ -371,6 +371,22 @@ def run_mc_only(args):
     return 0
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of this GPU pool (generated file), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def subdomain_unknowns(p):
+    """Interior nodes of all subdomains of a problem (subdomain I spans floor(I (n-1)/P) ..)."""
+    def widths(n, P):
+        return [((I + 1) * (n - 1)) // P - (I * (n - 1)) // P for I in range(P)]
+    return sum((wx - 1) * (wy - 1) for wx in widths(p.nx, p.px) for wy in widths(p.ny, p.py))
+
+
 def run_mix(args):
     """The batched mix: 64 independent problems (grids 65..513, splits 2x2..8x8, bump monitors,
     1e4 paths per node) stepped as one batch in a CUDA graph, against the same problems stepped
@@ -412,10 +428,24 @@ def run_mix(args):
     stream.synchronize()
     st = b.stats()
     T = e0.elapsed_time(e1) / 1e3
+    # the batched solve's own device time, from one more step outside the graph (events
+    # captured inside a graph carry no timing)
+    b.close()
+    b = S.SddBatch(hs, stream=stream, use_graph=False)
+    b.step()
+    solve_ms = b.stats()["solve_kernel_ms"]
+    U = sum(subdomain_unknowns(p) for p in mix)
+    peak, basis = hbm_peak_gbs()
+    solve_bytes = 40.0 * U  # FP64 x^n, y^n, omega read and x, y written once per unknown
+    solve_gbs = solve_bytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
     batch = {"s_per_step": T / args.steps, "interface_node_estimates_per_s": M * args.steps / T,
              "path_steps_last_step": st["path_steps"], "launches_per_step": (st["kernel_launches"] - l0) / args.steps,
              "solve_iters_max": st["solve_iters_max"], "solve_outer_max": st["solve_outer_max"],
-             "solve_rel_residual": st["solve_rel_residual"]}
+             "solve_rel_residual": st["solve_rel_residual"],
+             "solve_roofline": {"bound": "hbm", "kernel": "solve_batch_kernel", "ms": solve_ms,
+                                "unknowns": U, "algorithmic_bytes": solve_bytes, "achieved": solve_gbs,
+                                "peak": peak, "unit": "GB/s", "peak_basis": basis,
+                                "frac": solve_gbs / peak if solve_gbs else None}}
     b.close()
     if args.mix_batched_only:
         for h in hs:

@@ -133,6 +133,8 @@ typedef struct {
     int32_t mc_kernel_launches; /* path-kernel launches of the last MC call                     */
     int32_t reserved1;
     int64_t kernel_launches;    /* kernels launched by this problem since creation              */
+    double solve_kernel_ms;     /* device time of the last subdomain-solve launch(es) (face
+                                   coefficients and solves; CUDA events on the stream)          */
 } sdd_stats;
 
 /* Create a problem: validates params, copies the initial mesh x0, y0 (nx*ny each, host or
@@ -279,7 +281,8 @@ sdd_status sdd_batch_step(sdd_batch* b);
 
 /* Counters of the last batch step over all problems: M, path_steps, paths, mc_rounds,
  * nodes_not_reached, max_se, solve maxima, kernel_launches (since creation), and in
- * mc_kernel_ms the device time of the whole last step (CUDA events on the batch's stream).
+ * mc_kernel_ms the device time of the whole last step and in solve_kernel_ms that of its
+ * batched solve launch (CUDA events on the batch's stream).
  * Waits for the batch's stream.  Returns SDD_ERR_INVALID_ARG (counters still written) when a
  * problem's monitor was not finite and > 0 at every node or its mesh not finite in that step. */
 sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out);

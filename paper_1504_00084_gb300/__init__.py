@@ -51,7 +51,7 @@ class SddStats(ctypes.Structure):
                 ("solve_iters_max", ctypes.c_int32), ("solve_outer_max", ctypes.c_int32),
                 ("solve_rel_residual", ctypes.c_double), ("mc_kernel_ms", ctypes.c_double),
                 ("mc_kernel_launches", ctypes.c_int32), ("reserved1", ctypes.c_int32),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("solve_kernel_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -388,7 +388,12 @@ sdd_status run_solve(sdd_problem* p)
     S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
     S.mg = p->mg; S.mg_stride = p->mg_stride;
     S.stat_iters = p->st_iters; S.stat_outer = p->st_outer; S.stat_ok = p->st_ok; S.stat_res = p->st_res;
+    // device time of the solve launches
+    if (!p->solve_ev[0]) SDD_CK(cudaEventCreate(&p->solve_ev[0]));
+    if (!p->solve_ev[1]) SDD_CK(cudaEventCreate(&p->solve_ev[1]));
+    SDD_CK(cudaEventRecord(p->solve_ev[0], p->stream));
     SDD_CK(launch_solve(S, p->fp64, p->stream));
+    SDD_CK(cudaEventRecord(p->solve_ev[1], p->stream));
     p->launches += 2;
     const int ns = p->prm.px * p->prm.py;
     std::vector<int32_t> it(ns), ou(ns), ok(ns);
@@ -401,6 +406,11 @@ sdd_status run_solve(sdd_problem* p)
     p->stats.solve_iters_max = 0;
     p->stats.solve_outer_max = 0;
     p->stats.solve_rel_residual = 0.0;
+    {
+        float ms = 0.f;
+        SDD_CK(cudaEventElapsedTime(&ms, p->solve_ev[0], p->solve_ev[1]));
+        p->stats.solve_kernel_ms = ms;
+    }
     int bad = 0;
     for (int s = 0; s < ns; ++s) {
         if (it[s] > p->stats.solve_iters_max) p->stats.solve_iters_max = it[s];

@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -62,11 +63,13 @@ struct sdd_batch {
     double* t_dev = nullptr;
     double* t_host = nullptr;
     int32_t* sub_off_dev = nullptr;
+    int2* order_dev = nullptr;       // solve CTAs: (problem, subdomain), largest subdomains first
     int32_t* h_n_active = nullptr;
     // graph
     cudaGraphExec_t graph = nullptr;
     std::vector<const double*> graph_x;  // mesh pointers the graph was recorded with
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t sev0 = nullptr, sev1 = nullptr;  // around the batched face + solve launches
     int64_t launches = 0;
     int64_t launches_per_step = 0;
     int32_t rounds_last = 0;
@@ -101,6 +104,8 @@ struct sdd_batch {
         if (graph) cudaGraphExecDestroy(graph);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        if (sev0) cudaEventDestroy(sev0);
+        if (sev1) cudaEventDestroy(sev1);
         for (void* v : allocs) cudaFree(v);
         for (void* v : host_allocs) cudaFreeHost(v);
     }
@@ -262,8 +267,10 @@ sdd_status record_step(sdd_batch* b)
         any_be = any_be || p->prm.subdomain_scheme == 0;
         any_fe = any_fe || p->prm.subdomain_scheme == 1;
     }
+    B_CK(cudaEventRecord(b->sev0, b->stream));
     B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream, any_be,
-                            any_fe));
+                            any_fe, b->order_dev));
+    B_CK(cudaEventRecord(b->sev1, b->stream));
     launches += (any_be ? 1 : 0) + (any_fe ? 1 : 0);
     for (int i = 0; i < b->n; ++i) {
         sdd_problem* p = b->probs[i];
@@ -331,6 +338,7 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     ALLOC(b->task_counter, 16); ALLOC(b->slots, M * kSlotsPerNode * sizeof(TaskSlot));
     ALLOC(b->mcprob_dev, rec * n); ALLOC(b->solve_dev, sizeof(SolveParams) * n); ALLOC(b->t_dev, 8 * n);
     ALLOC(b->sub_off_dev, 4 * (n + 1));
+    ALLOC(b->order_dev, sizeof(int2) * (size_t)(b->total_subs > 0 ? b->total_subs : 1));
     if (sampled_any) ALLOC(b->node_role, M * 4);
     HALLOC(b->mcprob_host, rec * n); HALLOC(b->solve_host, sizeof(SolveParams) * n); HALLOC(b->t_host, 8 * n);
     HALLOC(b->h_n_active, 16);
@@ -338,10 +346,30 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
 #undef HALLOC
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->sev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->sev1);
     if (e == cudaSuccess && b->M > 0)
         e = cudaMemcpy(b->node_prob, node_prob.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->sub_off_dev, b->sub_off.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && b->total_subs > 0) {
+        // longest-first: subdomains by interior size, descending (ties in problem, subdomain order)
+        std::vector<std::pair<int64_t, int2>> subs;
+        for (int i = 0; i < n; ++i) {
+            const sdd_params& q = problems[i]->prm;
+            for (int k = 0; k < q.px * q.py; ++k) {
+                const int I = k % q.px, J = k / q.px;
+                const int64_t wi = split_line(I + 1, q.nx, q.px) - split_line(I, q.nx, q.px) - 1;
+                const int64_t wj = split_line(J + 1, q.ny, q.py) - split_line(J, q.ny, q.py) - 1;
+                subs.push_back({wi * wj, make_int2(i, k)});
+            }
+        }
+        std::stable_sort(subs.begin(), subs.end(), [](const std::pair<int64_t, int2>& a,
+                                                      const std::pair<int64_t, int2>& c) { return a.first > c.first; });
+        std::vector<int2> order;
+        for (const auto& v : subs) order.push_back(v.second);
+        e = cudaMemcpy(b->order_dev, order.data(), sizeof(int2) * order.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && sampled_any && b->M > 0)
         e = cudaMemcpy(b->node_role, node_role.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -424,6 +452,7 @@ sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out)
     s.kernel_launches = b->launches;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, b->ev0, b->ev1) == cudaSuccess) s.mc_kernel_ms = ms;  // whole last step
+    if (cudaEventElapsedTime(&ms, b->sev0, b->sev1) == cudaSuccess) s.solve_kernel_ms = ms;  // batched solve
     cudaGetLastError();
     if (b->M > 0) {
         std::vector<int64_t> st(b->M), np(b->M);

@@ -267,8 +267,10 @@ cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const
                           double* est, double* se, cudaStream_t s);
 cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s);
 cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s);
+// order (nullable): (problem, subdomain) of each CTA
 cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
-                               bool fp64_inner, cudaStream_t s, bool any_be = true, bool any_fe = false);
+                               bool fp64_inner, cudaStream_t s, bool any_be = true, bool any_fe = false,
+                               const int2* order = nullptr);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                           cudaStream_t s);
 

@@ -64,6 +64,7 @@ struct sdd_problem {
     std::vector<void*> allocs;
     size_t dev_bytes = 0;          // device bytes held (allocation granularity included)
     std::vector<cudaEvent_t> ev;  // start/stop pairs around path-kernel launches
+    cudaEvent_t solve_ev[2] = {nullptr, nullptr};  // around the subdomain-solve launches
     int64_t launches = 0;         // kernels launched since creation
 
     template <typename P>
@@ -80,6 +81,8 @@ struct sdd_problem {
     ~sdd_problem()
     {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : solve_ev)
+            if (e) cudaEventDestroy(e);
         for (void* v : allocs) cudaFree(v);
         if (h_n_active) cudaFreeHost(h_n_active);
     }

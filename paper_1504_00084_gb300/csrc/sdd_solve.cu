@@ -595,10 +595,18 @@ __global__ void __launch_bounds__(kSolveThreads) fe_kernel(const __grid_constant
     fe_body(P, blockIdx.x, sh);
 }
 
-// Batched problem record of CTA b: problem p with sub_off[p] <= b < sub_off[p + 1].
-__device__ __forceinline__ void batch_lookup(const SolveParams* probs, const int32_t* sub_off, int n,
-                                             SolveParams& sp, int& sub)
+// Batched problem record of CTA b: order[b] = (problem, subdomain) when given (largest
+// subdomains first, so the longest CTAs start in the first wave), else problem p with
+// sub_off[p] <= b < sub_off[p + 1].
+__device__ __forceinline__ void batch_lookup(const SolveParams* probs, const int32_t* sub_off, const int2* order,
+                                             int n, SolveParams& sp, int& sub)
 {
+    if (order) {
+        const int2 o = order[blockIdx.x];
+        sp = probs[o.x];
+        sub = o.y;
+        return;
+    }
     int lo = 0, hi = n - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -610,25 +618,27 @@ __device__ __forceinline__ void batch_lookup(const SolveParams* probs, const int
 
 // Batched forward-Euler subdomains (CTAs of backward-Euler problems return at once).
 __global__ void __launch_bounds__(kSolveThreads) fe_batch_kernel(const SolveParams* probs, const int32_t* sub_off,
-                                                                 int n)
+                                                                 const int2* order, int n)
 {
     __shared__ double sh[40];
     __shared__ SolveParams sp;
     __shared__ int sub;
-    if (threadIdx.x == 0) batch_lookup(probs, sub_off, n, sp, sub);
+    if (threadIdx.x == 0) batch_lookup(probs, sub_off, order, n, sp, sub);
     __syncthreads();
     if (sp.scheme == 1) fe_body(sp, sub, sh);
 }
 
-// Batched: CTA b solves subdomain b - sub_off[p] of problem p, sub_off[p] <= b < sub_off[p + 1].
+// Batched: CTA b solves the subdomain batch_lookup assigns it.  Two CTAs per SM (64 registers):
+// the solves are latency-bound, so a second resident CTA hides synchronisation stalls.
 template <typename TI>
-__global__ void __launch_bounds__(kSolveThreads) solve_batch_kernel(const SolveParams* probs,
-                                                                    const int32_t* sub_off, int n)
+__global__ void __launch_bounds__(kSolveThreads, 2) solve_batch_kernel(const SolveParams* probs,
+                                                                       const int32_t* sub_off, const int2* order,
+                                                                       int n)
 {
     __shared__ double sh[32 * 8 + 8];
     __shared__ SolveParams sp;
     __shared__ int sub;
-    if (threadIdx.x == 0) batch_lookup(probs, sub_off, n, sp, sub);
+    if (threadIdx.x == 0) batch_lookup(probs, sub_off, order, n, sp, sub);
     __syncthreads();
     if (sp.scheme == 0) solve_body<TI>(sp, sub, sh);  // forward-Euler problems: fe_batch_kernel
 }
@@ -643,16 +653,16 @@ cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s)
 }
 
 cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
-                               bool fp64_inner, cudaStream_t s, bool any_be, bool any_fe)
+                               bool fp64_inner, cudaStream_t s, bool any_be, bool any_fe, const int2* order)
 {
     if (total_subs <= 0) return cudaSuccess;
     if (any_be) {
         if (fp64_inner)
-            solve_batch_kernel<double><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+            solve_batch_kernel<double><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, order, n);
         else
-            solve_batch_kernel<float><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+            solve_batch_kernel<float><<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, order, n);
     }
-    if (any_fe) fe_batch_kernel<<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, n);
+    if (any_fe) fe_batch_kernel<<<total_subs, kSolveThreads, 0, s>>>(probs, sub_off, order, n);
     return cudaGetLastError();
 }
 
