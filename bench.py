@@ -60,11 +60,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="front", choices=["front", "mix", "serve"],
+    ap.add_argument("--workload", default="front", choices=["front", "mix", "serve", "sweep"],
                     help="front: the 257x257 / 4x4 moving-front problem (the benchmark line); "
                          "mix: the batch of 64 uneven problems, batched vs one at a time; "
                          "serve: one-step requests of the mix's shapes with Poisson arrivals through "
-                         "the continuous-batching server")
+                         "the continuous-batching server; sweep: precision sweep on the 257x257 sine "
+                         "mode against its closed form")
     ap.add_argument("--serve-n", type=int, default=64, help="serve: requests")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-first-chunk", type=int, default=10000, help="serve: first paths per node")
@@ -570,6 +571,74 @@ def run_serve(args):
     return 0
 
 
+def run_sweep(args):
+    """Precision sweep on the 257x257 / 4x4 sine mode (omega = 1, mesh xi + 0.05 sin(pi xi)
+    sin(pi eta), closed form xi + 0.05 e^{-2 pi^2 t / tau} sin sin at t = dt): for N = 1e3..1e6
+    paths per node, FP32 paths with FP64 or Kahan-FP32 sums (and FP64 paths up to 1e5), the
+    interface estimates' error against the closed form (absolute and in standard errors), the
+    FP32-vs-FP64 difference on the same paths, and the path-kernel time; then the subdomain
+    solves in FP32 with FP64 refinement against all-FP64 on the same interface data."""
+    import math
+
+    import numpy as np
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    import workloads as W
+
+    torch.cuda.set_device(0)
+    base = W.c2_sine()
+    x0, y0 = W.sine_mode_mesh(base, amp=0.05)
+    decay = math.exp(-2 * math.pi ** 2 * base.dt / base.tau)
+    rows = []
+    est64 = {}
+    for prec, name, Ns in ((W.PREC_FP64, "fp64", (1000, 10000, 100000)),
+                           (W.PREC_FP32_ACC64, "fp32_acc64", (1000, 10000, 100000, 1000000)),
+                           (W.PREC_FP32_KAHAN, "fp32_kahan", (1000, 10000, 100000, 1000000))):
+        for N in Ns:
+            p = base.replace(precision=prec, paths_per_node=N)
+            with S.SddProblem(S.params_from(p), x0, y0) as h:
+                h.set_monitor_analytic(p.monitor_kind, p.monitor_params)
+                est, se, _, _ = h.interface_mc()
+                st = h.stats()
+                nodes = h.nodes()
+            xi = nodes[:, 0] / (p.nx - 1)
+            eta = nodes[:, 1] / (p.ny - 1)
+            mode = 0.05 * decay * np.sin(np.pi * xi) * np.sin(np.pi * eta)
+            exact = np.stack([p.Lx * xi + mode, p.Ly * eta + mode], 1)
+            err = np.abs(est - exact)
+            row = {"precision": name, "paths_per_node": N, "max_abs_error": float(err.max()),
+                   "max_error_in_se": float((err / np.maximum(se, 1e-300)).max()),
+                   "mean_se": float(se.mean()), "path_kernel_ms": st["mc_kernel_ms"],
+                   "path_steps_per_s": st["path_steps"] / (st["mc_kernel_ms"] / 1e3)}
+            if name == "fp64":
+                est64[N] = est
+            elif N in est64:
+                row["max_diff_vs_fp64_same_paths"] = float(np.abs(est - est64[N]).max())
+            rows.append(row)
+    # solves: FP32 CG + FP64 refinement vs FP64, same interface data
+    iface = est64[max(est64)]
+    meshes = {}
+    for prec, name in ((W.PREC_FP64, "fp64"), (W.PREC_FP32_KAHAN, "fp32_refined")):
+        p = base.replace(precision=prec)
+        with S.SddProblem(S.params_from(p), x0, y0) as h:
+            h.set_monitor_analytic(p.monitor_kind, p.monitor_params)
+            gx, gy, _ = h.subdomain_solve(iface)
+            meshes[name] = (gx, gy, h.stats())
+    dx = max(float(np.abs(meshes["fp64"][0] - meshes["fp32_refined"][0]).max()),
+             float(np.abs(meshes["fp64"][1] - meshes["fp32_refined"][1]).max()))
+    out = {"metric": "precision sweep: interface error vs closed form, FP32 vs FP64",
+           "workload": "sine257_4x4: 257x257 grid, 4x4 subdomains, omega = 1, sine-mode mesh, one step",
+           "closed_form_decay": decay, "interface": rows,
+           "solve": {"max_mesh_diff_fp32_refined_vs_fp64": dx,
+                     "fp32_refined_rel_residual": meshes["fp32_refined"][2]["solve_rel_residual"],
+                     "fp64_rel_residual": meshes["fp64"][2]["solve_rel_residual"],
+                     "fp32_refined_solve_ms": meshes["fp32_refined"][2]["solve_kernel_ms"],
+                     "fp64_solve_ms": meshes["fp64"][2]["solve_kernel_ms"]}}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     args = parse()
     if args.mc_only > 0:
@@ -578,6 +647,8 @@ def main():
         return run_mix(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
