@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--paths", type=int, default=100000)
     ap.add_argument("--max-paths", type=int, default=1 << 25)
     ap.add_argument("--periodic", type=int, default=0)
+    ap.add_argument("--form", type=int, default=0, choices=[0, 1],
+                    help="0: tau x_t = div(omega grad x) (the benchmark plan's generator); 1: the paper's")
+    ap.add_argument("--tau", type=float, default=1e-2)
     ap.add_argument("--iface-stride", type=int, default=0,
                     help="Monte Carlo at every k-th interface node, the rest interpolated (0: all)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -87,7 +90,7 @@ def workload(args, rank=0):
     p = W.c1_front(prec, periodic=args.periodic)
     return p.replace(se_target=args.se_target, paths_per_node=args.paths,
                      max_paths_per_node=max(args.max_paths, args.paths), seed=p.seed + rank,
-                     iface_stride=args.iface_stride)
+                     iface_stride=args.iface_stride, form=args.form, tau=args.tau)
 
 
 def config_of(p, M):
@@ -98,7 +101,8 @@ def config_of(p, M):
             "max_paths_per_node": p.max_paths_per_node, "substeps": p.substeps, "tau": p.tau, "dt": p.dt,
             "path_precision": {0: "fp64", 1: "fp32 (fp64 sums)", 2: "fp32 (kahan fp32 sums)"}[p.precision],
             "l2": "256 MiB buffer written between timed steps (inputs are ~1 MB)",
-            **({"iface_stride": p.iface_stride} if p.iface_stride > 1 else {})}
+            **({"iface_stride": p.iface_stride} if p.iface_stride > 1 else {}),
+            **({"generator_form": "paper (x_t = grad w / w . grad x + lap x, scaled by tau)"} if p.form == 1 else {})}
 
 
 def reduce_over_ranks(dist, T, path_steps, estimates, device):

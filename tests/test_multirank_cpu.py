@@ -24,7 +24,7 @@ def _rank_main(rank, world, port, out):
 
     class A:
         precision, periodic, se_target, paths, max_paths = "kahan", 0, 1e-4, 100000, 1 << 25
-        iface_stride = 0
+        iface_stride, form, tau = 0, 0, 1e-2
 
     prob = bench.workload(A, rank)
     T, ps, est = bench.reduce_over_ranks(dist, 1.0 + rank, 1000 * (rank + 1), 1521, "cpu")
