@@ -11,7 +11,7 @@ import pytest
 import workloads as W
 from gpu_helpers import compare_paths, gpu_problem, oracle_inputs, real_of
 from oracle import mc, step as ostep
-from oracle.solve import box_system
+from oracle.solve import box_system, solve_box
 from oracle.layout import subdomains
 
 pytestmark = pytest.mark.gpu
@@ -293,6 +293,48 @@ def test_front257_full_size_sampled_nodes(S, precision):
         close = np.abs(gv - ov).max(axis=1) <= (FP64_VAL if fp64 else FP32_VAL)
         assert same.mean() >= (0.999 if fp64 else 0.99)
         assert close.mean() >= (0.9 if fp64 else 0.9)
+    h.close()
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_KAHAN])
+def test_large_grid_sampled_nodes(S, precision):
+    """A grid near the size limit: 4097 x 4097 nodes (16.8 M), 16 x 16 subdomains, 122 625
+    interface nodes, the paper's generator form at tau = 1.  All nodes run 256 paths in one
+    launch.  On seven nodes spread over the list (the first and the last node id included), every
+    path's exit step, side and value match the oracle, and the node estimates match the oracle's
+    estimates of the same paths (FP64: 1e-10; FP32: within the per-path tolerance).  A full
+    step repeats those estimates, and one inner subdomain's solve matches the oracle's."""
+    prob = W.c1_front(precision).replace(nx=4097, ny=4097, px=16, py=16, form=W.FORM_WINSLOW, tau=1.0,
+                                         paths_per_node=256, max_paths_per_node=256, se_target=0.0)
+    x, y = W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    est, se, n, _ = h.interface_mc()
+    om, inp, nodes = oracle_inputs(prob, x, y, prob.t0, 0)
+    assert len(nodes) == 122625 and np.all(n == 256)
+    pick = np.linspace(0, len(nodes) - 1, 7).astype(int)
+    fp64 = precision == W.PREC_FP64
+    for m in pick:
+        gv, gs, gd = h.debug_paths(int(m), 0, 256)
+        ov, os_, od, mg = mc.paths(inp, int(m), int(nodes[m, 0]), int(nodes[m, 1]), 0, 256)
+        robust, _ = compare_paths(gv, gs, gd, ov, os_, od, mg, FP64_MARGIN if fp64 else FP32_MARGIN,
+                                  FP64_VAL if fp64 else FP32_VAL)
+        assert robust > (0.999 if fp64 else 0.95)
+    shift = np.stack([x[nodes[pick, 1], nodes[pick, 0]], y[nodes[pick, 1], nodes[pick, 0]]], 1)
+    sums, _ = mc.interface_sums(inp, pick, nodes[pick], np.zeros(len(pick), np.int64),
+                                np.full(len(pick), 256, np.int64), shift)
+    oest, _, _ = mc.estimate(sums, np.full(len(pick), 256), shift)
+    assert np.abs(est[pick] - oest).max() <= (1e-10 if fp64 else FP32_VAL)
+    # the step repeats the same interface estimates; one inner subdomain (255 x 255 unknowns) is
+    # checked against the oracle's direct solve with those estimates as its rim values
+    gx, gy, status = h.step()
+    assert status == 0
+    rx, ry = ostep.scatter(prob, nodes, est)
+    i0, i1, j0, j1 = subdomains(prob.nx, prob.ny, prob.px, prob.py)[5 * 16 + 7]
+    ox, oy, order = solve_box(om, rx, ry, x, y, i0, i1, j0, j1, prob.dt, prob.tau, prob.form)
+    ii, jj = np.array(order).T
+    _, rhs, _ = box_system(om, None, i0, i1, j0, j1, prob.dt, prob.tau, prob.form)
+    tol = prob.solve_rtol * max(np.linalg.norm(rhs(rx, x)), np.linalg.norm(rhs(ry, y))) / float(om.min()) + 1e-12
+    assert np.abs(gx[jj, ii] - ox).max() <= tol and np.abs(gy[jj, ii] - oy).max() <= tol
     h.close()
 
 
