@@ -71,10 +71,11 @@ enum {
 };
 
 typedef struct {
-    int32_t nx, ny;          /* grid nodes per direction, >= 3                                      */
+    int32_t nx, ny;          /* grid nodes per direction, >= 3, nx * ny <= 2^28                      */
     int32_t px, py;          /* subdomains per direction, 1 <= px <= nx - 1, 1 <= py <= ny - 1;
                                 subdomain I spans node columns floor(I (nx-1)/px) ..
-                                floor((I+1)(nx-1)/px) (equal when px divides nx - 1), likewise J */
+                                floor((I+1)(nx-1)/px) (equal when px divides nx - 1), likewise J;
+                                the interface nodes they give must number below 2^23          */
     int32_t periodic;        /* 0: Dirichlet, boundary mesh fixed at (Lx xi, Ly eta) (Sec. 2);
                                 1: doubly periodic, x(xi+1) = x(xi) + Lx, y(eta+1) = y(eta) + Ly    */
     int32_t form;            /* SDD_FORM_DIV or SDD_FORM_WINSLOW                                   */
@@ -266,7 +267,8 @@ sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n,
  * ONE launch for all subdomain solves (one CTA per (problem, subdomain)).  Each problem's
  * results are bitwise those of sdd_step on it alone (own seed, local node ids in the Philox
  * counter, per-node path schedule, fixed-order reductions).  All problems must share
- * precision, se_target and paths_per_node (and max_paths_per_node when adaptive); the batch
+ * precision, se_target and paths_per_node (and max_paths_per_node when adaptive), and their
+ * interface nodes must number below 2^23 in total (else SDD_ERR_INVALID_ARG); the batch
  * keeps pointers to them (they must outlive it) and orders its work on `stream`.
  * use_graph = 1 (fixed N only, stream not NULL): the first step records its launches in a CUDA
  * graph that later steps replay (re-recorded if a problem's mesh buffers change). */
@@ -314,7 +316,7 @@ typedef struct {
     int32_t max_resident;        /* requests holding device state at once (running, finishing,
                                     or finished but not collected), in [1, 2^16]                */
     int64_t max_nodes;           /* node-pool capacity (interface nodes of resident requests),
-                                    in [1, 2^24]; each pool node costs about 12.5 KB            */
+                                    in [1, 2^23); each pool node costs about 12.5 KB            */
     int64_t mem_budget_bytes;    /* device bytes for per-request state (pool excluded), 0 = no
                                     limit                                                       */
     double se_target;            /* service level, meaning as in sdd_params (0: fixed N)        */

@@ -50,6 +50,7 @@ namespace {
 
 constexpr int64_t kMaxChunk = int64_t(1) << 19;  // paths per node per launch (see plan kernel)
 constexpr int kSlotsPerNode = (int)(kMaxChunk / kPathsPerTask);
+constexpr int64_t kMaxNodes = int64_t(1) << 23;  // kMaxNodes * kSlotsPerNode tasks fit in an int
 constexpr int kMaxAdaptiveRounds = 4096;
 const char kCkptMagic[8] = {'S', 'D', 'D', 'C', 'K', 'P', 'T', '1'};
 
@@ -157,6 +158,14 @@ sdd_status validate(const sdd_params* P)
     if (P->px < 1 || P->py < 1) return fail(SDD_ERR_INVALID_ARG, "px, py must be >= 1");
     if (P->px > P->nx - 1 || P->py > P->ny - 1)
         return fail(SDD_ERR_INVALID_ARG, "px <= nx - 1 and py <= ny - 1 (every subdomain spans a cell)");
+    {
+        // interface nodes in closed form; a round's tasks (up to kSlotsPerNode per node) are
+        // counted in 32 bits
+        const int64_t nx = P->nx, ny = P->ny, px = P->px, py = P->py;
+        const int64_t M = P->periodic ? px * (ny - 1) + py * (nx - 1) - px * py
+                                      : (px - 1) * (ny - 2) + (py - 1) * (nx - 2) - (px - 1) * (py - 1);
+        if (M >= kMaxNodes) return fail(SDD_ERR_INVALID_ARG, "interface nodes must number below 2^23");
+    }
     if (P->periodic != 0 && P->periodic != 1) return fail(SDD_ERR_INVALID_ARG, "periodic must be 0 or 1");
     if (P->form != SDD_FORM_DIV && P->form != SDD_FORM_WINSLOW) return fail(SDD_ERR_INVALID_ARG, "bad form");
     if (P->precision < SDD_FP64 || P->precision > SDD_FP32_KAHAN)

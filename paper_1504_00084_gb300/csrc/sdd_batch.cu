@@ -307,6 +307,10 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     }
     if (use_graph && (q.se_target > 0 || !stream))
         return sdd_fail(SDD_ERR_INVALID_ARG, "graph mode needs fixed N and a non-NULL stream");
+    int64_t m_total = 0;
+    for (int i = 0; i < n; ++i) m_total += problems[i]->M;
+    if (m_total >= ((int64_t)1 << 23))  // a round's tasks (up to kSlotsPerNode per node) fit in an int
+        return sdd_fail(SDD_ERR_INVALID_ARG, "the batch's interface nodes must number below 2^23");
     sdd_batch* b = new sdd_batch();
     b->probs.assign(problems, problems + n);
     b->n = n;

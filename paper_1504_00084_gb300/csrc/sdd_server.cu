@@ -460,8 +460,8 @@ sdd_status sdd_server_create(const sdd_server_params* params, void* stream, sdd_
     if (q.precision < SDD_FP64 || q.precision > SDD_FP32_KAHAN) return sdd_fail(SDD_ERR_INVALID_ARG, "bad precision");
     if (q.max_resident < 1 || q.max_resident > (1 << 16))
         return sdd_fail(SDD_ERR_INVALID_ARG, "max_resident must be in [1, 2^16]");
-    if (q.max_nodes < 1 || q.max_nodes > ((int64_t)1 << 24))
-        return sdd_fail(SDD_ERR_INVALID_ARG, "max_nodes must be in [1, 2^24]");
+    if (q.max_nodes < 1 || q.max_nodes >= ((int64_t)1 << 23))  // a round's tasks fit in an int
+        return sdd_fail(SDD_ERR_INVALID_ARG, "max_nodes must be in [1, 2^23)");
     if (q.mem_budget_bytes < 0) return sdd_fail(SDD_ERR_INVALID_ARG, "mem_budget_bytes must be >= 0");
     if (q.round_paths < 0) return sdd_fail(SDD_ERR_INVALID_ARG, "round_paths must be >= 0");
     if (!(q.se_target >= 0) || !isfinite(q.se_target)) return sdd_fail(SDD_ERR_INVALID_ARG, "se_target must be >= 0");

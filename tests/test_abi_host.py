@@ -133,3 +133,14 @@ def test_moving_boundary_needs_a_dirichlet_domain(sdd):
     h = ctypes.c_void_p()
     assert sdd.lib.sdd_create_problem(ctypes.byref(p), x.ctypes.data, x.ctypes.data, None,
                                       ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
+
+
+def test_interface_node_limit(sdd):
+    """A round's tasks are counted in 32 bits: problems (and server pools) with 2^23 or more
+    interface nodes are rejected before any device work.  4097^2 split 4096 x 4096 has 4095^2."""
+    p = base_params(sdd, nx=4097, ny=4097, px=4096, py=4096)
+    x = np.zeros((4097, 4097))
+    h = ctypes.c_void_p()
+    assert sdd.lib.sdd_create_problem(ctypes.byref(p), x.ctypes.data, x.ctypes.data, None,
+                                      ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
+    assert b"2^23" in sdd.lib.sdd_last_error()
