@@ -200,13 +200,17 @@ def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
     rate = float(steps.sum() / dt)
     _, _, se = mc.estimate(sums, np.full(len(pick), n), shift)
     need = np.maximum((se.max(axis=1) / prob.se_target) ** 2, 1.0) * n  # paths for SE <= target
+    sigma = se.max(axis=1) * np.sqrt(n)  # per-path standard deviation of the node values
     ps_per_est = float(np.mean(need * steps / n)) if ps_per_estimate_hint is None else ps_per_estimate_hint
     return {"value": rate / ps_per_est, "unit": UNIT, "cores": int(_clib.lib().oracle_max_threads()),
             "kind": "oracle",
             "sample": f"{len(pick)} of {M} interface nodes x {n} paths, first time step, "
                       f"{'fp64' if real is np.float64 else 'fp32'} paths, {dt:.1f} s; path-steps/s "
                       f"{rate:.4g} divided by {ps_per_est:.4g} path-steps per node estimate at SE<=1e-4",
-            "path_steps_per_s": rate}
+            "path_steps_per_s": rate,
+            "sigma_v": {"mean": float(sigma.mean()), "max": float(sigma.max()),
+                        "basis": "per-path standard deviation of a node's value (larger component), "
+                                 "se * sqrt(paths) over the sampled nodes"}}
 
 
 def run_reference(args):
@@ -231,7 +235,7 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
            "config": config_of(prob, M),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                            "sample": vals[0]["sample"]},
+                            "sample": vals[0]["sample"], "sigma_v": vals[0]["sigma_v"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
