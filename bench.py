@@ -193,8 +193,17 @@ def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
                                         np.full(len(pick), n, np.int64), shift)
         return time.perf_counter() - t, sums, steps
 
+    cores = int(_clib.lib().oracle_max_threads())
     dt0, _, st0 = run(512)
     rate0 = st0.sum() / max(dt0, 1e-9)
+    # the same C core on one thread, on a sample an eighth of the time
+    n1 = int(max(64, min(1 << 20, seconds / 8 * rate0 / cores / max(st0.sum() / 512, 1.0))))
+    _clib.lib().oracle_set_threads(1)
+    try:
+        dt1, _, st1 = run(n1)
+    finally:
+        _clib.lib().oracle_set_threads(cores)
+    rate1 = float(st1.sum() / max(dt1, 1e-9))
     n = int(max(512, min(1 << 20, seconds * rate0 / max(st0.sum() / 512, 1.0))))
     dt, sums, steps = run(n)
     rate = float(steps.sum() / dt)
@@ -202,12 +211,14 @@ def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
     need = np.maximum((se.max(axis=1) / prob.se_target) ** 2, 1.0) * n  # paths for SE <= target
     sigma = se.max(axis=1) * np.sqrt(n)  # per-path standard deviation of the node values
     ps_per_est = float(np.mean(need * steps / n)) if ps_per_estimate_hint is None else ps_per_estimate_hint
-    return {"value": rate / ps_per_est, "unit": UNIT, "cores": int(_clib.lib().oracle_max_threads()),
+    return {"value": rate / ps_per_est, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{len(pick)} of {M} interface nodes x {n} paths, first time step, "
                       f"{'fp64' if real is np.float64 else 'fp32'} paths, {dt:.1f} s; path-steps/s "
                       f"{rate:.4g} divided by {ps_per_est:.4g} path-steps per node estimate at SE<=1e-4",
             "path_steps_per_s": rate,
+            "single_core": {"path_steps_per_s": rate1, "value": rate1 / ps_per_est,
+                            "sample": f"{len(pick)} nodes x {n1} paths on one thread, {dt1:.1f} s"},
             "sigma_v": {"mean": float(sigma.mean()), "max": float(sigma.max()),
                         "basis": "per-path standard deviation of a node's value (larger component), "
                                  "se * sqrt(paths) over the sampled nodes"}}
@@ -235,7 +246,8 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f32" if args.precision != "fp64" else "f64", "data": "synthetic",
            "config": config_of(prob, M),
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
-                            "sample": vals[0]["sample"], "sigma_v": vals[0]["sigma_v"]},
+                            "sample": vals[0]["sample"], "sigma_v": vals[0]["sigma_v"],
+                            "single_core": vals[0]["single_core"]},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0

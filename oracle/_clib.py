@@ -65,6 +65,7 @@ def lib():
             L.oracle_philox4x32_10.argtypes = [P, P, P]
             L.oracle_philox_batch.argtypes = [I64, P, P, P]
             L.oracle_max_threads.restype = ctypes.c_int
+            L.oracle_set_threads.argtypes = [ctypes.c_int]
             for sfx, st in (("f64", ProblemF64), ("f32", ProblemF32)):
                 getattr(L, f"oracle_path_{sfx}").argtypes = [ctypes.POINTER(st), U32, ctypes.c_int,
                                                              ctypes.c_int, U32, P, P, P, P, P]

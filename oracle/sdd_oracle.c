@@ -79,6 +79,16 @@ int oracle_max_threads(void)
 #endif
 }
 
+/* Threads of the following parallel loops (timing of the single-core baseline). */
+void oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------------------------ */
 #define CAT2_(a, b) a##_##b
 #define CAT2(a, b) CAT2_(a, b)
