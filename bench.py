@@ -224,6 +224,48 @@ def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
                                  "se * sqrt(paths) over the sampled nodes"}}
 
 
+def mix_cpu_baseline(mix, seconds):
+    """The oracle (all host cores) on a bounded sample of the batched mix: up to 256 nodes of every
+    8th problem, first time step, FP32 paths, 10^3 paths per node; converted to interface-node
+    estimates/s at the mix's paths per node with the sample's path-steps per path."""
+    import numpy as np
+
+    import oracle
+    from oracle import _clib, mc
+    from oracle.layout import interface_nodes
+    from oracle.step import monitor_on_mesh
+    import workloads as W
+
+    oracle.build()
+    n = 1000
+    steps_tot, paths_tot, t_tot = 0, 0, 0.0
+    t_start = time.perf_counter()
+    for q in mix[::8]:
+        q = q.replace(precision=W.PREC_FP32_KAHAN)
+        x, y = W.identity_mesh(q)
+        om = monitor_on_mesh(q, x, y, q.t0)
+        inp = mc.prepare(q, x, y, om, 0, np.float32)
+        nodes = interface_nodes(q.nx, q.ny, q.px, q.py, q.periodic)
+        pick = np.unique(np.linspace(0, len(nodes) - 1, 256).astype(int))
+        shift = np.stack([x[nodes[pick, 1], nodes[pick, 0]], y[nodes[pick, 1], nodes[pick, 0]]], 1)
+        t = time.perf_counter()
+        _, st = mc.interface_sums(inp, pick, nodes[pick], np.zeros(len(pick), np.int64),
+                                  np.full(len(pick), n, np.int64), shift)
+        t_tot += time.perf_counter() - t
+        steps_tot += int(st.sum())
+        paths_tot += n * len(pick)
+        if time.perf_counter() - t_start > seconds:
+            break
+    rate = steps_tot / max(t_tot, 1e-9)
+    ps_per_est = steps_tot / paths_tot * mix[0].paths_per_node
+    return {"value": rate / ps_per_est, "unit": "interface-node estimates/s",
+            "cores": int(_clib.lib().oracle_max_threads()), "kind": "oracle",
+            "sample": f"{paths_tot // n} nodes of every 8th problem x {n} paths, first time step, fp32 paths, "
+                      f"{t_tot:.1f} s; path-steps/s {rate:.4g} divided by {ps_per_est:.4g} path-steps "
+                      f"per node estimate at {mix[0].paths_per_node} paths",
+            "path_steps_per_s": rate}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -503,6 +545,8 @@ def run_mix(args):
            "one_at_a_time_fp32_s_per_step": t32, "one_at_a_time_fp64_s_per_step": t64,
            "speedup_vs_one_at_a_time_fp32": t32 / batch["s_per_step"],
            "speedup_vs_one_at_a_time_fp64": t64 / batch["s_per_step"]}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = mix_cpu_baseline(mix, args.cpu_seconds)
     print(json.dumps(out))
     return 0
 
