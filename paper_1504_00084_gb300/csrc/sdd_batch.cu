@@ -70,6 +70,7 @@ struct sdd_batch {
     std::vector<const double*> graph_x;  // mesh pointers the graph was recorded with
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;  // around the batched face + solve launches
+    cudaEvent_t count_ev[2] = {nullptr, nullptr};  // after the round-count copies to h_n_active[2..3]
     int64_t launches = 0;
     int64_t launches_per_step = 0;
     int32_t rounds_last = 0;
@@ -106,6 +107,8 @@ struct sdd_batch {
         if (ev1) cudaEventDestroy(ev1);
         if (sev0) cudaEventDestroy(sev0);
         if (sev1) cudaEventDestroy(sev1);
+        for (cudaEvent_t c : count_ev)
+            if (c) cudaEventDestroy(c);
         for (void* v : allocs) cudaFree(v);
         for (void* v : host_allocs) cudaFreeHost(v);
     }
@@ -228,17 +231,24 @@ sdd_status record_step(sdd_batch* b)
                 rounds += 1;
             }
         } else {
-            for (int r = 0; r < kMaxRounds; ++r) {
-                B_CK(launch_plan(PP, b->stream));
-                launches += 1;
-                B_CK(cudaMemcpyAsync(b->h_n_active, b->n_active, 4, cudaMemcpyDeviceToHost, b->stream));
-                B_CK(cudaStreamSynchronize(b->stream));
-                if (*b->h_n_active == 0) break;
-                const sdd_status s = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
-                if (s != SDD_OK) return s;
-                B_CK(launch_reduce(RP, b->M, b->stream));
-                launches += 2;
-                rounds += 1;
+            // one round ahead of the host's decision, as for a single problem: the round queued
+            // after the last one with work finds no pending node and changes nothing
+            for (int r = 0; r <= kMaxRounds; ++r) {
+                if (r < kMaxRounds) {
+                    B_CK(launch_plan(PP, b->stream));
+                    B_CK(cudaMemcpyAsync(b->h_n_active + 2 + (r & 1), b->n_active, 4, cudaMemcpyDeviceToHost,
+                                         b->stream));
+                    B_CK(cudaEventRecord(b->count_ev[r & 1], b->stream));
+                    const sdd_status s = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
+                    if (s != SDD_OK) return s;
+                    B_CK(launch_reduce(RP, b->M, b->stream));
+                    launches += 3;
+                }
+                if (r > 0) {
+                    B_CK(cudaEventSynchronize(b->count_ev[(r - 1) & 1]));
+                    if (b->h_n_active[2 + ((r - 1) & 1)] == 0) break;
+                    rounds = r;
+                }
             }
         }
         b->rounds_last = rounds;
@@ -352,6 +362,8 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&b->sev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->sev1);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&b->count_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess && b->M > 0)
         e = cudaMemcpy(b->node_prob, node_prob.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)

@@ -59,7 +59,8 @@ struct sdd_problem {
     void* bnd = nullptr;            //   the same in the path precision
     double* bnd_scratch = nullptr;  //   tridiagonal sweeps
     // host
-    int32_t* h_n_active = nullptr;  // pinned: [0] active nodes, [1] invalid-input flag
+    int32_t* h_n_active = nullptr;  // pinned: [0] active nodes, [1] invalid-input flag, [2..3] round counts
+    cudaEvent_t count_ev[2] = {nullptr, nullptr};  // after the copies of [2] and [3]
     sdd_stats stats{};
     std::vector<void*> allocs;
     size_t dev_bytes = 0;          // device bytes held (allocation granularity included)
@@ -81,6 +82,8 @@ struct sdd_problem {
     ~sdd_problem()
     {
         for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        for (cudaEvent_t e : count_ev)
+            if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : solve_ev)
             if (e) cudaEventDestroy(e);
         for (void* v : allocs) cudaFree(v);
