@@ -39,9 +39,10 @@ SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
 ALU_PEAK_OPS = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6  # lane-ops/s
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one path-kernel launch on this grid, from an ncu
-# capture of the current kernel: the cold fill of the packed monitor and mesh records (~1.6 MB
-# of FP32 data per 257x257 grid), which does not grow with the number of paths.
-MC_TRAFFIC_BYTES_PER_LAUNCH = 1.28e6
+# capture of the current kernel on a full round (2^19 paths per node): the cold fill of the packed
+# monitor and mesh records (~1.6 MB of FP32 data per 257x257 grid), which does not grow with the
+# number of paths.
+MC_TRAFFIC_BYTES_PER_LAUNCH = 1.65e6
 
 
 def parse():
