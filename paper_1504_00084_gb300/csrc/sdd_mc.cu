@@ -278,21 +278,39 @@ __device__ __forceinline__ T side_lerp(const T* b, int n, T s)
 
 // Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; zero
 // where the exponential is too small to change 1 - p (and then cannot be the largest p of an
-// exiting path).
-template <typename T>
-__device__ __forceinline__ T bridge_p(T d0, T d1, T q)
-{
-    const T a = d0 * d1;
-    return (a > Consts<T>::bridge_skip * q) ? (T)0 : dexp(-a / q);
-}
-// FP32: the probability is only compared with a uniform deviate, so the hardware exponential
-// and divide (a few ulp) serve; the skip rule is unchanged.
-template <>
-__device__ __forceinline__ float bridge_p<float>(float d0, float d1, float q)
-{
-    const float a = d0 * d1;
-    return (a > Consts<float>::bridge_skip * q) ? 0.0f : __expf(-__fdividef(a, q));
-}
+// exiting path).  One object per substep holds what the four sides share.
+template <typename T> struct BridgeP {
+    T q, lim;
+    __device__ __forceinline__ explicit BridgeP(T q_)
+    {
+        q = q_;
+        lim = Consts<T>::bridge_skip * q_;
+    }
+    __device__ __forceinline__ T operator()(T d0, T d1) const
+    {
+        const T a = d0 * d1;
+        return (a > lim) ? (T)0 : dexp(-a / q);
+    }
+};
+// FP32: the probability is only compared with a uniform deviate, so the hardware 2^x of
+// a (-log2 e / q) serves (a few ulp), with the approximate division done once per substep rather
+// than once per side; the skip rule is unchanged.  Arguments of 2^x stay above -29 (a <= 20 q),
+// far from the flush-to-zero range.
+template <> struct BridgeP<float> {
+    float lim, sc;
+    __device__ __forceinline__ explicit BridgeP(float q_)
+    {
+        lim = Consts<float>::bridge_skip * q_;
+        sc = __fdividef(-1.4426950408889634f, q_);
+    }
+    __device__ __forceinline__ float operator()(float d0, float d1) const
+    {
+        const float a = d0 * d1;
+        float r;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a * sc));
+        return (a > lim) ? 0.0f : r;
+    }
+};
 
 // One substep k of path p at node m.  Returns 0 while the path goes on; 1 when it exits
 // at this substep ((vx, vy) = boundary mesh at the exit point, side = exit side); 2 when it
@@ -339,8 +357,9 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
         if (en - 1 > vmax) { vmax = en - 1; s = 3; }
         bool exited = vmax > 0;
         if (!exited && P.bb) {
-            const T p0 = bridge_p(xi, xn, q), p1 = bridge_p(1 - xi, 1 - xn, q);
-            const T p2 = bridge_p(eta, en, q), p3 = bridge_p(1 - eta, 1 - en, q);
+            const BridgeP<T> bridge_p(q);
+            const T p0 = bridge_p(xi, xn), p1 = bridge_p(1 - xi, 1 - xn);
+            const T p2 = bridge_p(eta, en), p3 = bridge_p(1 - eta, 1 - en);
             T surv = 1;
             surv *= (1 - p0);
             surv *= (1 - p1);
