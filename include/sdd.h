@@ -260,6 +260,13 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
  * on the legacy default stream; returns after `out` is written. */
 sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 
+/* Test hook: the number of out-of-range gather indices the path kernel met since the library
+ * was loaded, in a build compiled with -DSDD_BOUNDS_CHECK.  Such a build checks every monitor,
+ * mesh, boundary and queue index before its load; an index outside its array is counted and
+ * replaced by 0, so the load stays in bounds.  Returns -1 in a normal build and -2 on a CUDA
+ * error.  Waits for the device. */
+int64_t sdd_debug_bounds_violations(void);
+
 /* ---- Batches of independent problems ------------------------------------------------------
  * Many problems of uneven grid and subdomain counts advance one alternating step together
  * (Sec. 3.6 for each): per problem the monitor preparation and the scatter of Dirichlet data;

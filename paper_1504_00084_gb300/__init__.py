@@ -15,7 +15,8 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsdd.so")
+# SDD_LIB_PATH selects another build of the same library (e.g. the bounds-checked one).
+LIB_PATH = os.environ.get("SDD_LIB_PATH") or os.path.join(_HERE, "_build", "libsdd.so")
 
 SDD_OK = 0
 SDD_ERR_INVALID_ARG = 1
@@ -88,6 +89,7 @@ EXPORTS = [
     "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
     "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
     "sdd_save", "sdd_load", "sdd_interface_sampling", "sdd_step_mkp", "sdd_server_cancel",
+    "sdd_debug_bounds_violations",
 ]
 
 
@@ -115,6 +117,7 @@ def _load():
         "sdd_get_monitor": ([P, P, P, P], I32),
         "sdd_debug_paths": ([P, I32, I64, I64, P, P, P], I32),
         "sdd_debug_philox": ([P, P, I64, P], I32),
+        "sdd_debug_bounds_violations": ([], I64),
         "sdd_interface_mc_noalloc": ([ctypes.POINTER(SddParams), P, P, P, I32, P, P, P], I32),
         "sdd_batch_create": ([P, I32, P, I32, ctypes.POINTER(P)], I32),
         "sdd_batch_step": ([P], I32),
@@ -304,6 +307,11 @@ def sdd_debug_paths(h: int, node: int, p_begin: int, n_paths: int):
     _check(lib.sdd_debug_paths(h, node, p_begin, n_paths, val.ctypes.data, steps.ctypes.data,
                                side.ctypes.data), "sdd_debug_paths")
     return val, steps, side
+
+
+def sdd_debug_bounds_violations() -> int:
+    """Out-of-range gather indices met so far (bounds-checked build), -1 in a normal build."""
+    return int(lib.sdd_debug_bounds_violations())
 
 
 def sdd_debug_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:

@@ -35,6 +35,9 @@ def flags(extra=()):
             "-I", os.path.join(ROOT, "include"), "-I", CSRC, *extra]
 
 
+CHECKED = os.path.join(BUILD, "checked")  # -DSDD_BOUNDS_CHECK build (test use)
+
+
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
@@ -42,15 +45,19 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in [src, *HEADERS])
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose_ptxas: bool = False, bounds_check: bool = False) -> str:
+    """Compile and link the library; bounds_check builds the index-checked variant into
+    _build/checked/libsdd.so instead."""
+    out_dir = CHECKED if bounds_check else BUILD
+    lib_path = os.path.join(out_dir, "libsdd.so")
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DSDD_BOUNDS_CHECK"] if bounds_check else [])
     jobs = []
     objs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or verbose_ptxas or _stale(obj, src):
             jobs.append([cc, *flags(extra), "-c", src, "-o", obj])
@@ -62,16 +69,17 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
                 sys.stderr.write(r.stdout + r.stderr)
             if r.returncode != 0:
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or not os.path.exists(lib_path):
+        tmp = lib_path + f".tmp{os.getpid()}"
         link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(link, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

@@ -229,6 +229,7 @@ sdd_status check_boundary(const sdd_problem* p, const double* x, const double* y
 // Monitor on the current mesh, FD gradient, packed records, estimator shifts.
 sdd_status run_prep(sdd_problem* p)
 {
+    const TraceRange trace("sdd: monitor preparation");
     PrepParams P{};
     P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic;
     P.kind = p->mon_kind; P.n_params = p->n_params; P.precision = p->prm.precision;
@@ -293,6 +294,7 @@ sdd_status timed_mc_round(sdd_problem* p, int slot)
 
 sdd_status run_mc(sdd_problem* p)
 {
+    const TraceRange trace("sdd: interface Monte Carlo");
     const int M = p->M;
     p->stats.mc_rounds = 0;
     p->stats.mc_kernel_ms = 0.0;
@@ -393,6 +395,7 @@ sdd_status run_mc(sdd_problem* p)
 
 sdd_status run_solve(sdd_problem* p)
 {
+    const TraceRange trace("sdd: subdomain solves");
     SDD_CK(launch_scatter(p->prm.nx, p->prm.ny, p->prm.periodic, p->prm.Lx, p->prm.Ly, p->nodes, p->M,
                           p->est, p->xn, p->yn, p->stream, p->prm.moving_boundary ? p->bnd64 : nullptr));
     p->launches += (p->prm.periodic ? 0 : 1) + (p->M > 0 ? 1 : 0);
@@ -784,6 +787,7 @@ sdd_status sdd_subdomain_solve(sdd_problem* p, const double* iface_xy, double* x
 sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out)
 {
     if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    const TraceRange trace("sdd_step");
     SDD_TRY(run_prep(p));
     const sdd_status s_mc = run_mc(p);
     if (s_mc != SDD_OK && s_mc != SDD_ERR_SE_NOT_REACHED) return s_mc;

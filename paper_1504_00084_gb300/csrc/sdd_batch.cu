@@ -413,6 +413,7 @@ void sdd_batch_destroy(sdd_batch* b)
 sdd_status sdd_batch_step(sdd_batch* b)
 {
     if (!b) return sdd_fail(SDD_ERR_INVALID_ARG, "batch is NULL");
+    const TraceRange trace("sdd_batch_step");
     for (sdd_problem* p : b->probs) B_CK(cudaStreamSynchronize(p->stream));
     B_CK(cudaStreamSynchronize(b->stream));  // no step of this batch in flight: safe to refresh records
     refresh_records(b);

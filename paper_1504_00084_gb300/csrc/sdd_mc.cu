@@ -49,6 +49,42 @@ __device__ __forceinline__ double dfloor(double x) { return floor(x); }
 __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double dabs(double x) { return fabs(x); }
 
+}  // namespace
+
+// Gather-index check, compiled in only with SDD_BOUNDS_CHECK: an index outside [0, n) is counted
+// in g_bounds_violations and replaced by 0, so the load stays inside its array.  The normal
+// build returns the index unchanged.
+#ifdef SDD_BOUNDS_CHECK
+__device__ unsigned long long g_bounds_violations;
+template <typename I>
+__device__ __forceinline__ I checked(I i, long n)
+{
+    if ((long)i < 0 || (long)i >= n) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        return (I)0;
+    }
+    return i;
+}
+// the same for a pointer into the n-element array at base
+template <typename V>
+__device__ __forceinline__ const V* checked_ptr(const V* q, const V* base, long n)
+{
+    const long i = q - base;
+    if (i < 0 || i >= n) {
+        atomicAdd(&g_bounds_violations, 1ull);
+        return base;
+    }
+    return q;
+}
+#else
+template <typename I>
+__device__ __forceinline__ I checked(I i, long) { return i; }
+template <typename V>
+__device__ __forceinline__ const V* checked_ptr(const V* q, const V*, long) { return q; }
+#endif
+
+namespace {
+
 // sin(2 pi u), cos(2 pi u) for u in (0, 1).  t = 4u is exact; with q = rint(t) and r = t - q
 // (exact, |r| <= 1/2) the angle is (pi/2)(q + r), so q mod 4 permutes and signs the sine and
 // cosine of (pi/2) r, taken from their Taylor series: coefficients (pi/2)^n / n! rounded to
@@ -144,8 +180,10 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
     locate(P.nx, P.periodic, xi, i, fx);
     locate(P.ny, P.periodic, eta, j, fy);
     const int base = j * P.nx + i;  // grids hold at most 2^28 nodes
-    const Mon4<T> a = load_mon(P.mon + base), b = load_mon(P.mon + (base + 1));
-    const Mon4<T> c = load_mon(P.mon + (base + P.nx)), d = load_mon(P.mon + (base + P.nx + 1));
+    const long N = (long)P.nx * P.ny;
+    const Mon4<T> a = load_mon(P.mon + checked(base, N)), b = load_mon(P.mon + checked(base + 1, N));
+    const Mon4<T> c = load_mon(P.mon + checked(base + P.nx, N));
+    const Mon4<T> d = load_mon(P.mon + checked(base + P.nx + 1, N));
     if constexpr (sizeof(T) == 4) {
         // paired FP32 arithmetic (one instruction for two lanes of work), operation for
         // operation the contraction of the plain expressions below: bit-identical results
@@ -196,10 +234,12 @@ __device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
     locate(P.nx, P.periodic, xi, i, tx);
     locate(P.ny, P.periodic, eta, j, ty);
     const int nx = P.nx, ny = P.ny;
+    const long N = (long)nx * ny;
+    auto ld = [&](const Disp2<T>* q) { return load_disp(checked_ptr(q, P.disp, N)); };
     if (!P.bicubic) {
         const Disp2<T>* r0 = P.disp + (long)j * nx + i;
-        const Disp2<T> a = load_disp(r0), b = load_disp(r0 + 1);
-        const Disp2<T> c = load_disp(r0 + nx), d = load_disp(r0 + nx + 1);
+        const Disp2<T> a = ld(r0), b = ld(r0 + 1);
+        const Disp2<T> c = ld(r0 + nx), d = ld(r0 + nx + 1);
         const T gx = 1 - tx, gy = 1 - ty;
         ix = gx * gy * a.X + tx * gy * b.X + gx * ty * c.X + tx * ty * d.X;
         iy = gx * gy * a.Y + tx * gy * b.Y + gx * ty * c.Y + tx * ty * d.Y;
@@ -227,20 +267,19 @@ __device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
             if (P.periodic) {
                 const int m = nx - 1;
                 c = ((c % m) + m) % m;
-                const Disp2<T> v = load_disp(row + c);
+                const Disp2<T> v = ld(row + c);
                 cX[a] = v.X;
                 cY[a] = v.Y;
             } else if (c < 0) {
-                const Disp2<T> v0 = load_disp(row), v1 = load_disp(row + 1), v2 = load_disp(row + 2);
+                const Disp2<T> v0 = ld(row), v1 = ld(row + 1), v2 = ld(row + 2);
                 cX[a] = 3 * v0.X - 3 * v1.X + v2.X;
                 cY[a] = 3 * v0.Y - 3 * v1.Y + v2.Y;
             } else if (c > nx - 1) {
-                const Disp2<T> v0 = load_disp(row + nx - 1), v1 = load_disp(row + nx - 2),
-                               v2 = load_disp(row + nx - 3);
+                const Disp2<T> v0 = ld(row + nx - 1), v1 = ld(row + nx - 2), v2 = ld(row + nx - 3);
                 cX[a] = 3 * v0.X - 3 * v1.X + v2.X;
                 cY[a] = 3 * v0.Y - 3 * v1.Y + v2.Y;
             } else {
-                const Disp2<T> v = load_disp(row + c);
+                const Disp2<T> v = ld(row + c);
                 cX[a] = v.X;
                 cY[a] = v.Y;
             }
@@ -273,7 +312,7 @@ __device__ __forceinline__ T side_lerp(const T* b, int n, T s)
     int c = (int)dfloor(u);
     c = c < 0 ? 0 : (c > n - 2 ? n - 2 : c);
     const T f = u - (T)c;
-    return ((T)1 - f) * b[c] + f * b[c + 1];
+    return ((T)1 - f) * b[checked(c, n)] + f * b[checked(c + 1, n)];
 }
 
 // Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; zero
@@ -478,7 +517,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
     auto drain = [&](int count) {
         __syncwarp();
         if (lane < count) {
-            const int pos = qn - count + lane;
+            const int pos = checked(qn - count + lane, 64);
             const T fx = q_xi[pos], fy = q_eta[pos];
             T ix, iy;
             mesh_at(R, fx, fy, ix, iy);
@@ -521,7 +560,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
         if (dm) {  // some lane's path ended: queue survivors, hand out the next path indices
             const unsigned sm = __ballot_sync(kFull, st == 2);
             if (st == 2) {
-                const int pos = qn + __popc(sm & lt);
+                const int pos = checked(qn + __popc(sm & lt), 64);
                 q_xi[pos] = xi;
                 q_eta[pos] = eta;
                 q_path[pos] = path;
@@ -894,3 +933,15 @@ cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, u
 }
 
 }  // namespace sdd
+
+extern "C" int64_t sdd_debug_bounds_violations(void)
+{
+#ifdef SDD_BOUNDS_CHECK
+    unsigned long long v = 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+    if (cudaMemcpyFromSymbol(&v, sdd::g_bounds_violations, sizeof v) != cudaSuccess) return -2;
+    return (int64_t)v;
+#else
+    return -1;
+#endif
+}

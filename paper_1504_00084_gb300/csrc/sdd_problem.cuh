@@ -6,8 +6,19 @@
 
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sdd.h"
 #include "sdd_internal.cuh"
+
+// NVTX range over a host scope (monitor preparation, Monte Carlo rounds, solves, batch steps,
+// server progress), for timeline tools; header-only NVTX costs nothing with no tool attached.
+struct TraceRange {
+    explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
 
 struct sdd_problem {
     sdd_params prm{};

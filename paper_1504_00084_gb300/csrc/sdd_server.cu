@@ -579,6 +579,7 @@ sdd_status sdd_server_submit(sdd_server* s, const sdd_params* params, const doub
 sdd_status sdd_server_progress(sdd_server* s, int32_t* n_running, int32_t* n_queued)
 {
     if (!s) return sdd_fail(SDD_ERR_INVALID_ARG, "server is NULL");
+    const TraceRange trace("sdd_server_progress");
     // 1. finishing requests whose work is complete
     for (auto it = s->finishing.begin(); it != s->finishing.end();) {
         Request* r = *it;
