@@ -36,6 +36,8 @@ def flags(extra=()):
 
 
 CHECKED = os.path.join(BUILD, "checked")  # -DSDD_BOUNDS_CHECK build (test use)
+SANITIZED = os.path.join(BUILD, "asan")   # host code under AddressSanitizer + UBSan (test use)
+SAN_FLAGS = "-fsanitize=address,-fsanitize=undefined,-fno-omit-frame-pointer"
 
 
 def _stale(obj: str, src: str) -> bool:
@@ -45,14 +47,18 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in [src, *HEADERS])
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, bounds_check: bool = False) -> str:
-    """Compile and link the library; bounds_check builds the index-checked variant into
-    _build/checked/libsdd.so instead."""
-    out_dir = CHECKED if bounds_check else BUILD
+def build(force: bool = False, verbose_ptxas: bool = False, bounds_check: bool = False,
+          sanitize: bool = False) -> str:
+    """Compile and link the library.  bounds_check builds the index-checked variant into
+    _build/checked/libsdd.so; sanitize builds one whose host code carries AddressSanitizer and
+    UBSan into _build/asan/libsdd.so (load it with libasan preloaded)."""
+    out_dir = CHECKED if bounds_check else (SANITIZED if sanitize else BUILD)
     lib_path = os.path.join(out_dir, "libsdd.so")
     os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DSDD_BOUNDS_CHECK"] if bounds_check else [])
+    if sanitize:
+        extra += ["-Xcompiler", SAN_FLAGS]
     jobs = []
     objs = []
     for s in SOURCES:
@@ -71,7 +77,8 @@ def build(force: bool = False, verbose_ptxas: bool = False, bounds_check: bool =
                 raise RuntimeError("nvcc failed: " + " ".join(cmd))
     if force or jobs or not os.path.exists(lib_path):
         tmp = lib_path + f".tmp{os.getpid()}"
-        link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+        link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart",
+                *(["-Xcompiler", SAN_FLAGS] if sanitize else [])]
         r = subprocess.run(link, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
