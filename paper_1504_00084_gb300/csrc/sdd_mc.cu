@@ -457,32 +457,32 @@ template <typename T> struct LaneAcc<T, kAcc64> {
     }
 };
 // Kahan-compensated FP32 sums of v - fl(shift): no FP64 work per path; converted to sums of
-// v - shift (exact shift) once per task.
+// v - shift (exact shift) once per task.  The x and y components run as paired FP32
+// instructions, element for element the scalar operations (bit-identical sums).
 template <typename T> struct LaneAcc<T, kAccKahan32> {
-    float sxf, syf;
+    float2 nshift;  // -fl(shift), (x, y)
     double ex, ey;  // shift - fl(shift)
-    float s1x = 0, c1x = 0, s2x = 0, c2x = 0, s1y = 0, c1y = 0, s2y = 0, c2y = 0;
+    float2 s1 = {0.f, 0.f}, c1 = {0.f, 0.f}, s2 = {0.f, 0.f}, c2 = {0.f, 0.f};
     __device__ __forceinline__ LaneAcc(double sx, double sy)
-        : sxf((float)sx), syf((float)sy), ex(sx - (double)(float)sx), ey(sy - (double)(float)sy) {}
-    __device__ __forceinline__ static void kahan(float& s, float& c, float v)
+        : nshift(make_float2(-(float)sx, -(float)sy)), ex(sx - (double)(float)sx), ey(sy - (double)(float)sy) {}
+    __device__ __forceinline__ static float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
+    __device__ __forceinline__ static void kahan(float2& s, float2& c, float2 v)
     {
-        const float y = __fsub_rn(v, c);
-        const float t = __fadd_rn(s, y);
-        c = __fsub_rn(__fsub_rn(t, s), y);
+        const float2 y = __fadd2_rn(v, neg(c));
+        const float2 t = __fadd2_rn(s, y);
+        c = __fadd2_rn(__fadd2_rn(t, neg(s)), neg(y));
         s = t;
     }
     __device__ __forceinline__ void add(T vx, T vy)
     {
-        const float dx = __fsub_rn((float)vx, sxf), dy = __fsub_rn((float)vy, syf);
-        kahan(s1x, c1x, dx);
-        kahan(s2x, c2x, __fmul_rn(dx, dx));
-        kahan(s1y, c1y, dy);
-        kahan(s2y, c2y, __fmul_rn(dy, dy));
+        const float2 d = __fadd2_rn(make_float2((float)vx, (float)vy), nshift);
+        kahan(s1, c1, d);
+        kahan(s2, c2, __fmul2_rn(d, d));
     }
     __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long n) const
     {
-        const double S1x = (double)s1x - (double)c1x, S2x = (double)s2x - (double)c2x;
-        const double S1y = (double)s1y - (double)c1y, S2y = (double)s2y - (double)c2y;
+        const double S1x = (double)s1.x - (double)c1.x, S2x = (double)s2.x - (double)c2.x;
+        const double S1y = (double)s1.y - (double)c1.y, S2y = (double)s2.y - (double)c2.y;
         const double nn = (double)n;
         a = S1x - nn * ex;
         b = S2x - 2.0 * ex * S1x + nn * ex * ex;
