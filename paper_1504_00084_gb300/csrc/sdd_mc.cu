@@ -451,7 +451,8 @@ template <typename T> struct LaneAcc<T, kAcc64> {
         s1y += dy;
         s2y += dy * dy;
     }
-    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long) const
+    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long, double,
+                                           double) const
     {
         a = s1x; b = s2x; c = s1y; d = s2y;
     }
@@ -461,10 +462,8 @@ template <typename T> struct LaneAcc<T, kAcc64> {
 // instructions, element for element the scalar operations (bit-identical sums).
 template <typename T> struct LaneAcc<T, kAccKahan32> {
     float2 nshift;  // -fl(shift), (x, y)
-    double ex, ey;  // shift - fl(shift)
     float2 s1 = {0.f, 0.f}, c1 = {0.f, 0.f}, s2 = {0.f, 0.f}, c2 = {0.f, 0.f};
-    __device__ __forceinline__ LaneAcc(double sx, double sy)
-        : nshift(make_float2(-(float)sx, -(float)sy)), ex(sx - (double)(float)sx), ey(sy - (double)(float)sy) {}
+    __device__ __forceinline__ LaneAcc(double sx, double sy) : nshift(make_float2(-(float)sx, -(float)sy)) {}
     __device__ __forceinline__ static float2 neg(float2 v) { return make_float2(-v.x, -v.y); }
     __device__ __forceinline__ static void kahan(float2& s, float2& c, float2 v)
     {
@@ -479,8 +478,12 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
         kahan(s1, c1, d);
         kahan(s2, c2, __fmul2_rn(d, d));
     }
-    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long n) const
+    // sx, sy: the shifts again (read at the end of the task, so that they hold no registers while
+    // paths run)
+    __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long n,
+                                           double sx, double sy) const
     {
+        const double ex = sx - (double)(float)sx, ey = sy - (double)(float)sy;  // shift - fl(shift)
         const double S1x = (double)s1.x - (double)c1.x, S2x = (double)s2.x - (double)c2.x;
         const double S1y = (double)s1.y - (double)c1.y, S2y = (double)s2.y - (double)c2.y;
         const double nn = (double)n;
@@ -563,7 +566,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
                 const int pos = checked(qn + __popc(sm & lt), 64);
                 q_xi[pos] = xi;
                 q_eta[pos] = eta;
-                q_path[pos] = path;
+                if (DEBUG) q_path[pos] = path;
             }
             qn += __popc(sm);
             if (st != 0) {
@@ -579,7 +582,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
     }
     if (qn > 0) drain(qn);
     double a, b, c, d;
-    acc.finish(a, b, c, d, paths);
+    acc.finish(a, b, c, d, paths, P.shift[2 * g], P.shift[2 * g + 1]);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_xor_sync(kFull, a, off);
