@@ -119,13 +119,10 @@ __device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs)
 }
 
 template <typename T> struct Consts;
-template <> struct Consts<float> {
-    // exp(-a) below this argument's reach leaves 1 - exp(-a) == 1 exactly (and cannot be the
-    // largest crossing probability of an exiting path), so the exponential is skipped.
-    static constexpr float bridge_skip = 20.0f;
-};
 template <> struct Consts<double> {
     static constexpr double two_pi = 6.28318530717958647692;
+    // exp(-a) below this argument's reach leaves 1 - exp(-a) == 1 exactly (and cannot be the
+    // largest crossing probability of an exiting path), so the exponential is skipped.
     static constexpr double bridge_skip = 40.0;
 };
 
@@ -315,9 +312,10 @@ __device__ __forceinline__ T side_lerp(const T* b, int n, T s)
     return ((T)1 - f) * b[checked(c, n)] + f * b[checked(c + 1, n)];
 }
 
-// Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; zero
-// where the exponential is too small to change 1 - p (and then cannot be the largest p of an
-// exiting path).  One object per substep holds what the four sides share.
+// Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; in FP64
+// zero where the exponential is too small to change 1 - p (and then cannot be the largest p of
+// an exiting path), which skips the exponential there.  One object per substep holds what the
+// four sides share.
 template <typename T> struct BridgeP {
     T q, lim;
     __device__ __forceinline__ explicit BridgeP(T q_)
@@ -333,21 +331,17 @@ template <typename T> struct BridgeP {
 };
 // FP32: the probability is only compared with a uniform deviate, so the hardware 2^x of
 // a (-log2 e / q) serves (a few ulp), with the approximate division done once per substep rather
-// than once per side; the skip rule is unchanged.  Arguments of 2^x stay above -29 (a <= 20 q),
-// far from the flush-to-zero range.
+// than once per side.  No skip is needed: where a > 20 q, p < 2^-28.8, so 1 - p rounds to 1
+// and such a side can never hold the largest p of an exiting path; 2^x of a large negative
+// argument is 0.
 template <> struct BridgeP<float> {
-    float lim, sc;
-    __device__ __forceinline__ explicit BridgeP(float q_)
-    {
-        lim = Consts<float>::bridge_skip * q_;
-        sc = __fdividef(-1.4426950408889634f, q_);
-    }
+    float sc;
+    __device__ __forceinline__ explicit BridgeP(float q_) { sc = __fdividef(-1.4426950408889634f, q_); }
     __device__ __forceinline__ float operator()(float d0, float d1) const
     {
-        const float a = d0 * d1;
         float r;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a * sc));
-        return (a > lim) ? 0.0f : r;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d0 * d1 * sc));
+        return r;
     }
 };
 
