@@ -48,6 +48,8 @@ __device__ __forceinline__ float dfloor(float x) { return floorf(x); }
 __device__ __forceinline__ double dfloor(double x) { return floor(x); }
 __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double dabs(double x) { return fabs(x); }
+__device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double dmax(double a, double b) { return fmax(a, b); }
 
 }  // namespace
 
@@ -382,13 +384,10 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
     const T en = eta + by + sd * (r * sn);
 
     if (!P.periodic) {
-        // deepest violation of the unit square; ties keep the lower side index
-        T vmax = -xn;
-        int s = 0;
-        if (xn - 1 > vmax) { vmax = xn - 1; s = 1; }
-        if (-en > vmax) { vmax = -en; s = 2; }
-        if (en - 1 > vmax) { vmax = en - 1; s = 3; }
-        bool exited = vmax > 0;
+        // outside the unit square: the largest violation is positive; its side (ties keep the
+        // lower index) is found only for the paths that exit this way, in the exit block
+        bool exited = dmax(dmax(-xn, xn - 1), dmax(-en, en - 1)) > 0;
+        int s = -1;
         if (!exited && P.bb) {
             const BridgeP<T> bridge_p(q);
             const T p0 = bridge_p(xi, xn), p1 = bridge_p(1 - xi, 1 - xn);
@@ -408,6 +407,13 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
             }
         }
         if (exited) {
+            if (s < 0) {  // deepest violation
+                T vmax = -xn;
+                s = 0;
+                if (xn - 1 > vmax) { vmax = xn - 1; s = 1; }
+                if (-en > vmax) { vmax = -en; s = 2; }
+                if (en - 1 > vmax) { vmax = en - 1; s = 3; }
+            }
             T xe = clamp01(xn), ee = clamp01(en);
             if (s == 0) xe = 0;
             if (s == 1) xe = 1;
