@@ -36,3 +36,22 @@ def test_struct_layouts_match_the_header(tmp_path):
         cls = getattr(S, STRUCTS[cname])
         got = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
         assert got == int(value), (cname, field, got, value)
+
+
+def test_binding_argument_counts_match_the_prototypes():
+    import re
+    import paper_1504_00084_gb300 as S
+    text = open(os.path.join(ROOT, "include", "sdd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = dict((m.group(1), m.group(2)) for m in re.finditer(r"\b(sdd_[a-z_0-9]+)\s*\(([^;{]*?)\)\s*;", text))
+    assert protos
+    checked = 0
+    for name, params in protos.items():
+        fn = getattr(S.lib, name)
+        if fn.argtypes is None:
+            continue
+        params = params.strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+        checked += 1
+    assert checked >= 30
