@@ -483,6 +483,7 @@ def run_mix(args):
     hs = make(prec)
     M = sum(h.M for h in hs)
     b = S.SddBatch(hs, stream=stream, use_graph=True)
+    tpb = b.tune(0)  # path-kernel block size timed on the first round (results do not depend on it)
     for _ in range(args.warmup):
         b.step()
     stream.synchronize()
@@ -508,6 +509,7 @@ def run_mix(args):
     solve_gbs = solve_bytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
     batch = {"s_per_step": T / args.steps, "interface_node_estimates_per_s": M * args.steps / T,
              "path_steps_last_step": st["path_steps"], "launches_per_step": (st["kernel_launches"] - l0) / args.steps,
+             "path_kernel_threads_per_block": tpb,
              "solve_iters_max": st["solve_iters_max"], "solve_outer_max": st["solve_outer_max"],
              "solve_rel_residual": st["solve_rel_residual"],
              "solve_roofline": {"bound": "hbm", "kernel": "solve_batch_kernel", "ms": solve_ms,

@@ -288,6 +288,16 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
  * Returns after queueing the work on the batch's stream. */
 sdd_status sdd_batch_step(sdd_batch* b);
 
+/* Threads per block of the batch's path-kernel launches: threads_per_block = 128, 256 (the
+ * default) or 512 selects one; 0 tunes it.  Tuning prepares and plans the first Monte Carlo round
+ * of the next step, times one path-kernel launch at each size on that plan (each at all the
+ * blocks per SM its registers allow) into the scratch task slots, and keeps the fastest.  No
+ * problem's state changes, and results never depend on the size: every warp runs whole tasks of
+ * fixed paths, reduced in a fixed order.  *chosen (nullable) receives the size in use.  Waits
+ * for the batch's and the problems' streams; a recorded CUDA graph is recorded again at the next
+ * step.  SDD_ERR_INVALID_ARG for any other size. */
+sdd_status sdd_batch_tune(sdd_batch* b, int32_t threads_per_block, int32_t* chosen);
+
 /* Counters of the last batch step over all problems: M, path_steps, paths, mc_rounds,
  * nodes_not_reached, max_se, solve maxima, kernel_launches (since creation), and in
  * mc_kernel_ms the device time of the whole last step and in solve_kernel_ms that of its

@@ -84,7 +84,7 @@ EXPORTS = [
     "sdd_step", "sdd_get_stats", "sdd_get_interface_nodes", "sdd_interface_layout",
     "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
     "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
-    "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy",
+    "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy", "sdd_batch_tune",
     "sdd_mesh_quality",
     "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
     "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
@@ -121,6 +121,7 @@ def _load():
         "sdd_interface_mc_noalloc": ([ctypes.POINTER(SddParams), P, P, P, I32, P, P, P], I32),
         "sdd_batch_create": ([P, I32, P, I32, ctypes.POINTER(P)], I32),
         "sdd_batch_step": ([P], I32),
+        "sdd_batch_tune": ([P, I32, ctypes.POINTER(I32)], I32),
         "sdd_batch_get_stats": ([P, ctypes.POINTER(SddStats)], I32),
         "sdd_batch_destroy": ([P], None),
         "sdd_mesh_quality": ([P, P, ctypes.POINTER(F64), ctypes.POINTER(F64)], I32),
@@ -440,6 +441,12 @@ def sdd_batch_create(problems, stream=None, use_graph=False) -> int:
     return h.value
 
 
+def sdd_batch_tune(h: int, threads_per_block: int = 0) -> int:
+    chosen = ctypes.c_int32()
+    _check(lib.sdd_batch_tune(h, threads_per_block, ctypes.byref(chosen)), "sdd_batch_tune")
+    return int(chosen.value)
+
+
 def sdd_batch_step(b: int) -> None:
     _check(lib.sdd_batch_step(b), "sdd_batch_step")
 
@@ -463,6 +470,10 @@ class SddBatch:
 
     def step(self):
         sdd_batch_step(self.h)
+
+    def tune(self, threads_per_block: int = 0) -> int:
+        """Path-kernel block size: 128, 256 or 512, or 0 to time all three and keep the fastest."""
+        return sdd_batch_tune(self.h, threads_per_block)
 
     def stats(self):
         return sdd_batch_get_stats(self.h)

@@ -47,6 +47,8 @@ struct sdd_batch {
     int total_subs = 0;
     std::vector<int32_t> node_off, sub_off;
     int mc_grid = 1;
+    int tpb = 256;                   // path-kernel threads per block (sdd_batch_tune)
+    int nsm = 1;
     // device: concatenated node arrays and round plan
     int32_t* node_prob = nullptr;
     int32_t* node_role = nullptr;    // concatenated sampling roles (null: every node by Monte Carlo)
@@ -168,12 +170,21 @@ sdd_status launch_batch_mc(sdd_batch* b)
     P.shift = b->shift;
     P.node_of = b->node_of; P.p_begin = b->p_begin; P.p_count = b->p_count; P.task_off = b->task_off;
     P.n_active = b->n_active; P.task_counter = b->task_counter; P.slots = b->slots;
-    B_CK(launch_mc<T>(P, b->acc_mode, false, true, b->mc_grid, b->stream));
+    B_CK(launch_mc<T>(P, b->acc_mode, false, true, b->mc_grid, b->stream, b->tpb));
     return SDD_OK;
 }
 
-// The launches of one step.  `capturing`: only fixed-N work (no host round trip).
-sdd_status record_step(sdd_batch* b)
+// Path-kernel block size and the persistent grid it allows (all resident blocks of every SM).
+void set_block_size(sdd_batch* b, int tpb)
+{
+    b->tpb = tpb;
+    b->mc_grid = b->nsm * (b->fp64 ? mc_max_blocks_per_sm<double>(b->acc_mode, false, true, tpb)
+                                   : mc_max_blocks_per_sm<float>(b->acc_mode, false, true, tpb));
+}
+
+// The launches of one step.  `capturing`: only fixed-N work (no host round trip).  first_plan:
+// stop after planning the first Monte Carlo round (used to time the path kernel).
+sdd_status record_step(sdd_batch* b, bool first_plan = false)
 {
     const size_t rec = b->fp64 ? sizeof(McProblem<double>) : sizeof(McProblem<float>);
     int64_t launches = 0;
@@ -219,6 +230,10 @@ sdd_status record_step(sdd_batch* b)
         RP.slots = b->slots; RP.shift = b->shift; RP.acc = b->acc; RP.n_done = b->n_done; RP.steps = b->steps;
         RP.paths_run = b->paths_run; RP.next_total = b->next_total;
         RP.se_target = adaptive ? q.se_target : 0.0; RP.max_paths = maxp;
+        if (first_plan) {
+            B_CK(launch_plan(PP, b->stream));
+            return SDD_OK;
+        }
         int32_t rounds = 0;
         if (!adaptive) {
             const int64_t nr = (n0 + kMaxChunk - 1) / kMaxChunk;
@@ -394,11 +409,10 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
         delete b;
         return sdd_fail(e == cudaErrorMemoryAllocation ? SDD_ERR_OOM : SDD_ERR_CUDA, m.c_str());
     }
-    int dev = 0, nsm = 1;
+    int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    b->mc_grid = nsm * (b->fp64 ? mc_max_blocks_per_sm<double>(b->acc_mode, false, true)
-                                : mc_max_blocks_per_sm<float>(b->acc_mode, false, true));
+    cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+    set_block_size(b, 256);
     *out = b;
     return SDD_OK;
 }
@@ -454,6 +468,58 @@ sdd_status sdd_batch_step(sdd_batch* b)
         p->stats.step_index = (int32_t)p->step;
         p->stats.t = p->prm.t0 + (double)p->step * p->prm.dt;
     }
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_tune(sdd_batch* b, int32_t threads_per_block, int32_t* chosen)
+{
+    if (!b) return sdd_fail(SDD_ERR_INVALID_ARG, "batch is NULL");
+    if (threads_per_block != 0 && threads_per_block != 128 && threads_per_block != 256 && threads_per_block != 512)
+        return sdd_fail(SDD_ERR_INVALID_ARG, "threads_per_block must be 0, 128, 256 or 512");
+    const TraceRange trace("sdd_batch_tune");
+    for (sdd_problem* p : b->probs) B_CK(cudaStreamSynchronize(p->stream));
+    B_CK(cudaStreamSynchronize(b->stream));
+    int pick = threads_per_block;
+    if (pick == 0 && b->M == 0) pick = b->tpb;
+    if (pick == 0) {
+        // the next step's first round, up to its plan; then one path-kernel launch per candidate
+        // on that plan, into the scratch task slots (no problem's state changes: the next step
+        // prepares, initialises and plans again)
+        refresh_records(b);
+        sdd_status st = record_step(b, true);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t ce = cudaSuccess;
+        if (st == SDD_OK) ce = cudaEventCreate(&e0);
+        if (st == SDD_OK && ce == cudaSuccess) ce = cudaEventCreate(&e1);
+        float best = 0.f;
+        const int cand[3] = {128, 256, 512};
+        for (int k = 0; k < 3 && st == SDD_OK && ce == cudaSuccess; ++k) {
+            set_block_size(b, cand[k]);
+            ce = cudaMemsetAsync(b->task_counter, 0, sizeof(int32_t), b->stream);
+            if (ce == cudaSuccess) ce = cudaEventRecord(e0, b->stream);
+            if (ce != cudaSuccess) break;
+            st = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
+            if (st != SDD_OK) break;
+            ce = cudaEventRecord(e1, b->stream);
+            if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+            if (ce == cudaSuccess && (pick == 0 || ms < best)) {
+                best = ms;
+                pick = cand[k];
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st != SDD_OK) return st;
+        if (ce != cudaSuccess) return sdd_fail(SDD_ERR_CUDA, cudaGetErrorString(ce));
+    }
+    set_block_size(b, pick);
+    if (b->graph) {  // recorded with the previous size
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    if (chosen) *chosen = b->tpb;
     return SDD_OK;
 }
 

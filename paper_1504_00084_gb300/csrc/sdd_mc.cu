@@ -36,8 +36,10 @@ constexpr unsigned kFull = 0xffffffffu;
 #ifndef SDD_MC_MIN_BLOCKS
 #define SDD_MC_MIN_BLOCKS 4   // FP32: resident blocks per SM asked of the register allocator (64 registers)
 #endif
-// FP64 paths need more registers; two resident blocks keep them out of local memory.
-template <typename T> constexpr int mc_min_blocks() { return sizeof(T) == 8 ? 2 : SDD_MC_MIN_BLOCKS; }
+// FP64 paths need more registers; two resident blocks keep them out of local memory.  Other block
+// sizes (batched launches, chosen by sdd_batch_tune) keep the same threads per SM.
+template <typename T, int TPB = kMcThreads>
+constexpr int mc_min_blocks() { return (sizeof(T) == 8 ? 2 : SDD_MC_MIN_BLOCKS) * kMcThreads / TPB; }
 
 __device__ __forceinline__ float dlog(float x) { return logf(x); }
 __device__ __forceinline__ double dlog(double x) { return log(x); }
@@ -598,10 +600,10 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
 // Persistent path kernel.  BATCH: tasks of several problems share the launch; each task reads
 // its problem's record (the Philox counter uses the problem-local node id, so a problem's
 // results do not depend on what else shares the launch).
-template <typename T, int ACC, bool DEBUG, bool BATCH>
-__global__ void __launch_bounds__(kMcThreads, mc_min_blocks<T>()) mc_kernel(const __grid_constant__ McParams<T> P)
+template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB = kMcThreads>
+__global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(const __grid_constant__ McParams<T> P)
 {
-    constexpr int kWarps = kMcThreads / 32;
+    constexpr int kWarps = TPB / 32;
     __shared__ T q_xi[kWarps][64], q_eta[kWarps][64];
     __shared__ uint32_t q_path[kWarps][64];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -839,17 +841,27 @@ __global__ void philox_kernel(const uint32_t* ctr, const uint32_t* key, int64_t 
     out[4 * i + 3] = r.w;
 }
 
-template <typename T, int ACC, bool DEBUG, bool BATCH>
+template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB = kMcThreads>
 const void* mc_kernel_ptr()
 {
-    return reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG, BATCH>);
+    return reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG, BATCH, TPB>);
+}
+
+template <typename T, int TPB>
+const void* select_batch_mc(int acc_mode)
+{
+    return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false, true, TPB>()
+                                   : mc_kernel_ptr<T, kAcc64, false, true, TPB>();
 }
 
 template <typename T>
-const void* select_mc(int acc_mode, bool debug, bool batch)
+const void* select_mc(int acc_mode, bool debug, bool batch, int tpb)
 {
-    if (batch) return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false, true>()
-                                              : mc_kernel_ptr<T, kAcc64, false, true>();
+    if (batch) {
+        if (tpb == 128) return select_batch_mc<T, 128>(acc_mode);
+        if (tpb == 512) return select_batch_mc<T, 512>(acc_mode);
+        return select_batch_mc<T, kMcThreads>(acc_mode);
+    }
     if (debug) return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, true, false>()
                                               : mc_kernel_ptr<T, kAcc64, true, false>();
     return acc_mode == kAccKahan32 ? mc_kernel_ptr<T, kAccKahan32, false, false>()
@@ -858,13 +870,22 @@ const void* select_mc(int acc_mode, bool debug, bool batch)
 
 }  // namespace
 
+template <typename T, int TPB>
+void launch_batch_mc_kernel(const McParams<T>& P, bool kahan, int grid, cudaStream_t s)
+{
+    if (kahan) mc_kernel<T, kAccKahan32, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+    else mc_kernel<T, kAcc64, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+}
+
 template <typename T>
-cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s)
+cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s,
+                      int tpb)
 {
     const bool kahan = acc_mode == kAccKahan32;
     if (batch) {
-        if (kahan) mc_kernel<T, kAccKahan32, false, true><<<grid, kMcThreads, 0, s>>>(P);
-        else mc_kernel<T, kAcc64, false, true><<<grid, kMcThreads, 0, s>>>(P);
+        if (tpb == 128) launch_batch_mc_kernel<T, 128>(P, kahan, grid, s);
+        else if (tpb == 512) launch_batch_mc_kernel<T, 512>(P, kahan, grid, s);
+        else launch_batch_mc_kernel<T, kMcThreads>(P, kahan, grid, s);
     } else if (debug) {
         if (kahan) mc_kernel<T, kAccKahan32, true, false><<<grid, kMcThreads, 0, s>>>(P);
         else mc_kernel<T, kAcc64, true, false><<<grid, kMcThreads, 0, s>>>(P);
@@ -876,19 +897,20 @@ cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch
 }
 
 template <typename T>
-int mc_max_blocks_per_sm(int acc_mode, bool debug, bool batch)
+int mc_max_blocks_per_sm(int acc_mode, bool debug, bool batch, int tpb)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_mc<T>(acc_mode, debug, batch), kMcThreads,
+    const int threads = batch && (tpb == 128 || tpb == 512) ? tpb : kMcThreads;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, select_mc<T>(acc_mode, debug, batch, tpb), threads,
                                                       0) != cudaSuccess)
         return 1;
     return nb > 0 ? nb : 1;
 }
 
-template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, bool, int, cudaStream_t);
-template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, bool, int, cudaStream_t);
-template int mc_max_blocks_per_sm<float>(int, bool, bool);
-template int mc_max_blocks_per_sm<double>(int, bool, bool);
+template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, bool, int, cudaStream_t, int);
+template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, bool, int, cudaStream_t, int);
+template int mc_max_blocks_per_sm<float>(int, bool, bool, int);
+template int mc_max_blocks_per_sm<double>(int, bool, bool, int);
 
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
                            int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s,

@@ -112,3 +112,32 @@ def test_batch_mixing_subdomain_schemes_equals_alone():
         gx, gy = h.mesh()
         assert np.array_equal(gx, rx) and np.array_equal(gy, ry)
         h.close()
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_block_size_tuning_keeps_results(use_graph):
+    """sdd_batch_tune: the path-kernel block size (128, 256 or 512 threads, or tuned by timing all
+    three on the next step's first round) never changes results: every size gives bitwise the
+    meshes of stepping each problem alone, tuning itself changes no problem's state, and an
+    unsupported size is rejected."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    probs = small_mix(W.PREC_FP32_KAHAN, paths=4096, n=4)
+    steps = 3
+    ref = meshes_alone(probs, steps)
+    stream = torch.cuda.Stream()
+    hs = [gpu_problem(p) for p in probs]
+    with S.SddBatch(hs, stream=stream, use_graph=use_graph) as b:
+        assert b.tune(0) in (128, 256, 512)
+        for tpb in (128, 512, 256):
+            assert b.tune(tpb) == tpb
+            b.step()
+        with pytest.raises(S.SddError):
+            b.tune(96)
+        b.stats()
+    stream.synchronize()
+    for h, (rx, ry) in zip(hs, ref):
+        gx, gy = h.mesh()
+        assert np.array_equal(gx, rx) and np.array_equal(gy, ry)
+        h.close()
