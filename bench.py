@@ -74,6 +74,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="serve: mean arrivals per second")
     ap.add_argument("--serve-first-chunk", type=int, default=10000, help="serve: first paths per node")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0, help="serve: device-memory budget")
+    ap.add_argument("--serve-fp64-baseline", type=int, default=0,
+                    help="serve: also step the first K requests one at a time in plain FP64 (same SE target)")
     ap.add_argument("--serve-round-paths", type=int, default=1 << 27,
                     help="serve: paths per round, oldest requests first (0: all pending chunks)")
     ap.add_argument("--mix-n", type=int, default=64)
@@ -638,6 +640,22 @@ def run_serve(args):
            "kernel_launches": s1["kernel_launches"] - s0["kernel_launches"],
            "allocations": s1["allocations"], "resident_gb": s1["resident_bytes"] / 2 ** 30,
            "pool_gb": s1["pool_bytes"] / 2 ** 30, "pool_high_water": s1["pool_high_water"]}
+    kb = min(args.serve_fp64_baseline, n)
+    if kb > 0:
+        # the plain per-problem path: the same requests stepped one at a time with FP64 paths and
+        # FP64 sums at the same standard-error target
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for k in range(kb):
+            q = reqs[k].replace(precision=W.PREC_FP64)
+            x, y = meshes[k]
+            with S.SddProblem(S.params_from(q), x, y) as h:
+                h.set_monitor_analytic(q.monitor_kind, q.monitor_params)
+                h.step()
+        torch.cuda.synchronize()
+        ts = (time.perf_counter() - t) / kb
+        out["sequential_fp64"] = {"requests": kb, "s_per_request": ts, "requests_per_s": 1.0 / ts,
+                                  "served_speedup": (n / T) * ts}
     print(json.dumps(out))
     return 0
 
