@@ -338,25 +338,27 @@ sdd_status run_mc(sdd_problem* p)
         }
         p->stats.mc_rounds = (int32_t)rounds;
     } else {
-        // Rounds run one ahead of the host's decision: round r is queued before the host reads
-        // round r-1's count of active nodes, so the GPU does not wait on the host round trip.
-        // A round queued after the last one with work finds no pending node; its plan, path
-        // kernel and reduction change nothing.
-        for (int r = 0; r <= kMaxAdaptiveRounds; ++r) {
-            if (r < kMaxAdaptiveRounds) {
+        // Rounds run kRoundsAhead ahead of the host's decision: rounds r+1 .. r+kRoundsAhead are
+        // queued before the host reads round r's count of active nodes, so the GPU does not wait
+        // on the host's round trip even when the host thread is slow to wake.  A round queued
+        // after the last one with work finds no pending node; its plan, path kernel and
+        // reduction change nothing.
+        int queued = 0;
+        for (int r = 0; r < kMaxAdaptiveRounds; ++r) {
+            for (; queued < kMaxAdaptiveRounds && queued <= r + kRoundsAhead; ++queued) {
+                const int slot = queued % (kRoundsAhead + 1);
                 SDD_CK(launch_plan(PP, p->stream));
-                SDD_CK(cudaMemcpyAsync(p->h_n_active + 2 + (r & 1), p->n_active, sizeof(int32_t),
+                SDD_CK(cudaMemcpyAsync(p->h_n_active + 2 + slot, p->n_active, sizeof(int32_t),
                                        cudaMemcpyDeviceToHost, p->stream));
-                SDD_CK(cudaEventRecord(p->count_ev[r & 1], p->stream));
+                SDD_CK(cudaEventRecord(p->count_ev[slot], p->stream));
                 SDD_TRY(timed_mc_round(p, n_timed++));
                 SDD_CK(launch_reduce(RP, M, p->stream));
                 p->launches += 3;
             }
-            if (r > 0) {
-                SDD_CK(cudaEventSynchronize(p->count_ev[(r - 1) & 1]));
-                if (p->h_n_active[2 + ((r - 1) & 1)] == 0) break;
-                p->stats.mc_rounds = r;
-            }
+            const int slot = r % (kRoundsAhead + 1);
+            SDD_CK(cudaEventSynchronize(p->count_ev[slot]));
+            if (p->h_n_active[2 + slot] == 0) break;
+            p->stats.mc_rounds = r + 1;
         }
     }
     SDD_CK(launch_output(M, p->acc, p->n_done, p->shift, p->est, p->se, p->stream));
@@ -545,8 +547,8 @@ sdd_status sdd_alloc_problem(const sdd_params& prm, cudaStream_t stream, bool wi
         if (e == cudaSuccess) e = p->dalloc(ptr, b);
         if (e == cudaSuccess) p->dev_bytes += alloc_rounded(b);
     });
-    if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_n_active, 16, cudaHostAllocDefault);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&p->h_n_active, 32, cudaHostAllocDefault);
+    for (int k = 0; k <= kRoundsAhead && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&p->count_ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -72,7 +72,7 @@ struct sdd_batch {
     std::vector<const double*> graph_x;  // mesh pointers the graph was recorded with
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t sev0 = nullptr, sev1 = nullptr;  // around the batched face + solve launches
-    cudaEvent_t count_ev[2] = {nullptr, nullptr};  // after the round-count copies to h_n_active[2..3]
+    cudaEvent_t count_ev[kRoundsAhead + 1] = {};  // after the round-count copies to h_n_active[2..]
     int64_t launches = 0;
     int64_t launches_per_step = 0;
     int32_t rounds_last = 0;
@@ -246,24 +246,25 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
                 rounds += 1;
             }
         } else {
-            // one round ahead of the host's decision, as for a single problem: the round queued
-            // after the last one with work finds no pending node and changes nothing
-            for (int r = 0; r <= kMaxRounds; ++r) {
-                if (r < kMaxRounds) {
+            // kRoundsAhead rounds ahead of the host's decision, as for a single problem: rounds
+            // queued after the last one with work find no pending node and change nothing
+            int queued = 0;
+            for (int r = 0; r < kMaxRounds; ++r) {
+                for (; queued < kMaxRounds && queued <= r + kRoundsAhead; ++queued) {
+                    const int slot = queued % (kRoundsAhead + 1);
                     B_CK(launch_plan(PP, b->stream));
-                    B_CK(cudaMemcpyAsync(b->h_n_active + 2 + (r & 1), b->n_active, 4, cudaMemcpyDeviceToHost,
+                    B_CK(cudaMemcpyAsync(b->h_n_active + 2 + slot, b->n_active, 4, cudaMemcpyDeviceToHost,
                                          b->stream));
-                    B_CK(cudaEventRecord(b->count_ev[r & 1], b->stream));
+                    B_CK(cudaEventRecord(b->count_ev[slot], b->stream));
                     const sdd_status s = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
                     if (s != SDD_OK) return s;
                     B_CK(launch_reduce(RP, b->M, b->stream));
                     launches += 3;
                 }
-                if (r > 0) {
-                    B_CK(cudaEventSynchronize(b->count_ev[(r - 1) & 1]));
-                    if (b->h_n_active[2 + ((r - 1) & 1)] == 0) break;
-                    rounds = r;
-                }
+                const int slot = r % (kRoundsAhead + 1);
+                B_CK(cudaEventSynchronize(b->count_ev[slot]));
+                if (b->h_n_active[2 + slot] == 0) break;
+                rounds = r + 1;
             }
         }
         b->rounds_last = rounds;
@@ -370,14 +371,14 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     ALLOC(b->order_dev, sizeof(int2) * (size_t)(b->total_subs > 0 ? b->total_subs : 1));
     if (sampled_any) ALLOC(b->node_role, M * 4);
     HALLOC(b->mcprob_host, rec * n); HALLOC(b->solve_host, sizeof(SolveParams) * n); HALLOC(b->t_host, 8 * n);
-    HALLOC(b->h_n_active, 16);
+    HALLOC(b->h_n_active, 32);
 #undef ALLOC
 #undef HALLOC
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&b->sev0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->sev1);
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+    for (int k = 0; k <= kRoundsAhead && e == cudaSuccess; ++k)
         e = cudaEventCreateWithFlags(&b->count_ev[k], cudaEventDisableTiming);
     if (e == cudaSuccess && b->M > 0)
         e = cudaMemcpy(b->node_prob, node_prob.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);

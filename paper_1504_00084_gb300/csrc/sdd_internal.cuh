@@ -84,6 +84,7 @@ enum AccMode { kAcc64 = 0, kAccKahan32 = 1 };
 
 // Paths handed to one warp at a time (64 per lane on average).
 constexpr int kPathsPerTask = 2048;
+constexpr int kRoundsAhead = 2;  // adaptive Monte Carlo rounds queued ahead of the host's decision
 // Adaptive chunk totals are multiples of this many paths.
 constexpr int64_t kAdaptiveGranule = 1024;
 

@@ -70,8 +70,8 @@ struct sdd_problem {
     void* bnd = nullptr;            //   the same in the path precision
     double* bnd_scratch = nullptr;  //   tridiagonal sweeps
     // host
-    int32_t* h_n_active = nullptr;  // pinned: [0] active nodes, [1] invalid-input flag, [2..3] round counts
-    cudaEvent_t count_ev[2] = {nullptr, nullptr};  // after the copies of [2] and [3]
+    int32_t* h_n_active = nullptr;  // pinned: [0] active nodes, [1] invalid-input flag, [2..] round counts
+    cudaEvent_t count_ev[sdd::kRoundsAhead + 1] = {};  // after the copies of the round counts
     sdd_stats stats{};
     std::vector<void*> allocs;
     size_t dev_bytes = 0;          // device bytes held (allocation granularity included)
