@@ -269,6 +269,42 @@ def mix_cpu_baseline(mix, seconds):
             "path_steps_per_s": rate}
 
 
+def accuracy_vs_fp64_oracle(prob, stream, n=4096, nodes=8):
+    """The bench problem's first step at a fixed n paths per node on the GPU (the bench's own
+    precision), against the oracle with FP64 paths and sums on the same Philox streams, at a
+    spread of nodes: the largest difference of the estimates, absolute and in units of the GPU's
+    standard error.  Near the front, paths are chaotic (a rounding difference can grow by orders
+    of magnitude), so the two are draws of the same estimator rather than equal numbers."""
+    import numpy as np
+
+    import oracle
+    import paper_1504_00084_gb300 as S
+    from oracle import mc
+    from oracle.layout import interface_nodes
+    from oracle.step import monitor_on_mesh
+    import workloads as W
+
+    oracle.build()
+    q = prob.replace(se_target=0.0, paths_per_node=n, max_paths_per_node=n)
+    x, y = W.identity_mesh(q)
+    with S.SddProblem(S.params_from(q), x, y, stream=stream) as h:
+        h.set_monitor_analytic(q.monitor_kind, q.monitor_params)
+        est, se, _, _ = h.interface_mc()
+    q64 = q.replace(precision=W.PREC_FP64)
+    om = monitor_on_mesh(q64, x, y, q64.t0)
+    inp = mc.prepare(q64, x, y, om, 0, np.float64)
+    ij = interface_nodes(q.nx, q.ny, q.px, q.py, q.periodic)
+    pick = np.linspace(0, len(ij) - 1, nodes).astype(int)
+    shift = np.stack([x[ij[pick, 1], ij[pick, 0]], y[ij[pick, 1], ij[pick, 0]]], 1)
+    sums, _ = mc.interface_sums(inp, pick, ij[pick], np.zeros(len(pick), np.int64),
+                                np.full(len(pick), n, np.int64), shift)
+    oest, _, _ = mc.estimate(sums, np.full(len(pick), n), shift)
+    d = np.abs(est[pick] - oest)
+    return {"nodes": int(len(pick)), "paths_per_node": n, "max_abs": float(d.max()),
+            "max_in_se": float((d / np.maximum(se[pick], 1e-300)).max()),
+            "basis": "first step at fixed paths; GPU at the bench precision vs the FP64 oracle"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -415,6 +451,8 @@ def run_ours(args):
     if not args.no_cpu_baseline and world == 1:
         ps_per_est = path_steps / max(M * args.steps, 1)
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, ps_per_est)
+        # part of the oracle leg: the GPU's first-step estimates against the FP64 oracle's
+        out["cpu_baseline"]["accuracy_vs_fp64_oracle"] = accuracy_vs_fp64_oracle(prob, stream)
     print(json.dumps(out))
     if dist is not None:
         dist.destroy_process_group()
