@@ -31,12 +31,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "interface-node estimates/s & path-steps/s at SE≤1e-4; % FP32 peak; p99 latency"
 UNIT = "interface-node estimates/s"
-# Irreducible 32-bit lane operations of one FP32 path-step (Philox4x32-10, three uniforms,
-# Box-Muller, bilinear monitor gather, Euler-Maruyama update, endpoint and bridge tests, loop
-# control); itemised with the roofline in the design notes.
-OPS_PER_PATH_STEP = 230
-SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
-ALU_PEAK_OPS = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6  # lane-ops/s
+# Algorithmic 32-bit operations of one path-step (Sec. 3.4, Eq. 7), each special function
+# counted once: Philox4x32-10 (10 rounds of two 32x32->64 products as hi/lo pairs and two
+# three-way xors) 60, three uniforms 9, Box-Muller (one log, one sqrt, one sin, one cos and
+# their products) 8, bilinear gather of three fields (cell location, weights, 12 FMA) 30,
+# drift and diffusion (one sqrt) 5, Euler-Maruyama update 4, endpoint test 6, Brownian-bridge
+# test (distances, four exponentials, survival product, compare) 28, loop and path bookkeeping 8.
+OPS_PER_PATH_STEP = 158
+# Issued warp instructions per path-step of the current FP32 path kernel on the benchmarked
+# configuration (ncu, smsp__inst_executed.sum / path-steps on a full 2^19-path round); the
+# issue fraction below divides by 4 warp instructions per clock per SM.
+WARP_INST_PER_PATH_STEP = 11.02
+LANES_PER_SM_CLK, ISSUE_PER_SM_CLK, SM_MAX_MHZ = 128, 4, 2070.0
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one path-kernel launch on this grid, from an ncu
 # capture of the current kernel on a full round (2^19 paths per node): the cold fill of the packed
@@ -168,10 +174,11 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
+def cpu_baseline(prob, seconds):
     """The oracle (C core, OpenMP over nodes, all host cores) on a bounded sample of the same
     workload: a spread of interface nodes, first time step, FP32 paths.  Converted to
-    interface-node estimates/s with the path-steps one estimate at SE <= target needs."""
+    interface-node estimates/s with the path-steps one estimate at SE <= target needs, taken
+    from the sample itself (the same basis in the repository's line and the reference arm)."""
     import numpy as np
 
     import oracle
@@ -213,7 +220,7 @@ def cpu_baseline(prob, seconds, ps_per_estimate_hint=None):
     _, _, se = mc.estimate(sums, np.full(len(pick), n), shift)
     need = np.maximum((se.max(axis=1) / prob.se_target) ** 2, 1.0) * n  # paths for SE <= target
     sigma = se.max(axis=1) * np.sqrt(n)  # per-path standard deviation of the node values
-    ps_per_est = float(np.mean(need * steps / n)) if ps_per_estimate_hint is None else ps_per_estimate_hint
+    ps_per_est = float(np.mean(need * steps / n))
     return {"value": rate / ps_per_est, "unit": UNIT, "cores": cores,
             "kind": "oracle",
             "sample": f"{len(pick)} of {M} interface nodes x {n} paths, first time step, "
@@ -428,7 +435,11 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    achieved = OPS_PER_PATH_STEP * path_steps / (mc_ms / 1e3) if mc_ms > 0 else 0.0
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else SM_MAX_MHZ
+    alu_peak = sms * LANES_PER_SM_CLK * mhz * 1e6  # lane-ops/s
+    ps_rate = path_steps / (mc_ms / 1e3) if mc_ms > 0 else 0.0
+    achieved = OPS_PER_PATH_STEP * ps_rate
     out = {"metric": METRIC, "value": est_all / T_all, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * T_all / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -439,18 +450,24 @@ def run_ours(args):
            "max_se": max_se, "nodes_not_reached": not_reached,
            "wall_s": wall,
            "gpu_launches": int(launches),
-           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": ALU_PEAK_OPS / 1e12,
-                        "unit": "Tops/s (32-bit lane ops)", "frac": achieved / ALU_PEAK_OPS,
+           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
+                        "unit": "Tops/s (32-bit lane ops)", "frac": achieved / alu_peak,
                         "traffic": MC_TRAFFIC_BYTES_PER_LAUNCH if args.precision == "kahan" else None,
                         "traffic_unit": "bytes per launch", "kernel": "mc_kernel<float>",
                         "ops_per_path_step": OPS_PER_PATH_STEP,
+                        "ops_basis": "algorithmic operations of a path-step, each special function once",
+                        "path_steps_per_s_in_kernel": ps_rate,
                         "kernel_ms": mc_ms, "kernel_launches": mc_launches,
                         "kernel_share_of_step": (mc_ms / 1e3) / T if T > 0 else None,
-                        "peak_basis": "152 SMs x 128 lanes x 2070 MHz (recipe unit counts and max clock)"},
+                        "peak_basis": f"{sms} SMs (queried) x {LANES_PER_SM_CLK} lanes x {mhz:.0f} MHz "
+                                      f"(median sampled SM clock under load)",
+                        "issue": {"warp_inst_per_path_step": WARP_INST_PER_PATH_STEP,
+                                  "frac": WARP_INST_PER_PATH_STEP * ps_rate / (sms * ISSUE_PER_SM_CLK * mhz * 1e6),
+                                  "basis": "issued warp instructions (ncu count of this kernel) over "
+                                           "4 per clock per SM: the instruction-level fraction"}},
            "clocks": clocks, "e2e": e2e}
     if not args.no_cpu_baseline and world == 1:
-        ps_per_est = path_steps / max(M * args.steps, 1)
-        out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, ps_per_est)
+        out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         # part of the oracle leg: the GPU's first-step estimates against the FP64 oracle's
         out["cpu_baseline"]["accuracy_vs_fp64_oracle"] = accuracy_vs_fp64_oracle(prob, stream)
     print(json.dumps(out))

@@ -426,13 +426,19 @@ void sdd_server_destroy(sdd_server* s);
  *            without waiting for the GPU.
  * Intermediates live in one 16 MiB device array inside the library, held by every GPU that
  * loads it until the process exits.  Requests needing more are rejected with
- * SDD_ERR_INVALID_ARG: the requirement is about 72 B per grid node (FP32; 120 B in FP64),
- * 200 B per interface node and 48 B per task of min(N, 2^19)/2048 paths per node -- e.g. a
- * 257x257 grid with 1521 interface nodes fits for N <= 2.6e5.  Host pointers are rejected.
- * The first call on a device (with that device current) resolves the array's device address
- * with cudaGetSymbolAddress; make that first call before any stream capture.  Every call
- * shares the array and leaves its contents behind; each call re-initialises what it reads,
- * and calls that overlap on the GPU race.  Errors are reported by the status only
+ * SDD_ERR_INVALID_ARG: the requirement is 48 B per grid node (FP32; 72 B in FP64), 116 B per
+ * interface node and 48 B per task of 2048 paths, min(N, 2^19)/2048 tasks per interface node
+ * (rounded up), each block aligned to 256 B -- e.g. a 257x257 grid with 1521 interface nodes
+ * fits in FP32 for N <= 3.7e5.  Host pointers are rejected.  A problem without interface nodes
+ * (one Dirichlet subdomain) returns SDD_OK and writes nothing (est_xy and se_xy may be NULL).
+ * The inputs are not validated on the device: the estimates are undefined unless omega is
+ * finite and > 0, x and y are finite, and on Dirichlet grids the boundary nodes of (x, y) are
+ * the identity mesh (sdd_interface_mc reports such inputs as SDD_ERR_INVALID_ARG instead).
+ * The first call with a device current resolves the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.  The address is
+ * resolved again when the device's context has changed since (after cudaDeviceReset).
+ * Every call shares the array and leaves its contents behind; each call re-initialises what it
+ * reads, and calls that overlap on the GPU race.  Errors are reported by the status only
  * (sdd_last_error is not updated by this call). */
 sdd_status sdd_interface_mc_noalloc(const sdd_params* params, const double* x, const double* y,
                                     const double* omega, int32_t step_index, double* est_xy,

@@ -50,13 +50,41 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t
     return c;
 }
 
+// The same generator with its ten round keys given: rk[2r], rk[2r + 1] is the key of round r
+// (key0 + r W0, key1 + r W1).  A launch over one problem reads them from its parameter block,
+// so no key arithmetic runs per call.
+__device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t* rk)
+{
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t h0 = __umulhi(kM0, c.x), l0 = kM0 * c.x;
+        const uint32_t h1 = __umulhi(kM1, c.z), l1 = kM1 * c.z;
+        c = U4{h1 ^ c.y ^ rk[2 * r], l1, h0 ^ c.w ^ rk[2 * r + 1], l0};
+    }
+    return c;
+}
+
+// Round keys of philox4x32_10_rk for the 64-bit seed (key0 = low word, key1 = high word).
+inline void philox_round_keys(uint64_t seed, uint32_t rk[20])
+{
+    uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk[2 * r] = k0;
+        rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
 // Uniform in (0, 1) from one word without rounding: FP32 keeps the top 23 bits,
 // u = (floor(w / 2^9) + 1/2) 2^-23; FP64 u = (w + 1/2) 2^-32.  Built from the exponent bits
 // of [1, 2): 1 + k 2^-23 (resp. 1 + w 2^-32) minus (1 - 2^-24) (resp. 1 - 2^-33); the
 // difference is representable, so the subtraction is exact.
 __device__ __forceinline__ float uniform_open(uint32_t w, float)
 {
-    return __int_as_float(0x3F800000 | (w >> 9)) - 0x1.fffffep-1f;
+    // w >> 9 < 2^23, so adding the exponent bits equals or-ing them (one shift-and-add)
+    return __int_as_float((w >> 9) + 0x3F800000u) - 0x1.fffffep-1f;
 }
 __device__ __forceinline__ double uniform_open(uint32_t w, double)
 {
@@ -98,6 +126,8 @@ template <typename T> struct McProblem {
     T Lx, Ly;
     uint32_t key0, key1, tstep;
     int32_t node_offset;       // global index of the problem's node 0 in the launch's node arrays
+    uint32_t rk[20];           // Philox round keys of (key0, key1) (single-problem launches)
+    uint32_t cell_bias;        // (nx + 1) * 0x4B000000 mod 2^32: see monitor_at
     const T* bnd;              // moving boundary: tangential boundary coordinates (null: identity)
 };
 

@@ -50,8 +50,8 @@ __device__ __forceinline__ float dfloor(float x) { return floorf(x); }
 __device__ __forceinline__ double dfloor(double x) { return floor(x); }
 __device__ __forceinline__ float dabs(float x) { return fabsf(x); }
 __device__ __forceinline__ double dabs(double x) { return fabs(x); }
-__device__ __forceinline__ float dmax(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ double dmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float dmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double dmin(double a, double b) { return fmin(a, b); }
 
 }  // namespace
 
@@ -97,8 +97,11 @@ namespace {
 __device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs)
 {
     const float t = 4.0f * u;
-    const float q = rintf(t);
-    const int qint = (int)q;
+    // q = rint(t) from the rounding of t + 1.5 2^23 (unit spacing there, ties to even, as rintf);
+    // the sum's low mantissa bits hold q itself, so q mod 4 needs no conversion
+    const float big = t + 0x1.8p23f;
+    const float q = big - 0x1.8p23f;
+    const int qint = __float_as_int(big);
     const float r = t - q;
     const float r2 = r * r;
     float ps = 0x1.507834p-13f;                 // (pi/2)^9 / 9!
@@ -173,14 +176,40 @@ __device__ __forceinline__ void locate(int n, int periodic, T s, int& cell, T& f
 }
 
 // Bilinear interpolation of the packed monitor at (xi, eta) (Sec. 3.4).
+// FP32 cell and offset of coordinate s in [0, 1] on a Dirichlet n-node line, without
+// conversions: v = min(s (n - 1), n - 3/2) has floor(v) = the clamped cell (cell n - 2 for
+// s = 1), and v + 2^23 rounded down holds floor(v) in its low mantissa bits (unit spacing
+// there), so it is the float 2^23 + cell, exactly; the returned bits are 0x4B000000 + cell.
+// Paths inside the unit square only (a Dirichlet path leaves at its first step outside).
+__device__ __forceinline__ uint32_t locate_dirichlet(int n, float s, float& frac)
+{
+    const float u = s * (float)(n - 1);
+    const float v = fminf(u, (float)(n - 1) - 0.5f);
+    const float t = __fadd_rd(v, 0x1.0p23f);
+    frac = u - (t - 0x1.0p23f);
+    return (uint32_t)__float_as_int(t);
+}
+
 template <typename T>
 __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T& w, T& wx, T& we)
 {
-    int i, j;
     T fx, fy;
-    locate(P.nx, P.periodic, xi, i, fx);
-    locate(P.ny, P.periodic, eta, j, fy);
-    const int base = j * P.nx + i;  // grids hold at most 2^28 nodes
+    int base;  // grids hold at most 2^28 nodes
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (!P.periodic) {
+            const uint32_t bi = locate_dirichlet(P.nx, xi, fx);
+            const uint32_t bj = locate_dirichlet(P.ny, eta, fy);
+            base = (int)(bj * (uint32_t)P.nx + bi - P.cell_bias);
+            done = true;
+        }
+    }
+    if (!done) {
+        int i, j;
+        locate(P.nx, P.periodic, xi, i, fx);
+        locate(P.ny, P.periodic, eta, j, fy);
+        base = j * P.nx + i;
+    }
     const long N = (long)P.nx * P.ny;
     const Mon4<T> a = load_mon(P.mon + checked(base, N)), b = load_mon(P.mon + checked(base + 1, N));
     const Mon4<T> c = load_mon(P.mon + checked(base + P.nx, N));
@@ -353,14 +382,44 @@ template <> struct BridgeP<float> {
 // at this substep ((vx, vy) = boundary mesh at the exit point, side = exit side); 2 when it
 // completes its K-th substep ((xi, eta) = final point; its value, the previous mesh there,
 // is evaluated later for 32 such paths at once).
-template <typename T>
+// RK: the problem record holds the round keys in the launch's parameter block (single-problem
+// launches); otherwise the keys are stepped inside the generator.
+// The parts of Philox rounds 0 and 1 that do not depend on the substep k (counter (k, p, m, n)):
+// round 0's product of word 2 (the node id m) and round 1's product of word 0 (which depends on
+// p and m only) are taken once per path.
+struct PhiloxHoist {
+    uint32_t tz;    // n ^ rk1: round 0's word 2 input besides hi(M0 k)
+    uint32_t y1k;   // lo(M1 m) ^ rk2: round 1's word 0 input besides hi(M1 z1)
+    uint32_t H, L;  // hi, lo of M0 x1 with x1 = hi(M1 m) ^ p ^ rk0 (per path)
+};
+
+__device__ __forceinline__ U4 philox_hoisted(const uint32_t* rk, const PhiloxHoist& h, uint32_t k)
+{
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    const uint32_t h0 = __umulhi(kM0, k), l0 = kM0 * k;
+    const uint32_t z1 = h0 ^ h.tz;           // round 0 output (x1, y1, z1, l0)
+    const uint32_t h1 = __umulhi(kM1, z1), l1 = kM1 * z1;
+    U4 c{h1 ^ h.y1k, l1, h.H ^ l0 ^ rk[3], h.L};
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+        const uint32_t a0 = __umulhi(kM0, c.x), b0 = kM0 * c.x;
+        const uint32_t a1 = __umulhi(kM1, c.z), b1 = kM1 * c.z;
+        c = U4{a1 ^ c.y ^ rk[2 * r], b1, a0 ^ c.w ^ rk[2 * r + 1], b0};
+    }
+    return c;
+}
+
+template <typename T, bool RK>
 __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, uint32_t p, int k,
-                                             T& xi, T& eta, T& vx, T& vy, int& side)
+                                             T& xi, T& eta, T& vx, T& vy, int& side, const PhiloxHoist& ph)
 {
     // the monitor gather first: its loads are in flight while Philox runs
     T wv, wx, we;
     monitor_at(P, xi, eta, wv, wx, we);
-    const U4 w = philox4x32_10(U4{(uint32_t)k, p, m, P.tstep}, P.key0, P.key1);
+    const U4 c{(uint32_t)k, p, m, P.tstep};
+    U4 w;
+    if constexpr (RK) w = philox_hoisted(P.rk, ph, (uint32_t)k);
+    else w = philox4x32_10(c, P.key0, P.key1);
     const T u1 = uniform_open(w.x, T()), u2 = uniform_open(w.y, T()), ub = uniform_open(w.z, T());
     const T lgu = dlog(u1);
     T sn, cs;
@@ -386,14 +445,18 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
     const T en = eta + by + sd * (r * sn);
 
     if (!P.periodic) {
-        // outside the unit square: the largest violation is positive; its side (ties keep the
-        // lower index) is found only for the paths that exit this way, in the exit block
-        bool exited = dmax(dmax(-xn, xn - 1), dmax(-en, en - 1)) > 0;
+        // outside the unit square: the largest violation is positive, i.e. the smallest of the
+        // distances xn, 1 - xn, en, 1 - en is negative (1 - v is exactly -(v - 1) in floating
+        // point, so the two forms decide alike); the distances serve the bridge test as well.
+        // The side (ties keep the lower index) is found only for the paths that exit this way,
+        // in the exit block.
+        const T oxn = 1 - xn, oen = 1 - en;
+        bool exited = dmin(dmin(xn, oxn), dmin(en, oen)) < 0;
         int s = -1;
         if (!exited && P.bb) {
             const BridgeP<T> bridge_p(q);
-            const T p0 = bridge_p(xi, xn), p1 = bridge_p(1 - xi, 1 - xn);
-            const T p2 = bridge_p(eta, en), p3 = bridge_p(1 - eta, 1 - en);
+            const T p0 = bridge_p(xi, xn), p1 = bridge_p(1 - xi, oxn);
+            const T p2 = bridge_p(eta, en), p3 = bridge_p(1 - eta, oen);
             T surv = 1;
             surv *= (1 - p0);
             surv *= (1 - p1);
@@ -497,7 +560,7 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
 };
 
 // Paths pb .. pe-1 of local node m of problem R (global node g): one warp, one task.
-template <typename T, int ACC, bool DEBUG>
+template <typename T, int ACC, bool DEBUG, bool RK>
 __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T>& R, int m, int g,
                                          int task, int64_t pb, int64_t pe, T* q_xi, T* q_eta,
                                          uint32_t* q_path)
@@ -512,6 +575,17 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
     LaneAcc<T, ACC> acc(sx, sy);
     uint32_t steps = 0, paths = 0;          // per lane and task: far below 2^32
     uint32_t path = (uint32_t)pb + lane;    // path indices are below 2^32
+    PhiloxHoist ph{};
+    uint32_t x1base = 0;
+    if constexpr (RK) {
+        constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+        ph.tz = R.tstep ^ R.rk[1];
+        ph.y1k = (kM1 * (uint32_t)m) ^ R.rk[2];
+        x1base = __umulhi(kM1, (uint32_t)m) ^ R.rk[0];
+        const uint32_t x1 = x1base ^ path;
+        ph.H = __umulhi(kM0, x1);
+        ph.L = kM0 * x1;
+    }
     const uint32_t pend = (uint32_t)pe;
     bool live = path < pend;
     uint32_t next = (uint32_t)pb + 32;
@@ -544,7 +618,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
         if (live) {
             T vx, vy;
             int side;
-            st = path_substep<T>(R, (uint32_t)m, path, k, xi, eta, vx, vy, side);
+            st = path_substep<T, RK>(R, (uint32_t)m, path, k, xi, eta, vx, vy, side, ph);
             ++k;
             if (st != 0) {
                 steps += (uint32_t)k;
@@ -573,6 +647,11 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
             qn += __popc(sm);
             if (st != 0) {
                 path = next + __popc(dm & lt);
+                if constexpr (RK) {
+                    const uint32_t x1 = x1base ^ path;
+                    ph.H = __umulhi(0xD2511F53u, x1);
+                    ph.L = 0xD2511F53u * x1;
+                }
                 live = path < pend;
                 xi = xi0;
                 eta = eta0;
@@ -625,10 +704,10 @@ __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(cons
         const int64_t pe = pb + kPathsPerTask < chunk_end ? pb + kPathsPerTask : chunk_end;
         if constexpr (BATCH) {
             const McProblem<T> R = P.probs[P.node_prob[g]];
-            run_task<T, ACC, DEBUG>(P, R, g - R.node_offset, g, task, pb, pe, q_xi[warp], q_eta[warp],
-                                    q_path[warp]);
+            run_task<T, ACC, DEBUG, false>(P, R, g - R.node_offset, g, task, pb, pe, q_xi[warp], q_eta[warp],
+                                           q_path[warp]);
         } else {
-            run_task<T, ACC, DEBUG>(P, P.prob, g, g, task, pb, pe, q_xi[warp], q_eta[warp], q_path[warp]);
+            run_task<T, ACC, DEBUG, true>(P, P.prob, g, g, task, pb, pe, q_xi[warp], q_eta[warp], q_path[warp]);
         }
     }
 }

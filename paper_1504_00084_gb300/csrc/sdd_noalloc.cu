@@ -11,8 +11,13 @@
 // re-initialises everything it reads, and calls that overlap on the GPU race.
 //
 // The array's name in host code is a host-side stand-in, not a device address; its device
-// address is resolved once per device with cudaGetSymbolAddress on the first call made with
-// that device current (make that first call before any stream capture).
+// address is resolved with cudaGetSymbolAddress on the first call made with a device current
+// (make that first call before any stream capture), and again whenever that device's context
+// has changed since (a cudaDeviceReset in between reloads the module at another address).
+//
+// Inputs are not checked on the device: omega must be finite and > 0, the mesh finite, and on
+// Dirichlet grids the boundary the identity; otherwise the estimates are undefined.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,8 +37,43 @@ constexpr int64_t kMaxChunk = int64_t(1) << 19;     // paths per node per launch
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-void* g_scratch_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+// Device address of g_noalloc_scratch per device, with the unique id of the context it was
+// resolved in (context ids are never reused within a process).
+struct ScratchAddr {
+    void* addr = nullptr;
+    unsigned long long ctx_id = 0;
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
 std::mutex g_scratch_mu;
+
+// Unique id of the calling thread's current context (0 when there is none or the driver
+// entry points are unavailable).  The driver functions are found through the runtime, so the
+// library needs no link against the driver library.
+unsigned long long current_context_id()
+{
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        cudaGetLastError();
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 sdd_status scratch_for_current_device(void** out)
 {
@@ -44,16 +84,20 @@ sdd_status scratch_for_current_device(void** out)
     }
     if (dev < 0 || dev >= kMaxDevices) return SDD_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    ScratchAddr& c = g_scratch_addr[dev];
+    const unsigned long long id = current_context_id();
+    if (!c.addr || id == 0 || id != c.ctx_id) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // creates the context if needed
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
+            c = ScratchAddr{};
             return SDD_ERR_CUDA;
         }
-        g_scratch_addr[dev] = p;
+        c.addr = p;
+        c.ctx_id = current_context_id();
     }
-    *out = g_scratch_addr[dev];
+    *out = c.addr;
     return SDD_OK;
 }
 
@@ -161,6 +205,8 @@ sdd_status run(const sdd_params* P, const Buffers& b, int M, int acc_mode, int32
     R.Lx = (T)P->Lx; R.Ly = (T)P->Ly;
     R.key0 = (uint32_t)(P->seed & 0xFFFFFFFFu);
     R.key1 = (uint32_t)(P->seed >> 32);
+    philox_round_keys(P->seed, R.rk);
+    R.cell_bias = (uint32_t)(P->nx + 1) * 0x4B000000u;
     R.tstep = (uint32_t)step_index;
     R.node_offset = 0;
     mp.shift = b.shift;
@@ -196,7 +242,7 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
                                                const double* omega, int32_t step_index, double* est_xy,
                                                double* se_xy, void* stream)
 {
-    if (!P || !x || !y || !omega || !est_xy || !se_xy || step_index < 0) return SDD_ERR_INVALID_ARG;
+    if (!P || !x || !y || !omega || step_index < 0) return SDD_ERR_INVALID_ARG;
     if (P->nx < 3 || P->ny < 3 || P->px < 1 || P->py < 1 || (P->nx - 1) % P->px || (P->ny - 1) % P->py)
         return SDD_ERR_INVALID_ARG;
     if ((P->periodic != 0 && P->periodic != 1) || (P->form != SDD_FORM_DIV && P->form != SDD_FORM_WINSLOW) ||
@@ -213,7 +259,8 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
     const int64_t nhl = P->periodic ? P->py : P->py - 1;
     const int64_t M = nvl * nj + nhl * (int64_t)P->px * (sx - 1);
     const int64_t N = (int64_t)P->nx * P->ny;
-    if (M < 1 || M > (int64_t(1) << 20) || N > (int64_t(1) << 24)) return SDD_ERR_INVALID_ARG;
+    if (M < 0 || M > (int64_t(1) << 20) || N > (int64_t(1) << 24)) return SDD_ERR_INVALID_ARG;
+    if (M > 0 && (!est_xy || !se_xy)) return SDD_ERR_INVALID_ARG;
     const int64_t chunk = P->paths_per_node < kMaxChunk ? P->paths_per_node : kMaxChunk;
     const int64_t slots = M * ((chunk + kPathsPerTask - 1) / kPathsPerTask);
     const bool fp64 = P->precision == SDD_FP64;
@@ -221,8 +268,9 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
     Carve sizing{nullptr};
     if (carve(sizing, b, (size_t)N, (size_t)M, (size_t)slots, fp64 ? 8 : 4) > kScratchBytes)
         return SDD_ERR_INVALID_ARG;  // larger than the fixed scratch array
-    if (!on_device(x) || !on_device(y) || !on_device(omega) || !on_device(est_xy) || !on_device(se_xy))
-        return SDD_ERR_INVALID_ARG;
+    if (!on_device(x) || !on_device(y) || !on_device(omega)) return SDD_ERR_INVALID_ARG;
+    if (M == 0) return SDD_OK;  // one Dirichlet subdomain: no interface node, nothing to write
+    if (!on_device(est_xy) || !on_device(se_xy)) return SDD_ERR_INVALID_ARG;
     void* base = nullptr;
     const sdd_status st = scratch_for_current_device(&base);
     if (st != SDD_OK) return st;

@@ -144,3 +144,15 @@ def test_interface_node_limit(sdd):
     assert sdd.lib.sdd_create_problem(ctypes.byref(p), x.ctypes.data, x.ctypes.data, None,
                                       ctypes.byref(h)) == sdd.SDD_ERR_INVALID_ARG
     assert b"2^23" in sdd.lib.sdd_last_error()
+
+
+def test_noalloc_source_calls_no_allocator():
+    """The allocation-free entry point's translation unit names no device or host allocation
+    routine of the CUDA runtime or driver (its intermediates live in a fixed device array)."""
+    import re
+    src = open(os.path.join(ROOT, "paper_1504_00084_gb300", "csrc", "sdd_noalloc.cu")).read()
+    code = re.sub(r"//[^\n]*", "", src)   # comments may name what the code avoids
+    for name in ("cudaMalloc", "cudaFree", "cudaMallocAsync", "cudaFreeAsync", "cudaHostAlloc", "cudaMallocHost",
+                 "cudaMallocManaged", "cudaMallocPitch", "cudaMalloc3D", "cudaMallocArray", "cuMemAlloc",
+                 "cuMemCreate", "cudaMemPool", "malloc(", "new ", "std::vector"):
+        assert name not in code, name

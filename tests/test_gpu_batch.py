@@ -141,3 +141,54 @@ def test_batch_block_size_tuning_keeps_results(use_graph):
         gx, gy = h.mesh()
         assert np.array_equal(gx, rx) and np.array_equal(gy, ry)
         h.close()
+
+
+def oracle_anchor_problems(paths=1000):
+    """FP64 problems of uneven shapes for the oracle comparisons of batches and served requests:
+    33 x 33 split 3 x 5 (subdomains of 10/11/11 by 6/6/7/6/7 cells, Gaussian monitor), a
+    periodic 33 x 33 split 3 x 3 with the peak off centre at tau = 1, and the paper's generator
+    form on a 25 x 25 grid split 2 x 3 at tau = 1.  (Periodic paths never exit: at tau = 1e-2
+    their 100 substeps multiply a position difference by ~1e5, so a second step started from
+    meshes that differ at 1e-10 would differ at 1e-5; at tau = 1 the factor stays near 1.)"""
+    base = W.c0_small_fp64().replace(paths_per_node=paths)
+    return [base.replace(px=3, py=5, seed=11),
+            base.replace(px=3, py=3, periodic=1, tau=1.0, monitor_params=[6.0, 40.0, 0.3, 0.6], seed=12),
+            base.replace(nx=25, ny=25, px=2, py=3, form=W.FORM_WINSLOW, tau=1.0, seed=13)]
+
+
+def test_batch_fp64_matches_oracle():
+    """Batched steps against the oracle itself: three FP64 problems of different grids, uneven
+    splits, boundary kinds and generator forms in one batch (plus one of the bump-monitor mix),
+    two steps.  After the first step every interface node's new position (its estimate) is the
+    oracle's within 1e-10, and every mesh node within the interface tolerance plus the solver's
+    residual bound; after the second, the meshes are within 1e-9 of two oracle steps."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    from gpu_helpers import mesh_tolerance
+    from oracle import step as ostep
+    probs = oracle_anchor_problems()
+    extra = small_mix(W.PREC_FP64, paths=1000, n=1)[0]
+    hs = [gpu_problem(p) for p in probs + [extra]]
+    stream = torch.cuda.Stream()
+    with S.SddBatch(hs, stream=stream) as b:
+        b.step()
+        stream.synchronize()
+        first = [h.mesh() for h in hs[:3]]
+        b.step()
+        stream.synchronize()
+    for prob, h, (g1x, g1y) in zip(probs, hs, first):
+        x, y = W.identity_mesh(prob)
+        r1 = ostep.step(prob, x, y, prob.t0, 0)
+        nodes = r1["nodes"]
+        g_est = np.stack([g1x[nodes[:, 1], nodes[:, 0]], g1y[nodes[:, 1], nodes[:, 0]]], 1)
+        assert np.abs(g_est - r1["est"]).max() <= 1e-10
+        bx, by = ostep.scatter(prob, nodes, r1["est"])
+        tol = mesh_tolerance(prob, r1["omega"], bx, by, x, y, 1e-10)
+        assert np.abs(g1x - r1["x"]).max() <= tol and np.abs(g1y - r1["y"]).max() <= tol
+        r2 = ostep.step(prob, r1["x"], r1["y"], prob.t0 + prob.dt, 1)
+        g2x, g2y = h.mesh()
+        assert np.abs(g2x - r2["x"]).max() <= 1e-9 and np.abs(g2y - r2["y"]).max() <= 1e-9
+        assert h.stats()["step_index"] == 2
+    for h in hs:
+        h.close()

@@ -7,7 +7,7 @@ import pytest
 import workloads as W
 from gpu_helpers import gpu_problem
 from oracle import step as ostep
-from test_gpu_parity import _mesh_tolerance
+from gpu_helpers import mesh_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -40,12 +40,12 @@ def test_mkp_matches_oracle_fp64(monitor):
     gx, gy, _ = h.step_mkp(K)
     r0 = ostep.step(prob, x, y, prob.t0, 0)
     ox1, oy1 = r0["x"], r0["y"]
-    tol1 = _mesh_tolerance(prob, r0["omega"], *ostep.scatter(prob, r0["nodes"], r0["est"]), x, y, 1e-10)
+    tol1 = mesh_tolerance(prob, r0["omega"], *ostep.scatter(prob, r0["nodes"], r0["est"]), x, y, 1e-10)
     assert np.abs(x1 - ox1).max() <= tol1 and np.abs(y1 - oy1).max() <= tol1
     r = ostep.mkp_step(prob, x1, y1, prob.t0 + prob.dt, 1, K)
     sub = prob.replace(dt=prob.dt / K)
     bx, by = ostep.scatter(sub, r["nodes"], r["est"])
-    tol = K * 2 * _mesh_tolerance(sub, r["omega"], bx, by, x1, y1, 1e-10)
+    tol = K * 2 * mesh_tolerance(sub, r["omega"], bx, by, x1, y1, 1e-10)
     assert np.abs(gx - r["x"]).max() <= tol and np.abs(gy - r["y"]).max() <= tol
     st = h.stats()
     assert st["step_index"] == 2 and abs(st["t"] - (prob.t0 + 2 * prob.dt)) < 1e-15

@@ -1,23 +1,22 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle on the same seeded inputs
 and Philox streams.  Tolerances: per-path values 1e-12 (FP64) / 1e-5 (FP32); exit steps and
-sides bit-exact wherever the oracle's decision margins clear the precision's noise floor;
-node estimates 1e-10 (FP64); meshes within the interface tolerance plus the solver's
-residual bound (see test docstrings)."""
+sides bit-exact on every path whose oracle decision margin exceeds about one rounding unit
+(1e-12 FP64, 1e-7 FP32), with such near ties at most 0.1 % of the paths; node estimates 1e-10
+(FP64); meshes within the interface tolerance plus the solver's residual bound (see test
+docstrings)."""
 import math
 
 import numpy as np
 import pytest
 
 import workloads as W
-from gpu_helpers import compare_paths, gpu_problem, oracle_inputs, real_of
+from gpu_helpers import (FP32_VAL, FP64_VAL, compare_node_paths, gpu_problem, mesh_tolerance, oracle_inputs,
+                         real_of)
 from oracle import mc, step as ostep
 from oracle.solve import box_system, solve_box
 from oracle.layout import subdomains
 
 pytestmark = pytest.mark.gpu
-
-FP64_MARGIN, FP64_VAL = 1e-9, 1e-12
-FP32_MARGIN, FP32_VAL = 1e-4, 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -60,23 +59,19 @@ def _paths_case(S, prob, nodes_to_check, n, mesh=None):
     x, y = mesh if mesh is not None else W.identity_mesh(prob)
     h = gpu_problem(prob, x, y)
     om, inp, nodes = oracle_inputs(prob, x, y, prob.t0, 0)
-    fp64 = prob.precision == W.PREC_FP64
-    res = []
-    for m in nodes_to_check:
-        gv, gs, gd = h.debug_paths(m, 0, n)
-        ov, os_, od, mg = mc.paths(inp, m, int(nodes[m, 0]), int(nodes[m, 1]), 0, n)
-        res.append(compare_paths(gv, gs, gd, ov, os_, od, mg,
-                                 FP64_MARGIN if fp64 else FP32_MARGIN, FP64_VAL if fp64 else FP32_VAL))
+    tally = compare_node_paths(h, inp, nodes, nodes_to_check, n, prob)
     h.close()
-    return res
+    return tally
 
 
 @pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_ACC64])
 def test_paths_c0(S, precision):
+    """Every path: exit step and side as the oracle's (outside near ties, which number at most
+    0.1 %), value within 1e-12 (FP64) / 1e-5 (FP32) wherever the decisions agree."""
     prob = W.c0_small_fp64().replace(precision=precision)
-    res = _paths_case(S, prob, [0, 15, 30, 45, 60], 1000)
-    for robust, mism in res:
-        assert robust > (0.999 if precision == W.PREC_FP64 else 0.95)
+    t = _paths_case(S, prob, [0, 15, 30, 45, 60], 1000).check()
+    if precision == W.PREC_FP64:
+        assert t.mism == 0
 
 
 @pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_ACC64])
@@ -99,9 +94,47 @@ def test_paths_variants(S, precision, variant):
         prob = prob.replace(moving_boundary=1, monitor_params=[10.0, 8.0, 0.5, 0.2])
     else:
         mesh = W.sine_mode_mesh(prob, amp=0.04)
-    res = _paths_case(S, prob, [0, 7, 20], 700, mesh)
-    for robust, mism in res:
-        assert robust > (0.999 if precision == W.PREC_FP64 else 0.9)
+    t = _paths_case(S, prob, [0, 7, 20], 700, mesh).check()
+    if precision == W.PREC_FP64:
+        assert t.mism == 0
+
+
+@pytest.mark.parametrize("K", [1, 2, 5])
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_KAHAN])
+def test_front257_short_horizon_all_nodes(S, K, precision):
+    """The benchmarked configuration (257x257, 4x4, all 1521 interface nodes, moving front,
+    ds = 1e-5) over a short horizon of K substeps (dt = K ds), element by element.
+
+    - Exit step and side: the oracle's on every one of 64 paths per node, outside near ties.
+    - FP64 node estimates at 1000 paths per node within 1e-10 of the oracle's, path counts and
+      substep totals exact; FP32 estimates within 0.1 standard error (1e-6 at K = 1).
+    - Per-path values within 1e-12 (FP64) / 1e-5 (FP32): at K = 1 on every path.  From the
+      second substep on, a path inside the front carries a drift whose gradient times ds is
+      about 2.5e3 (grad omega / tau changes by ~1e4 per cell of 1/256), so a rounding-level
+      position difference is multiplied by that factor at each such substep; values then stay
+      within tolerance on at least 99.8 % (K = 2) and 98 % (K = 5) of the paths."""
+    prob = W.c1_front(precision).replace(substeps=K, dt=K * 1e-5, paths_per_node=1000, se_target=0.0,
+                                         max_paths_per_node=1000)
+    x, y = W.identity_mesh(prob)
+    h = gpu_problem(prob, x, y)
+    est, se, n, _ = h.interface_mc()
+    total_steps = h.stats()["path_steps"]
+    om, inp, nodes = oracle_inputs(prob, x, y, prob.t0, 0)
+    assert len(nodes) == 1521
+    tally = compare_node_paths(h, inp, nodes, range(len(nodes)), 64, prob)
+    h.close()
+    tally.check(value_frac={1: 1.0, 2: 0.998, 5: 0.98}[K])
+    if precision == W.PREC_FP64:
+        assert tally.mism == 0
+    oest, ose, on, osteps = mc.interface_mc(prob, x, y, om, nodes, 0, real_of(prob))
+    assert np.array_equal(n, on)
+    if precision == W.PREC_FP64:
+        assert total_steps == int(osteps.sum())
+        assert np.abs(est - oest).max() <= 1e-10
+        assert np.abs(se - ose).max() <= 1e-10
+    else:
+        bound = 1e-6 if K == 1 else 0.1 * np.maximum(se, 1e-6)
+        assert np.all(np.abs(est - oest) <= bound)
 
 
 def test_node_estimates_c0_fp64(S):
@@ -143,22 +176,6 @@ def test_adaptive_matches_oracle(S):
     h.close()
 
 
-def _mesh_tolerance(prob, om, rims_x, rims_y, xn, yn, est_tol):
-    """Interface tolerance (max principle carries it into the interiors) plus the solver's
-    bound ||x - x*||_2 <= ||A^-1|| rtol ||b||_2 with ||A^-1|| <= 1 / lambda_min, lambda_min >= 1
-    (form 0) or >= min omega (form 1)."""
-    lam = 1.0 if prob.form == W.FORM_DIV else float(om.min())
-    worst = 0.0
-    for (i0, i1, j0, j1) in subdomains(prob.nx, prob.ny, prob.px, prob.py):
-        if i1 - i0 < 2 or j1 - j0 < 2:
-            continue
-        A, rhs, _ = box_system(om, None, i0, i1, j0, j1, prob.dt, prob.tau, prob.form)
-        bx = np.linalg.norm(rhs(rims_x, xn))
-        by = np.linalg.norm(rhs(rims_y, yn))
-        worst = max(worst, prob.solve_rtol * max(bx, by) / lam)
-    return est_tol + worst + 1e-12
-
-
 @pytest.mark.parametrize("variant", ["c0", "periodic", "winslow", "uneven", "uneven_periodic",
                                      "forward_euler", "forward_euler_winslow_periodic", "moving_boundary"])
 def test_full_step_fp64(S, variant):
@@ -185,7 +202,7 @@ def test_full_step_fp64(S, variant):
     gx, gy, status = h.step()
     r = ostep.step(prob, x, y, prob.t0, 0)
     bx, by = ostep.scatter(prob, r["nodes"], r["est"], r["bnd"])
-    tol = _mesh_tolerance(prob, r["omega"], bx, by, x, y, 1e-10)
+    tol = mesh_tolerance(prob, r["omega"], bx, by, x, y, 1e-10)
     assert np.abs(gx - r["x"]).max() <= tol
     assert np.abs(gy - r["y"]).max() <= tol
     if prob.moving_boundary:
@@ -206,7 +223,7 @@ def test_subdomain_solve_fp32_refinement_matches_oracle(S):
     om = ostep.monitor_on_mesh(prob, x, y, prob.t0)
     bx, by = ostep.scatter(prob, nodes, iface)
     ox, oy = ostep.subdomain_solves(prob, om, bx, by, x, y)
-    tol = _mesh_tolerance(prob, om, bx, by, x, y, 0.0)
+    tol = mesh_tolerance(prob, om, bx, by, x, y, 0.0)
     assert np.abs(gx - ox).max() <= tol and np.abs(gy - oy).max() <= tol
     assert h.stats()["solve_outer_max"] >= 2
     h.close()
@@ -313,12 +330,9 @@ def test_large_grid_sampled_nodes(S, precision):
     assert len(nodes) == 122625 and np.all(n == 256)
     pick = np.linspace(0, len(nodes) - 1, 7).astype(int)
     fp64 = precision == W.PREC_FP64
-    for m in pick:
-        gv, gs, gd = h.debug_paths(int(m), 0, 256)
-        ov, os_, od, mg = mc.paths(inp, int(m), int(nodes[m, 0]), int(nodes[m, 1]), 0, 256)
-        robust, _ = compare_paths(gv, gs, gd, ov, os_, od, mg, FP64_MARGIN if fp64 else FP32_MARGIN,
-                                  FP64_VAL if fp64 else FP32_VAL)
-        assert robust > (0.999 if fp64 else 0.95)
+    t = compare_node_paths(h, inp, nodes, pick, 256, prob).check()
+    if fp64:
+        assert t.mism == 0
     shift = np.stack([x[nodes[pick, 1], nodes[pick, 0]], y[nodes[pick, 1], nodes[pick, 0]]], 1)
     sums, _ = mc.interface_sums(inp, pick, nodes[pick], np.zeros(len(pick), np.int64),
                                 np.full(len(pick), 256, np.int64), shift)

@@ -1,6 +1,7 @@
 """Mesh quality on the GPU (Eq. 8) and the paper's periodic five-ring experiment (Sec. 4.2):
-100 SDD steps on 41 x 41 nodes with 2 x 2 and 4 x 4 subdomains against the single-domain
-reference mesh; the paper reports R_max = R_mean = 1."""
+100 SDD steps on 41 x 41 nodes with 2 x 2, 3 x 3 and 4 x 4 subdomains against the single-domain
+reference mesh (the paper reports R_max = R_mean = 1), and in the paper's one-substep setting
+against the oracle's own SDD trajectory."""
 import numpy as np
 import pytest
 
@@ -39,39 +40,75 @@ def test_ring_monitor_parity():
     h.close()
 
 
-def _five_ring(px, substeps):
-    prob = W.five_ring(px).replace(substeps=substeps)
-    x, y = W.identity_mesh(prob)
-    h = gpu_problem(prob, x, y)
-    for _ in range(prob.steps):
+def _single_domain_reference(prob):
+    xs, ys = W.identity_mesh(prob)
+    for n in range(prob.steps):
+        om = monitor_on_grid(prob.monitor_kind, prob.monitor_params, xs, ys, n * prob.dt, 1, prob.Lx, prob.Ly)
+        xs, ys = periodic_single_domain_step(om, xs, ys, prob.dt, prob.tau, prob.form, prob.Lx, prob.Ly)
+    return cell_quality(xs, ys)
+
+
+def _five_ring_gpu(prob, keep=()):
+    h = gpu_problem(prob)
+    kept = {}
+    for s in range(1, prob.steps + 1):
         h.step()
+        if s in keep:
+            kept[s] = h.mesh()
     gx, gy = h.mesh()
     q_gpu, _, _ = h.quality()
     h.close()
     q_sdd = cell_quality(gx, gy)
     assert np.allclose(q_gpu, q_sdd, rtol=1e-12)
-    xs, ys = x, y
-    for n in range(prob.steps):
-        om = monitor_on_grid(prob.monitor_kind, prob.monitor_params, xs, ys, n * prob.dt, 1, prob.Lx, prob.Ly)
-        xs, ys = periodic_single_domain_step(om, xs, ys, prob.dt, prob.tau, prob.form, prob.Lx, prob.Ly)
-    q_sd = cell_quality(xs, ys)
-    r = ratio_stats(q_sd, q_sdd)
-    print(f"five-ring {px}x{px} K={substeps}: {r} Q_SD max {q_sd.max():.3f} Q_SDD max {q_sdd.max():.3f}")
-    assert q_sd.max() > 1.2  # the mesh adapted: cells concentrate at the rings
-    return r
+    return q_sdd, kept
 
 
 @pytest.mark.parametrize("px", [2, 3, 4])
-@pytest.mark.parametrize("substeps", [1, 16])
-def test_five_ring_quality_ratio(px, substeps):
-    """Paper's setting is one Euler-Maruyama substep per step.  The rings are resolved by about
-    one cell (the monitor jumps from 1 to 9.5 within a cell), so a single substep carries a
-    drift of several cells evaluated at its start point: the interface estimates are biased
-    near the rings, and a few cells there come out much worse than in the single-domain mesh
-    although the mean ratio stays at 1.  Sixteen substeps remove most of that bias."""
-    r = _five_ring(px, substeps)
-    assert 0.97 <= r["R_mean"] <= 1.03
-    if substeps >= 16:   # the paper's R_max = R_mean = 1 (two digits; R_max read as max Q_SD / max Q_SDD)
-        assert 0.99 <= r["R_mean"] <= 1.01
-        assert 0.98 <= r["maxQ_ratio"] <= 1.02
-        assert r["R_max"] <= 1.1
+def test_five_ring_resolved_substeps_quality_ratio(px):
+    """Sixteen Euler-Maruyama substeps per step: the paper's R_max = R_mean = 1 to two digits
+    (R_max read as max Q_SD / max Q_SDD; the largest per-cell ratio stays below 1.1)."""
+    prob = W.five_ring(px).replace(substeps=16)
+    q_sdd, _ = _five_ring_gpu(prob)
+    q_sd = _single_domain_reference(prob)
+    r = ratio_stats(q_sd, q_sdd)
+    print(f"five-ring {px}x{px} K=16: {r} Q_SD max {q_sd.max():.3f} Q_SDD max {q_sdd.max():.3f}")
+    assert q_sd.max() > 1.2  # the mesh adapted: cells concentrate at the rings
+    assert 0.99 <= r["R_mean"] <= 1.01
+    assert 0.98 <= r["maxQ_ratio"] <= 1.02
+    assert r["R_max"] <= 1.1
+
+
+@pytest.mark.parametrize("px", [2, 3, 4])
+def test_five_ring_paper_setting_is_the_oracle_trajectory(px):
+    """The paper's own setting, one Euler-Maruyama substep per step (ds = dt), 100 steps.
+
+    The GPU's SDD trajectory is the oracle's SDD trajectory on the same Philox streams: meshes
+    within 1e-6 after steps 1, 10 and 100, and the final quality ratios against the single-domain
+    reference equal to the oracle's (max-Q ratio to 1e-4 relative, mean R to 1e-6).  The mean ratio R stays within 3 % of 1 (the paper's
+    R_mean = 1); the max-Q ratio does not reach the paper's 1 in either implementation.  Cause
+    (the method at this resolution, not the kernel): with one substep an interface estimate is
+    the explicit drift step xi + (grad omega / omega) dt, which moves nodes at the rings by up
+    to 1.5 cells while dt |d b / d xi| = 1.2, so neighbouring interface nodes overshoot the
+    implicit single-domain solution by up to 0.7 cell and a few cells fold (tested on the
+    oracle alone in test_oracle_quality.py)."""
+    from oracle import step as ostep
+    prob = W.five_ring(px)
+    keep = (1, 10, 100)
+    q_sdd, kept = _five_ring_gpu(prob, keep)
+    x, y = W.identity_mesh(prob)
+    for n in range(prob.steps):
+        r = ostep.step(prob, x, y, prob.t0 + n * prob.dt, n)
+        x, y = r["x"], r["y"]
+        if n + 1 in keep:
+            gx, gy = kept[n + 1]
+            assert max(np.abs(gx - x).max(), np.abs(gy - y).max()) <= 1e-6
+    q_oracle = cell_quality(x, y)
+    q_sd = _single_domain_reference(prob)
+    r_gpu = ratio_stats(q_sd, q_sdd)
+    r_or = ratio_stats(q_sd, q_oracle)
+    print(f"five-ring {px}x{px} K=1: gpu {r_gpu} oracle {r_or}")
+    # the worst cells are nearly folded (Q up to ~1e2..1e4), so Q amplifies the meshes' 1e-8
+    # differences: the ratios agree to 1e-4 relative
+    assert abs(r_gpu["maxQ_ratio"] - r_or["maxQ_ratio"]) <= 1e-4 * r_or["maxQ_ratio"]
+    assert abs(r_gpu["R_mean"] - r_or["R_mean"]) <= 1e-6
+    assert 0.97 <= r_gpu["R_mean"] <= 1.03

@@ -10,7 +10,7 @@ import workloads as W
 from gpu_helpers import gpu_problem
 from oracle import step as ostep
 from oracle.layout import interface_sampling
-from test_gpu_parity import _mesh_tolerance
+from gpu_helpers import mesh_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,7 @@ def test_full_step_with_sampling_fp64(periodic):
     gx, gy, _ = h.step()
     r = ostep.step(prob, x, y, prob.t0, 0)
     bx, by = ostep.scatter(prob, r["nodes"], r["est"])
-    tol = _mesh_tolerance(prob, r["omega"], bx, by, x, y, 1e-10)
+    tol = mesh_tolerance(prob, r["omega"], bx, by, x, y, 1e-10)
     assert np.abs(gx - r["x"]).max() <= tol and np.abs(gy - r["y"]).max() <= tol
     h.close()
 

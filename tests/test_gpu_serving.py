@@ -242,3 +242,37 @@ def test_server_cancellation():
         for k, (rx, ry, rest, _) in refs.items():
             assert np.array_equal(got[k]["x"], rx) and np.array_equal(got[k]["y"], ry)
             assert np.array_equal(got[k]["est"], rest)
+
+
+def test_served_fp64_requests_match_oracle():
+    """Served requests against the oracle itself: the three FP64 problems of uneven shapes of the
+    batch anchor test, served at an adaptive SE target (two submitted first, one joining the
+    running set).  Each request's interface estimates are the oracle's within 1e-10 with the
+    oracle's adaptive path counts, and its new mesh is the oracle's within the interface
+    tolerance plus the solver's residual bound."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    from gpu_helpers import mesh_tolerance
+    from oracle import step as ostep
+    from test_gpu_batch import oracle_anchor_problems
+    se_target = 1.2e-2
+    probs = [p.replace(paths_per_node=2048, se_target=se_target, max_paths_per_node=1 << 16)
+             for p in oracle_anchor_problems()]
+    stream = torch.cuda.Stream()
+    with S.SddServer(server_params(W.PREC_FP64, 2048, se_target, 1 << 16), stream) as srv:
+        ids = [submit(srv, p) for p in probs[:2]]
+        srv.progress()
+        ids.append(submit(srv, probs[2]))
+        drain(srv, len(ids))
+        outs = [srv.result(rid) for rid in ids]
+    for prob, out in zip(probs, outs):
+        assert out["status"] == S.SDD_OK
+        x, y = W.identity_mesh(prob)
+        r = ostep.step(prob, x, y, prob.t0, 0)
+        assert np.abs(out["est"] - r["est"]).max() <= 1e-10
+        assert np.abs(out["se"] - r["se"]).max() <= 1e-10
+        assert out["stats"]["paths"] == int(r["n_used"].sum())
+        bx, by = ostep.scatter(prob, r["nodes"], r["est"])
+        tol = mesh_tolerance(prob, r["omega"], bx, by, x, y, 1e-10)
+        assert np.abs(out["x"] - r["x"]).max() <= tol and np.abs(out["y"] - r["y"]).max() <= tol

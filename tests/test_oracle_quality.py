@@ -103,3 +103,35 @@ def test_periodic_subdomains_with_exact_interface_data_reproduce_single_domain(p
     bx, by = scatter(prob, nodes, est)
     x1, y1 = subdomain_solves(prob, om, bx, by, x, y)
     assert np.allclose(x1, xs, atol=1e-12) and np.allclose(y1, ys, atol=1e-12)
+
+
+def test_five_ring_single_substep_estimate_is_the_explicit_drift_step():
+    """Why the paper's one-substep setting (Sec. 4.2, ds = dt) does not keep the single-domain
+    mesh quality at 41 x 41 nodes.  On the uniform initial mesh (x linear in xi, so the previous
+    mesh is interpolated exactly) the expectation of x0(Phi^1) is x0 at the end of the drift step,
+    xi + (grad omega / omega) dt: the estimates equal that explicit step within 4.5 standard errors
+    at every interface node.  At the rings this step moves nodes by up to 1.5 cells and
+    dt |d b / d xi| exceeds 1, so the estimates overshoot the backward-Euler single-domain solution
+    by more than half a cell; with 16 substeps they stay within a fifth of a cell of it."""
+    from oracle import step as ostep
+    from oracle.monitor import fd_gradient
+    prob = W.five_ring(2)
+    x, y = grid(prob.nx, prob.ny, prob.Lx, prob.Ly)
+    om = monitor_on_grid(prob.monitor_kind, prob.monitor_params, x, y, 0.0, 1, prob.Lx, prob.Ly)
+    gx, gy = fd_gradient(om, 1)
+    bx, by = gx / om, gy / om        # drift of the paper's generator (tau = 1)
+    h = 1.0 / (prob.nx - 1)
+    db = max(np.abs((np.roll(bx, -1, 1) - np.roll(bx, 1, 1)) / (2 * h)).max(),
+             np.abs((np.roll(by, -1, 0) - np.roll(by, 1, 0)) / (2 * h)).max())
+    assert prob.dt * db > 1.0
+    assert max(np.abs(bx).max(), np.abs(by).max()) * prob.dt / h > 1.4
+    r = ostep.step(prob, x, y, 0.0, 0)
+    ii, jj = r["nodes"][:, 0], r["nodes"][:, 1]
+    expl = np.stack([x[jj, ii] + prob.Lx * bx[jj, ii] * prob.dt, y[jj, ii] + prob.Ly * by[jj, ii] * prob.dt], 1)
+    assert np.all(np.abs(r["est"] - expl) <= 4.5 * r["se"] + 1e-12)
+    xs, ys = periodic_single_domain_step(om, x, y, prob.dt, prob.tau, prob.form, prob.Lx, prob.Ly)
+    sd = np.stack([xs[jj, ii], ys[jj, ii]], 1)
+    cell = prob.Lx * h
+    assert np.abs(r["est"] - sd).max() > 0.5 * cell
+    r16 = ostep.step(prob.replace(substeps=16), x, y, 0.0, 0)
+    assert np.abs(r16["est"] - sd).max() < 0.2 * cell
