@@ -41,14 +41,14 @@ OPS_PER_PATH_STEP = 158
 # Issued warp instructions per path-step of the current FP32 path kernel on the benchmarked
 # configuration (ncu, smsp__inst_executed.sum / path-steps on a full 2^19-path round); the
 # issue fraction below divides by 4 warp instructions per clock per SM.
-WARP_INST_PER_PATH_STEP = 11.02
+WARP_INST_PER_PATH_STEP = 10.52
 LANES_PER_SM_CLK, ISSUE_PER_SM_CLK, SM_MAX_MHZ = 128, 4, 2070.0
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one path-kernel launch on this grid, from an ncu
 # capture of the current kernel on a full round (2^19 paths per node): the cold fill of the packed
 # monitor and mesh records (~1.6 MB of FP32 data per 257x257 grid), which does not grow with the
 # number of paths.
-MC_TRAFFIC_BYTES_PER_LAUNCH = 1.64e6
+MC_TRAFFIC_BYTES_PER_LAUNCH = 1.66e6
 
 
 def parse():
@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--tau", type=float, default=1e-2)
     ap.add_argument("--iface-stride", type=int, default=0,
                     help="Monte Carlo at every k-th interface node, the rest interpolated (0: all)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default path-kernel launch configuration instead of running the autotuner "
+                         "(sdd_tune / sdd_batch_tune_mc) before the warm-up steps")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -365,9 +368,17 @@ def run_ours(args):
     x0, y0 = W.identity_mesh(prob)
     stream = torch.cuda.current_stream()
 
+    tuned = {}
+
     def fresh_problem():
         h = S.SddProblem(S.params_from(prob), x0, y0, stream=stream)
         h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
+        # launch configuration: tuned once on the first problem's first round (outside any timed
+        # region), then given to every later problem so both timed runs do the same work
+        if not args.no_tune and not tuned:
+            tuned.update(h.tune_mc(True))
+        elif tuned:
+            h.set_mc_config(blocks_per_sm=tuned["blocks_per_sm"], paths_per_task=tuned["paths_per_task"])
         for _ in range(args.warmup):
             S.sdd_step(h.h)
         torch.cuda.synchronize()
@@ -465,7 +476,9 @@ def run_ours(args):
                                   "frac": WARP_INST_PER_PATH_STEP * ps_rate / (sms * ISSUE_PER_SM_CLK * mhz * 1e6),
                                   "basis": "issued warp instructions (ncu count of this kernel) over "
                                            "4 per clock per SM: the instruction-level fraction"}},
-           "clocks": clocks, "e2e": e2e}
+           "clocks": clocks, "e2e": e2e,
+           "launch_config": tuned or {"threads_per_block": 256, "paths_per_task": 2048,
+                                      "blocks_per_sm": "register limit", "tuned": False}}
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds)
         # part of the oracle leg: the GPU's first-step estimates against the FP64 oracle's
@@ -540,7 +553,9 @@ def run_mix(args):
     hs = make(prec)
     M = sum(h.M for h in hs)
     b = S.SddBatch(hs, stream=stream, use_graph=True)
-    tpb = b.tune(0)  # path-kernel block size timed on the first round (results do not depend on it)
+    # launch configuration timed on the first round: block size and blocks per SM change no
+    # result; the task size changes the grouping of the sums (and is set on every problem)
+    cfg = b.mc_config() if args.no_tune else b.tune_mc(True)
     for _ in range(args.warmup):
         b.step()
     stream.synchronize()
@@ -566,10 +581,10 @@ def run_mix(args):
     solve_gbs = solve_bytes / (solve_ms / 1e3) / 1e9 if solve_ms > 0 else None
     batch = {"s_per_step": T / args.steps, "interface_node_estimates_per_s": M * args.steps / T,
              "path_steps_last_step": st["path_steps"], "launches_per_step": (st["kernel_launches"] - l0) / args.steps,
-             "path_kernel_threads_per_block": tpb,
+             "launch_config": cfg,
              "solve_iters_max": st["solve_iters_max"], "solve_outer_max": st["solve_outer_max"],
              "solve_rel_residual": st["solve_rel_residual"],
-             "solve_roofline": {"bound": "hbm", "kernel": "solve_batch_kernel", "ms": solve_ms,
+             "solve_roofline": {"bound": "hbm", "kernel": "solve_batch_items_kernel (clusters of 2 CTAs for subdomains of >= 32768 unknowns) or solve_batch_kernel", "ms": solve_ms,
                                 "unknowns": U, "algorithmic_bytes": solve_bytes, "achieved": solve_gbs,
                                 "peak": peak, "unit": "GB/s", "peak_basis": basis,
                                 "frac": solve_gbs / peak if solve_gbs else None}}
@@ -701,16 +716,27 @@ def run_serve(args):
         # FP64 sums at the same standard-error target
         torch.cuda.synchronize()
         t = time.perf_counter()
+        ps64, nodes64 = 0, 0
         for k in range(kb):
             q = reqs[k].replace(precision=W.PREC_FP64)
             x, y = meshes[k]
             with S.SddProblem(S.params_from(q), x, y) as h:
                 h.set_monitor_analytic(q.monitor_kind, q.monitor_params)
                 h.step()
+                st = h.stats()
+                ps64 += st["path_steps"]
+                nodes64 += st["M"]
         torch.cuda.synchronize()
-        ts = (time.perf_counter() - t) / kb
+        t64 = time.perf_counter() - t
+        ts = t64 / kb
         out["sequential_fp64"] = {"requests": kb, "s_per_request": ts, "requests_per_s": 1.0 / ts,
-                                  "served_speedup": (n / T) * ts}
+                                  "interface_node_estimates_per_s": nodes64 / t64,
+                                  "path_steps_per_s": ps64 / t64,
+                                  "served_speedup": (n / T) * ts,
+                                  "served_speedup_estimates": (nodes / T) / (nodes64 / t64),
+                                  "basis": "the first requests of the draw stepped one at a time with FP64 paths and "
+                                           "sums at the same SE target; served_speedup compares requests/s, "
+                                           "served_speedup_estimates interface-node estimates/s (size-independent)"}
     print(json.dumps(out))
     return 0
 

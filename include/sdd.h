@@ -204,6 +204,46 @@ sdd_status sdd_step_mkp(sdd_problem* p, int32_t K, double* x_out, double* y_out)
 /* Counters of the last calls (see sdd_stats). */
 sdd_status sdd_get_stats(const sdd_problem* p, sdd_stats* out);
 
+/* ---- Launch configuration of the path kernel (Sec. 3.4's N paths per node) -----------------
+ * The path kernel is a persistent grid of blocks_per_sm x SMs blocks of threads_per_block
+ * threads; each warp takes tasks of paths_per_task consecutive paths of one node, and a
+ * Monte Carlo round gives a node at most 256 tasks (256 x paths_per_task paths).
+ *   threads_per_block : 128, 256 or 512 for batches (sdd_batch_set_mc_config); 256 for a
+ *                       single problem.
+ *   blocks_per_sm     : 1 .. max_blocks_per_sm, the register limit of the kernel (read-only
+ *                       field, filled by the get calls; ignored by the set calls).
+ *   paths_per_task    : 1024, 2048 (the default) or 4096.
+ * What does and does not change results: threads_per_block and blocks_per_sm never do (every
+ * warp runs whole tasks of fixed paths, and the sums are reduced task by task in a fixed order).
+ * paths_per_task groups a node's paths differently for the estimator sums (per lane, per task,
+ * per round): FP64 estimates then differ in the last bits (about 1e-16 relative per sum), and in
+ * the adaptive mode a node whose SE lies within that of the target may take another chunk.  A
+ * batch uses one paths_per_task for all its problems, so a batched problem gives bitwise the
+ * results of stepping it alone with the same paths_per_task.  The configuration is not part of
+ * a checkpoint (sdd_save). */
+typedef struct {
+    int32_t threads_per_block;
+    int32_t blocks_per_sm;
+    int32_t paths_per_task;
+    int32_t max_blocks_per_sm;
+} sdd_mc_config;
+
+/* The problem's current configuration. */
+sdd_status sdd_get_mc_config(const sdd_problem* p, sdd_mc_config* out);
+
+/* Set the configuration (0 in a field keeps its current value; blocks_per_sm 0 = the maximum).
+ * SDD_ERR_INVALID_ARG for values outside the lists above. */
+sdd_status sdd_set_mc_config(sdd_problem* p, const sdd_mc_config* cfg);
+
+/* Autotuner: prepares the next step's first Monte Carlo round (monitor, initial chunk, plan),
+ * times one path-kernel launch of that round (the faster of two) at every blocks_per_sm from 1
+ * to the maximum and, with tune_paths_per_task = 1, at paths_per_task 1024, 2048 and 4096
+ * (otherwise at the current one), keeps the configuration with the least time per path, and
+ * writes it to *chosen (nullable).  The launches write only scratch task slots: no state of the
+ * problem changes (the next step prepares, initialises and plans again).  Waits for the
+ * problem's stream. */
+sdd_status sdd_tune(sdd_problem* p, int32_t tune_paths_per_task, sdd_mc_config* chosen);
+
 /* Interface nodes of the problem: ij (M x 2 int32 (i, j), nullable) and *M. */
 sdd_status sdd_get_interface_nodes(const sdd_problem* p, int32_t* ij, int32_t* M);
 
@@ -305,6 +345,18 @@ sdd_status sdd_batch_tune(sdd_batch* b, int32_t threads_per_block, int32_t* chos
  * Waits for the batch's stream.  Returns SDD_ERR_INVALID_ARG (counters still written) when a
  * problem's monitor was not finite and > 0 at every node or its mesh not finite in that step. */
 sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out);
+
+/* Launch configuration of the batch's path kernel (sdd_mc_config).  Setting paths_per_task
+ * sets it on every problem of the batch as well; a recorded CUDA graph is recorded again at the
+ * next step. */
+sdd_status sdd_batch_get_mc_config(sdd_batch* b, sdd_mc_config* out);
+sdd_status sdd_batch_set_mc_config(sdd_batch* b, const sdd_mc_config* cfg);
+
+/* Autotuner of a batch: as sdd_tune, over threads_per_block 128, 256 and 512, every
+ * blocks_per_sm their register limits allow and, with tune_paths_per_task = 1, paths_per_task
+ * 1024, 2048 and 4096; the chosen paths_per_task goes to every problem.  Waits for the batch's
+ * and the problems' streams.  (sdd_batch_tune tunes threads_per_block alone.) */
+sdd_status sdd_batch_tune_mc(sdd_batch* b, int32_t tune_paths_per_task, sdd_mc_config* chosen);
 
 /* Release the batch (not its problems). */
 void sdd_batch_destroy(sdd_batch* b);

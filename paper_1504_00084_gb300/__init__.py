@@ -58,6 +58,14 @@ class SddStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class SddMcConfig(ctypes.Structure):
+    _fields_ = [("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("paths_per_task", ctypes.c_int32), ("max_blocks_per_sm", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SddServerParams(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_resident", ctypes.c_int32),
                 ("max_nodes", ctypes.c_int64), ("mem_budget_bytes", ctypes.c_int64),
@@ -89,7 +97,8 @@ EXPORTS = [
     "sdd_server_create", "sdd_server_submit", "sdd_server_progress", "sdd_server_poll",
     "sdd_server_result", "sdd_server_get_stats", "sdd_server_destroy",
     "sdd_save", "sdd_load", "sdd_interface_sampling", "sdd_step_mkp", "sdd_server_cancel",
-    "sdd_debug_bounds_violations",
+    "sdd_debug_bounds_violations", "sdd_get_mc_config", "sdd_set_mc_config", "sdd_tune",
+    "sdd_batch_get_mc_config", "sdd_batch_set_mc_config", "sdd_batch_tune_mc",
 ]
 
 
@@ -123,6 +132,12 @@ def _load():
         "sdd_batch_step": ([P], I32),
         "sdd_batch_tune": ([P, I32, ctypes.POINTER(I32)], I32),
         "sdd_batch_get_stats": ([P, ctypes.POINTER(SddStats)], I32),
+        "sdd_get_mc_config": ([P, ctypes.POINTER(SddMcConfig)], I32),
+        "sdd_set_mc_config": ([P, ctypes.POINTER(SddMcConfig)], I32),
+        "sdd_tune": ([P, I32, ctypes.POINTER(SddMcConfig)], I32),
+        "sdd_batch_get_mc_config": ([P, ctypes.POINTER(SddMcConfig)], I32),
+        "sdd_batch_set_mc_config": ([P, ctypes.POINTER(SddMcConfig)], I32),
+        "sdd_batch_tune_mc": ([P, I32, ctypes.POINTER(SddMcConfig)], I32),
         "sdd_batch_destroy": ([P], None),
         "sdd_mesh_quality": ([P, P, ctypes.POINTER(F64), ctypes.POINTER(F64)], I32),
         "sdd_server_create": ([ctypes.POINTER(SddServerParams), P, ctypes.POINTER(P)], I32),
@@ -431,6 +446,57 @@ class SddProblem:
     def debug_paths(self, node, p_begin, n_paths):
         return sdd_debug_paths(self.h, node, p_begin, n_paths)
 
+    def mc_config(self):
+        return sdd_get_mc_config(self.h)
+
+    def set_mc_config(self, threads_per_block=0, blocks_per_sm=0, paths_per_task=0):
+        sdd_set_mc_config(self.h, threads_per_block, blocks_per_sm, paths_per_task)
+
+    def tune_mc(self, tune_paths_per_task=True):
+        """Time the next step's first path-kernel round over the launch configurations and keep the
+        fastest (sdd_tune); returns the chosen configuration."""
+        return sdd_tune(self.h, tune_paths_per_task)
+
+
+def _mc_config(threads_per_block=0, blocks_per_sm=0, paths_per_task=0) -> SddMcConfig:
+    c = SddMcConfig()
+    c.threads_per_block, c.blocks_per_sm, c.paths_per_task = threads_per_block, blocks_per_sm, paths_per_task
+    return c
+
+
+def sdd_get_mc_config(h: int) -> dict:
+    c = SddMcConfig()
+    _check(lib.sdd_get_mc_config(h, ctypes.byref(c)), "sdd_get_mc_config")
+    return c.as_dict()
+
+
+def sdd_set_mc_config(h: int, threads_per_block=0, blocks_per_sm=0, paths_per_task=0) -> None:
+    c = _mc_config(threads_per_block, blocks_per_sm, paths_per_task)
+    _check(lib.sdd_set_mc_config(h, ctypes.byref(c)), "sdd_set_mc_config")
+
+
+def sdd_tune(h: int, tune_paths_per_task: bool = True) -> dict:
+    c = SddMcConfig()
+    _check(lib.sdd_tune(h, 1 if tune_paths_per_task else 0, ctypes.byref(c)), "sdd_tune")
+    return c.as_dict()
+
+
+def sdd_batch_get_mc_config(b: int) -> dict:
+    c = SddMcConfig()
+    _check(lib.sdd_batch_get_mc_config(b, ctypes.byref(c)), "sdd_batch_get_mc_config")
+    return c.as_dict()
+
+
+def sdd_batch_set_mc_config(b: int, threads_per_block=0, blocks_per_sm=0, paths_per_task=0) -> None:
+    c = _mc_config(threads_per_block, blocks_per_sm, paths_per_task)
+    _check(lib.sdd_batch_set_mc_config(b, ctypes.byref(c)), "sdd_batch_set_mc_config")
+
+
+def sdd_batch_tune_mc(b: int, tune_paths_per_task: bool = True) -> dict:
+    c = SddMcConfig()
+    _check(lib.sdd_batch_tune_mc(b, 1 if tune_paths_per_task else 0, ctypes.byref(c)), "sdd_batch_tune_mc")
+    return c.as_dict()
+
 
 def sdd_batch_create(problems, stream=None, use_graph=False) -> int:
     handles = [p.h if isinstance(p, SddProblem) else p for p in problems]
@@ -477,6 +543,15 @@ class SddBatch:
 
     def stats(self):
         return sdd_batch_get_stats(self.h)
+
+    def mc_config(self):
+        return sdd_batch_get_mc_config(self.h)
+
+    def set_mc_config(self, threads_per_block=0, blocks_per_sm=0, paths_per_task=0):
+        sdd_batch_set_mc_config(self.h, threads_per_block, blocks_per_sm, paths_per_task)
+
+    def tune_mc(self, tune_paths_per_task=True):
+        return sdd_batch_tune_mc(self.h, tune_paths_per_task)
 
     def close(self):
         if self.h:

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "sdd.h"
@@ -48,8 +49,7 @@ namespace {
         if (s_ != SDD_OK) return s_;           \
     } while (0)
 
-constexpr int64_t kMaxChunk = int64_t(1) << 19;  // paths per node per launch (see plan kernel)
-constexpr int kSlotsPerNode = (int)(kMaxChunk / kPathsPerTask);
+constexpr int kSlotsPerNode = kTasksPerRound;  // task slots per node: one round's tasks
 constexpr int64_t kMaxNodes = int64_t(1) << 23;  // kMaxNodes * kSlotsPerNode tasks fit in an int
 constexpr int kMaxAdaptiveRounds = 4096;
 const char kCkptMagic[8] = {'S', 'D', 'D', 'C', 'K', 'P', 'T', '1'};
@@ -260,6 +260,7 @@ McParams<T> mc_params(const sdd_problem* p)
     P.node_of = p->node_of; P.p_begin = p->p_begin; P.p_count = p->p_count;
     P.task_off = p->task_off; P.n_active = p->n_active; P.task_counter = p->task_counter;
     P.slots = p->slots;
+    P.task_paths = p->task_paths;
     return P;
 }
 
@@ -321,6 +322,7 @@ sdd_status run_mc(sdd_problem* p)
     PP.M = M; PP.n_done = p->n_done; PP.next_total = p->next_total; PP.node_of = p->node_of;
     PP.p_begin = p->p_begin; PP.p_count = p->p_count; PP.task_off = p->task_off;
     PP.n_active = p->n_active; PP.task_counter = p->task_counter;
+    PP.task_paths = p->task_paths;
     ReduceParams RP{};
     RP.node_of = p->node_of; RP.p_count = p->p_count; RP.task_off = p->task_off;
     RP.n_active = p->n_active; RP.slots = p->slots; RP.shift = p->shift; RP.acc = p->acc;
@@ -329,7 +331,8 @@ sdd_status run_mc(sdd_problem* p)
     RP.max_paths = maxp;
     if (!adaptive) {
         // fixed N: the number of launches is known, no host round trip
-        const int64_t rounds = (n0 + kMaxChunk - 1) / kMaxChunk;
+        const int64_t chunk = (int64_t)kTasksPerRound * p->task_paths;
+        const int64_t rounds = (n0 + chunk - 1) / chunk;
         for (int64_t r = 0; r < rounds; ++r) {
             SDD_CK(launch_plan(PP, p->stream));
             SDD_TRY(timed_mc_round(p, n_timed++));
@@ -414,7 +417,10 @@ sdd_status run_solve(sdd_problem* p)
     if (!p->solve_ev[0]) SDD_CK(cudaEventCreate(&p->solve_ev[0]));
     if (!p->solve_ev[1]) SDD_CK(cudaEventCreate(&p->solve_ev[1]));
     SDD_CK(cudaEventRecord(p->solve_ev[0], p->stream));
-    SDD_CK(launch_solve(S, p->fp64, p->stream));
+    if (!p->h_items.empty())
+        SDD_CK(launch_solve_items(S, p->solve_items, (int)p->h_items.size(), p->fp64, p->stream));
+    else
+        SDD_CK(launch_solve(S, p->fp64, p->stream));
     SDD_CK(cudaEventRecord(p->solve_ev[1], p->stream));
     p->launches += 2;
     const int ns = p->prm.px * p->prm.py;
@@ -483,6 +489,7 @@ void problem_arrays(sdd_problem* p, bool with_mc, F&& f)
     f((void**)&p->quality, (N + 2) * 8);
     f((void**)&p->mg, p->mg_stride * ns);
     f((void**)&p->bad, 16);
+    f((void**)&p->solve_items, (p->h_items.size() + 1) * sizeof(SolveItem));
     const size_t nb = 2 * (size_t)q.nx + 2 * (size_t)q.ny;
     f((void**)&p->bnd64, nb * 8);
     f((void**)&p->bnd, nb * rs);
@@ -513,6 +520,17 @@ sdd_problem* problem_shell(const sdd_params& prm, cudaStream_t stream)
             if (m > mg) mg = m;
         }
     p->mg_stride = mg;
+    // subdomains by interior size, largest first; large ones are solved by a cluster of CTAs
+    std::vector<std::pair<int64_t, int2>> subs;
+    for (int k = 0; k < prm.px * prm.py; ++k) {
+        const int I = k % prm.px, J = k / prm.px;
+        const int64_t wi = split_line(I + 1, prm.nx, prm.px) - split_line(I, prm.nx, prm.px) - 1;
+        const int64_t wj = split_line(J + 1, prm.ny, prm.py) - split_line(J, prm.ny, prm.py) - 1;
+        subs.push_back({wi * wj, make_int2(0, k)});
+    }
+    std::stable_sort(subs.begin(), subs.end(), [](const std::pair<int64_t, int2>& a,
+                                                  const std::pair<int64_t, int2>& c) { return a.first > c.first; });
+    if (prm.subdomain_scheme == 0) p->h_items = solve_items(subs);
     p->stats.M = p->M;
     p->stats.t = prm.t0;
     return p;
@@ -566,6 +584,9 @@ sdd_status sdd_alloc_problem(const sdd_params& prm, cudaStream_t stream, bool wi
     if (e == cudaSuccess && p->n_interp > 0)
         e = cudaMemcpyAsync(p->interp, p->h_interp.data(), (size_t)p->n_interp * sizeof(InterpRule),
                             cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess && !p->h_items.empty())
+        e = cudaMemcpyAsync(p->solve_items, p->h_items.data(), p->h_items.size() * sizeof(SolveItem),
+                            cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // p->ij is pageable host memory
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -578,6 +599,9 @@ sdd_status sdd_alloc_problem(const sdd_params& prm, cudaStream_t stream, bool wi
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int per_sm = p->fp64 ? mc_max_blocks_per_sm<double>(p->acc_mode, false, false)
                                : mc_max_blocks_per_sm<float>(p->acc_mode, false, false);
+    p->nsm = nsm;
+    p->mc_max_blocks_per_sm = per_sm;
+    p->mc_blocks_per_sm = per_sm;
     p->mc_grid = nsm * per_sm;
     *out = p;
     return SDD_OK;
@@ -887,6 +911,104 @@ sdd_status sdd_get_stats(const sdd_problem* p, sdd_stats* out)
     return SDD_OK;
 }
 
+sdd_status sdd_get_mc_config(const sdd_problem* p, sdd_mc_config* out)
+{
+    if (!p || !out) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    out->threads_per_block = 256;
+    out->blocks_per_sm = p->mc_blocks_per_sm;
+    out->paths_per_task = p->task_paths;
+    out->max_blocks_per_sm = p->mc_max_blocks_per_sm;
+    return SDD_OK;
+}
+
+sdd_status sdd_set_mc_config(sdd_problem* p, const sdd_mc_config* c)
+{
+    if (!p || !c) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    if (c->threads_per_block != 0 && c->threads_per_block != 256)
+        return fail(SDD_ERR_INVALID_ARG, "a single problem's path kernel runs 256 threads per block");
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > p->mc_max_blocks_per_sm)
+        return fail(SDD_ERR_INVALID_ARG, "blocks_per_sm must be in [0, max_blocks_per_sm]");
+    if (c->paths_per_task != 0 && !sdd_valid_task_paths(c->paths_per_task))
+        return fail(SDD_ERR_INVALID_ARG, "paths_per_task must be 1024, 2048 or 4096");
+    if (c->paths_per_task) p->task_paths = c->paths_per_task;
+    p->mc_blocks_per_sm = c->blocks_per_sm ? c->blocks_per_sm : p->mc_max_blocks_per_sm;
+    p->mc_grid = p->nsm * p->mc_blocks_per_sm;
+    return SDD_OK;
+}
+
+sdd_status sdd_tune(sdd_problem* p, int32_t tune_paths_per_task, sdd_mc_config* chosen)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    if (tune_paths_per_task != 0 && tune_paths_per_task != 1)
+        return fail(SDD_ERR_INVALID_ARG, "tune_paths_per_task must be 0 or 1");
+    const TraceRange trace("sdd_tune");
+    SDD_CK(cudaStreamSynchronize(p->stream));
+    if (p->M > 0) {
+        SDD_TRY(run_prep(p));
+        const int64_t n0 = p->prm.paths_per_node;
+        const int64_t maxp = p->prm.se_target > 0 ? p->prm.max_paths_per_node : n0;
+        SDD_CK(launch_mc_init(p->M, n0, maxp, p->acc, p->n_done, p->steps, p->paths_run, p->next_total,
+                              p->stream, p->n_interp > 0 ? p->iface_role : nullptr));
+        p->launches += 1;
+        PlanParams PP{};
+        PP.M = p->M; PP.n_done = p->n_done; PP.next_total = p->next_total; PP.node_of = p->node_of;
+        PP.p_begin = p->p_begin; PP.p_count = p->p_count; PP.task_off = p->task_off;
+        PP.n_active = p->n_active; PP.task_counter = p->task_counter;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        SDD_CK(cudaEventCreate(&e0));
+        cudaError_t ce = cudaEventCreate(&e1);
+        const int tps[3] = {1024, 2048, 4096};
+        const int nt = tune_paths_per_task ? 3 : 1;
+        double best = -1.0;
+        int best_t = p->task_paths, best_b = p->mc_blocks_per_sm;
+        for (int a = 0; a < nt && ce == cudaSuccess; ++a) {
+            const int T = tune_paths_per_task ? tps[a] : p->task_paths;
+            // paths of the round at this task size (a round gives a node at most 256 tasks)
+            const int64_t round = n0 < (int64_t)kTasksPerRound * T ? n0 : (int64_t)kTasksPerRound * T;
+            PP.task_paths = T;
+            for (int bps = 1; bps <= p->mc_max_blocks_per_sm && ce == cudaSuccess; ++bps) {
+                float ms_min = 0.f;
+                for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {
+                    ce = launch_plan(PP, p->stream);
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e0, p->stream);
+                    if (ce != cudaSuccess) break;
+                    if (p->fp64) {
+                        McParams<double> P = mc_params<double>(p);
+                        P.task_paths = T;
+                        ce = launch_mc<double>(P, p->acc_mode, false, false, p->nsm * bps, p->stream);
+                    } else {
+                        McParams<float> P = mc_params<float>(p);
+                        P.task_paths = T;
+                        ce = launch_mc<float>(P, p->acc_mode, false, false, p->nsm * bps, p->stream);
+                    }
+                    if (ce == cudaSuccess) ce = cudaEventRecord(e1, p->stream);
+                    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                    if (ce == cudaSuccess && (rep == 0 || ms < ms_min)) ms_min = ms;
+                    p->launches += 2;
+                }
+                const double per_path = (double)ms_min / (double)round;
+                if (ce == cudaSuccess && (best < 0 || per_path < best)) {
+                    best = per_path;
+                    best_t = T;
+                    best_b = bps;
+                }
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(SDD_ERR_CUDA, cudaGetErrorString(ce));
+        }
+        p->task_paths = best_t;
+        p->mc_blocks_per_sm = best_b;
+        p->mc_grid = p->nsm * best_b;
+    }
+    return chosen ? sdd_get_mc_config(p, chosen) : SDD_OK;
+}
+
 sdd_status sdd_get_interface_nodes(const sdd_problem* p, int32_t* ij, int32_t* M)
 {
     if (!p || !M) return fail(SDD_ERR_INVALID_ARG, "NULL argument");
@@ -996,7 +1118,7 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
     if (node < 0 || node >= p->M) return fail(SDD_ERR_INVALID_ARG, "node out of range");
     if (n_paths < 1 || p_begin < 0 || p_begin + n_paths > ((int64_t)1 << 32))
         return fail(SDD_ERR_INVALID_ARG, "path range out of [0, 2^32)");
-    const int64_t tasks = (n_paths + kPathsPerTask - 1) / kPathsPerTask;
+    const int64_t tasks = (n_paths + p->task_paths - 1) / p->task_paths;
     if (tasks > p->slot_cap) return fail(SDD_ERR_INVALID_ARG, "too many paths for one debug call");
     SDD_TRY(run_prep(p));
     double* dval = nullptr;

@@ -30,8 +30,7 @@ using namespace sdd;
 
 namespace {
 
-constexpr int64_t kMaxChunk = int64_t(1) << 19;           // paths per node per round (plan kernel)
-constexpr int kSlotsPerNode = (int)(kMaxChunk / kPathsPerTask);
+constexpr int kSlotsPerNode = kTasksPerRound;  // task slots per node: one round's tasks
 constexpr int kMaxRounds = 4096;
 
 }  // namespace
@@ -48,6 +47,9 @@ struct sdd_batch {
     std::vector<int32_t> node_off, sub_off;
     int mc_grid = 1;
     int tpb = 256;                   // path-kernel threads per block (sdd_batch_tune)
+    int bps = 0;                     // resident path-kernel blocks per SM (0: the register limit)
+    int max_bps = 1;                 // the register limit at tpb
+    int task_paths = kPathsPerTask;  // paths per warp task, shared by every problem
     int nsm = 1;
     // device: concatenated node arrays and round plan
     int32_t* node_prob = nullptr;
@@ -66,6 +68,8 @@ struct sdd_batch {
     double* t_host = nullptr;
     int32_t* sub_off_dev = nullptr;
     int2* order_dev = nullptr;       // solve CTAs: (problem, subdomain), largest subdomains first
+    SolveItem* items_dev = nullptr;  // cooperative solve items (n_items > 0: large subdomains present)
+    int n_items = 0;
     int32_t* h_n_active = nullptr;
     // graph
     cudaGraphExec_t graph = nullptr;
@@ -170,16 +174,20 @@ sdd_status launch_batch_mc(sdd_batch* b)
     P.shift = b->shift;
     P.node_of = b->node_of; P.p_begin = b->p_begin; P.p_count = b->p_count; P.task_off = b->task_off;
     P.n_active = b->n_active; P.task_counter = b->task_counter; P.slots = b->slots;
+    P.task_paths = b->task_paths;
     B_CK(launch_mc<T>(P, b->acc_mode, false, true, b->mc_grid, b->stream, b->tpb));
     return SDD_OK;
 }
 
-// Path-kernel block size and the persistent grid it allows (all resident blocks of every SM).
-void set_block_size(sdd_batch* b, int tpb)
+// Path-kernel block size and the persistent grid: bps resident blocks on every SM (0: all the
+// kernel's registers allow at that block size).
+void set_block_size(sdd_batch* b, int tpb, int bps = 0)
 {
     b->tpb = tpb;
-    b->mc_grid = b->nsm * (b->fp64 ? mc_max_blocks_per_sm<double>(b->acc_mode, false, true, tpb)
-                                   : mc_max_blocks_per_sm<float>(b->acc_mode, false, true, tpb));
+    b->max_bps = b->fp64 ? mc_max_blocks_per_sm<double>(b->acc_mode, false, true, tpb)
+                         : mc_max_blocks_per_sm<float>(b->acc_mode, false, true, tpb);
+    b->bps = bps > 0 && bps < b->max_bps ? bps : 0;
+    b->mc_grid = b->nsm * (b->bps > 0 ? b->bps : b->max_bps);
 }
 
 // The launches of one step.  `capturing`: only fixed-N work (no host round trip).  first_plan:
@@ -225,6 +233,7 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
         PP.M = b->M; PP.n_done = b->n_done; PP.next_total = b->next_total; PP.node_of = b->node_of;
         PP.p_begin = b->p_begin; PP.p_count = b->p_count; PP.task_off = b->task_off;
         PP.n_active = b->n_active; PP.task_counter = b->task_counter;
+        PP.task_paths = b->task_paths;
         ReduceParams RP{};
         RP.node_of = b->node_of; RP.p_count = b->p_count; RP.task_off = b->task_off; RP.n_active = b->n_active;
         RP.slots = b->slots; RP.shift = b->shift; RP.acc = b->acc; RP.n_done = b->n_done; RP.steps = b->steps;
@@ -236,7 +245,8 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
         }
         int32_t rounds = 0;
         if (!adaptive) {
-            const int64_t nr = (n0 + kMaxChunk - 1) / kMaxChunk;
+            const int64_t chunk = (int64_t)kTasksPerRound * b->task_paths;
+            const int64_t nr = (n0 + chunk - 1) / chunk;
             for (int64_t r = 0; r < nr; ++r) {
                 B_CK(launch_plan(PP, b->stream));
                 const sdd_status s = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
@@ -294,8 +304,15 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
         any_fe = any_fe || p->prm.subdomain_scheme == 1;
     }
     B_CK(cudaEventRecord(b->sev0, b->stream));
-    B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream, any_be,
-                            any_fe, b->order_dev));
+    if (b->n_items > 0) {
+        B_CK(launch_solve_batch_items(b->solve_dev, b->items_dev, b->n_items, fp64_inner, b->stream));
+        if (any_fe)
+            B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream,
+                                    false, true, b->order_dev));
+    } else {
+        B_CK(launch_solve_batch(b->solve_dev, b->sub_off_dev, b->n, b->total_subs, fp64_inner, b->stream, any_be,
+                                any_fe, b->order_dev));
+    }
     B_CK(cudaEventRecord(b->sev1, b->stream));
     launches += (any_be ? 1 : 0) + (any_fe ? 1 : 0);
     for (int i = 0; i < b->n; ++i) {
@@ -325,9 +342,10 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     for (int i = 1; i < n; ++i) {
         const sdd_params& r = problems[i]->prm;
         if (r.precision != q.precision || r.se_target != q.se_target || r.paths_per_node != q.paths_per_node ||
-            (q.se_target > 0 && r.max_paths_per_node != q.max_paths_per_node))
+            (q.se_target > 0 && r.max_paths_per_node != q.max_paths_per_node) ||
+            problems[i]->task_paths != problems[0]->task_paths)
             return sdd_fail(SDD_ERR_INVALID_ARG,
-                            "batched problems must share precision, se_target and path counts");
+                            "batched problems must share precision, se_target, path counts and paths_per_task");
         for (int k = 0; k < i; ++k)
             if (problems[k] == problems[i]) return sdd_fail(SDD_ERR_INVALID_ARG, "a problem appears twice");
     }
@@ -344,6 +362,7 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     b->fp64 = q.precision == SDD_FP64;
     b->acc_mode = q.precision == SDD_FP32_KAHAN ? kAccKahan32 : kAcc64;
     b->use_graph = use_graph != 0;
+    b->task_paths = problems[0]->task_paths;
     std::vector<int32_t> node_prob, node_role;
     bool sampled_any = false;
     b->sub_off.push_back(0);
@@ -401,6 +420,17 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
         std::vector<int2> order;
         for (const auto& v : subs) order.push_back(v.second);
         e = cudaMemcpy(b->order_dev, order.data(), sizeof(int2) * order.size(), cudaMemcpyHostToDevice);
+        // backward-Euler subdomains only: forward-Euler problems run in their own kernel
+        std::vector<std::pair<int64_t, int2>> be;
+        for (const auto& v : subs)
+            if (problems[v.second.x]->prm.subdomain_scheme == 0) be.push_back(v);
+        const std::vector<SolveItem> items = solve_items(be);
+        if (e == cudaSuccess && !items.empty()) {
+            e = b->dalloc(&b->items_dev, sizeof(SolveItem) * items.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpy(b->items_dev, items.data(), sizeof(SolveItem) * items.size(), cudaMemcpyHostToDevice);
+            b->n_items = (int)items.size();
+        }
     }
     if (e == cudaSuccess && sampled_any && b->M > 0)
         e = cudaMemcpy(b->node_role, node_role.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
@@ -522,6 +552,126 @@ sdd_status sdd_batch_tune(sdd_batch* b, int32_t threads_per_block, int32_t* chos
     }
     if (chosen) *chosen = b->tpb;
     return SDD_OK;
+}
+
+sdd_status sdd_batch_get_mc_config(sdd_batch* b, sdd_mc_config* out)
+{
+    if (!b || !out) return sdd_fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    out->threads_per_block = b->tpb;
+    out->blocks_per_sm = b->bps > 0 ? b->bps : b->max_bps;
+    out->paths_per_task = b->task_paths;
+    out->max_blocks_per_sm = b->max_bps;
+    return SDD_OK;
+}
+
+namespace {
+
+// Applies a validated configuration (tpb, bps, task size) to the batch and its problems.
+void apply_mc_config(sdd_batch* b, int tpb, int bps, int task_paths)
+{
+    set_block_size(b, tpb, bps);
+    b->task_paths = task_paths;
+    for (sdd_problem* p : b->probs) p->task_paths = task_paths;
+    if (b->graph) {  // recorded with the previous configuration
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+}
+
+}  // namespace
+
+sdd_status sdd_batch_set_mc_config(sdd_batch* b, const sdd_mc_config* c)
+{
+    if (!b || !c) return sdd_fail(SDD_ERR_INVALID_ARG, "NULL argument");
+    const int tpb = c->threads_per_block ? c->threads_per_block : b->tpb;
+    if (tpb != 128 && tpb != 256 && tpb != 512)
+        return sdd_fail(SDD_ERR_INVALID_ARG, "threads_per_block must be 0, 128, 256 or 512");
+    const int max_bps = b->fp64 ? mc_max_blocks_per_sm<double>(b->acc_mode, false, true, tpb)
+                                : mc_max_blocks_per_sm<float>(b->acc_mode, false, true, tpb);
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > max_bps)
+        return sdd_fail(SDD_ERR_INVALID_ARG, "blocks_per_sm must be in [0, the limit at threads_per_block]");
+    if (c->paths_per_task != 0 && !sdd_valid_task_paths(c->paths_per_task))
+        return sdd_fail(SDD_ERR_INVALID_ARG, "paths_per_task must be 1024, 2048 or 4096");
+    for (sdd_problem* p : b->probs) B_CK(cudaStreamSynchronize(p->stream));
+    B_CK(cudaStreamSynchronize(b->stream));
+    apply_mc_config(b, tpb, c->blocks_per_sm, c->paths_per_task ? c->paths_per_task : b->task_paths);
+    return SDD_OK;
+}
+
+sdd_status sdd_batch_tune_mc(sdd_batch* b, int32_t tune_paths_per_task, sdd_mc_config* chosen)
+{
+    if (!b) return sdd_fail(SDD_ERR_INVALID_ARG, "batch is NULL");
+    if (tune_paths_per_task != 0 && tune_paths_per_task != 1)
+        return sdd_fail(SDD_ERR_INVALID_ARG, "tune_paths_per_task must be 0 or 1");
+    const TraceRange trace("sdd_batch_tune_mc");
+    for (sdd_problem* p : b->probs) B_CK(cudaStreamSynchronize(p->stream));
+    B_CK(cudaStreamSynchronize(b->stream));
+    if (b->M > 0) {
+        // the next step's first round, up to its plan (no problem's state changes: the next step
+        // prepares, initialises and plans again); then per candidate a plan at its task size and
+        // one timed path-kernel launch (the faster of two) into the scratch task slots
+        const int tpb0 = b->tpb, bps0 = b->bps, tp0 = b->task_paths;
+        refresh_records(b);
+        sdd_status st = record_step(b, true);
+        const sdd_params& q = b->probs[0]->prm;
+        const int64_t n0 = q.paths_per_node;
+        PlanParams PP{};
+        PP.M = b->M; PP.n_done = b->n_done; PP.next_total = b->next_total; PP.node_of = b->node_of;
+        PP.p_begin = b->p_begin; PP.p_count = b->p_count; PP.task_off = b->task_off;
+        PP.n_active = b->n_active; PP.task_counter = b->task_counter;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        cudaError_t ce = cudaSuccess;
+        if (st == SDD_OK) ce = cudaEventCreate(&e0);
+        if (st == SDD_OK && ce == cudaSuccess) ce = cudaEventCreate(&e1);
+        const int tps[3] = {1024, 2048, 4096}, tpbs[3] = {128, 256, 512};
+        const int nt = tune_paths_per_task ? 3 : 1;
+        double best = -1.0;
+        int best_tpb = tpb0, best_bps = bps0, best_t = tp0;
+        for (int a = 0; a < nt && st == SDD_OK && ce == cudaSuccess; ++a) {
+            const int T = tune_paths_per_task ? tps[a] : tp0;
+            const int64_t round = n0 < (int64_t)kTasksPerRound * T ? n0 : (int64_t)kTasksPerRound * T;
+            PP.task_paths = T;
+            b->task_paths = T;  // read by launch_batch_mc; restored or replaced below
+            for (int k = 0; k < 3 && st == SDD_OK && ce == cudaSuccess; ++k) {
+                set_block_size(b, tpbs[k]);
+                const int max_bps = b->max_bps;
+                for (int bps = 1; bps <= max_bps && st == SDD_OK && ce == cudaSuccess; ++bps) {
+                    set_block_size(b, tpbs[k], bps);
+                    float ms_min = 0.f;
+                    for (int rep = 0; rep < 2 && st == SDD_OK && ce == cudaSuccess; ++rep) {
+                        ce = launch_plan(PP, b->stream);
+                        if (ce == cudaSuccess) ce = cudaEventRecord(e0, b->stream);
+                        if (ce != cudaSuccess) break;
+                        st = b->fp64 ? launch_batch_mc<double>(b) : launch_batch_mc<float>(b);
+                        if (st != SDD_OK) break;
+                        ce = cudaEventRecord(e1, b->stream);
+                        if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+                        float ms = 0.f;
+                        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+                        if (ce == cudaSuccess && (rep == 0 || ms < ms_min)) ms_min = ms;
+                        b->launches += 2;
+                    }
+                    const double per_path = (double)ms_min / (double)round;
+                    if (st == SDD_OK && ce == cudaSuccess && (best < 0 || per_path < best)) {
+                        best = per_path;
+                        best_tpb = tpbs[k];
+                        best_bps = bps;
+                        best_t = T;
+                    }
+                }
+            }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st != SDD_OK || ce != cudaSuccess) {
+            apply_mc_config(b, tpb0, bps0, tp0);
+            if (st != SDD_OK) return st;
+            cudaGetLastError();
+            return sdd_fail(SDD_ERR_CUDA, cudaGetErrorString(ce));
+        }
+        apply_mc_config(b, best_tpb, best_bps, best_t);
+    }
+    return chosen ? sdd_batch_get_mc_config(b, chosen) : SDD_OK;
 }
 
 sdd_status sdd_batch_get_stats(sdd_batch* b, sdd_stats* out)

@@ -16,6 +16,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+#include <vector>
+
 namespace sdd {
 
 // ---------------------------------------------------------------------------------------
@@ -110,8 +113,11 @@ struct alignas(16) TaskSlot {
 
 enum AccMode { kAcc64 = 0, kAccKahan32 = 1 };
 
-// Paths handed to one warp at a time (64 per lane on average).
+// Paths handed to one warp at a time (64 per lane on average): the default task size.  A
+// problem's task size may be 1024, 2048 or 4096 (sdd_set_mc_config); a round then gives a node at
+// most kTasksPerRound tasks, so the task slots per node stay the same.
 constexpr int kPathsPerTask = 2048;
+constexpr int kTasksPerRound = 256;
 constexpr int kRoundsAhead = 2;  // adaptive Monte Carlo rounds queued ahead of the host's decision
 // Adaptive chunk totals are multiples of this many paths.
 constexpr int64_t kAdaptiveGranule = 1024;
@@ -144,6 +150,7 @@ template <typename T> struct McParams {
     const int32_t* n_active;   // device scalar
     int32_t* task_counter;     // dynamic task dispenser (reset by the plan kernel)
     TaskSlot* slots;           // one per task
+    int32_t task_paths;        // paths per task (0: kPathsPerTask)
     // debug records (null unless the debug variant runs; single-problem launches only)
     double* dbg_val;
     int32_t* dbg_steps;
@@ -167,6 +174,8 @@ struct PlanParams {
     const int32_t* range_pre;  // exclusive prefix of the range lengths (n_ranges + 1)
     int n_ranges;
     int64_t max_tasks;         // > 0: cap on the round's tasks (nodes in planning order)
+    int32_t task_paths;        // paths per task (0: kPathsPerTask); a node takes at most
+                               // kTasksPerRound tasks per round
 };
 
 struct ReduceParams {
@@ -239,6 +248,28 @@ __host__ __device__ inline int split_line(int I, int n, int P)
     return (int)(((int64_t)I * (int64_t)(n - 1)) / (int64_t)P);
 }
 
+// Large subdomains are solved by a cluster of kCoopWidth CTAs (sdd_solve.cu): those with at
+// least kCoopUnknowns interior unknowns.
+#ifndef SDD_SOLVE_COOP
+#define SDD_SOLVE_COOP 2
+#endif
+#ifndef SDD_SOLVE_COOP_MIN
+#define SDD_SOLVE_COOP_MIN 32768
+#endif
+constexpr int kCoopWidth = SDD_SOLVE_COOP;
+constexpr int64_t kCoopUnknowns = SDD_SOLVE_COOP_MIN;
+
+// One CTA's work in a cooperative solve launch: subdomain `sub` of problem `prob`, solved by a
+// team of `width` CTAs (kCoopWidth: this CTA's cluster; 1: this CTA alone; 0: idle).
+struct SolveItem {
+    int32_t prob, sub, width, pad;
+};
+
+// Work items of a solve launch over the given subdomains (problem, subdomain, interior unknowns),
+// in the given order: a cooperative subdomain takes a whole cluster; the others are packed
+// kCoopWidth to a cluster.  Empty when no subdomain is cooperative (the one-CTA kernels serve).
+std::vector<SolveItem> solve_items(const std::vector<std::pair<int64_t, int2>>& subs);
+
 // Multigrid hierarchy of an n x m subdomain interior: levels while both sizes stay odd and
 // >= 3 (n -> (n-1)/2), and the bytes of its per-level arrays (x, b, t pairs; faces; identity).
 __host__ __device__ inline int mg_levels(int n, int m)
@@ -305,6 +336,12 @@ cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off,
                                const int2* order = nullptr);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                           cudaStream_t s);
+// Cooperative solve launches (items from solve_items); the single-problem one also computes the
+// face coefficients first, as launch_solve does.
+cudaError_t launch_solve_items(const SolveParams& P, const SolveItem* items, int n_items, bool fp64_inner,
+                               cudaStream_t s);
+cudaError_t launch_solve_batch_items(const SolveParams* probs, const SolveItem* items, int n_items,
+                                     bool fp64_inner, cudaStream_t s);
 
 // Host/device shared scheduling rule of the adaptive estimator.
 __host__ __device__ inline int64_t adaptive_next_total(int64_t n_done, double se, double target,

@@ -700,8 +700,9 @@ __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(cons
         }
         const int g = P.node_of[lo];
         const int64_t chunk_end = P.p_begin[lo] + P.p_count[lo];
-        const int64_t pb = P.p_begin[lo] + ((int64_t)task - P.task_off[lo]) * kPathsPerTask;
-        const int64_t pe = pb + kPathsPerTask < chunk_end ? pb + kPathsPerTask : chunk_end;
+        const int64_t tp = P.task_paths > 0 ? P.task_paths : kPathsPerTask;
+        const int64_t pb = P.p_begin[lo] + ((int64_t)task - P.task_off[lo]) * tp;
+        const int64_t pe = pb + tp < chunk_end ? pb + tp : chunk_end;
         if constexpr (BATCH) {
             const McProblem<T> R = P.probs[P.node_prob[g]];
             run_task<T, ACC, DEBUG, false>(P, R, g - R.node_offset, g, task, pb, pe, q_xi[warp], q_eta[warp],
@@ -717,7 +718,6 @@ __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(cons
 // One block; node order is preserved so the plan is deterministic.
 // ---------------------------------------------------------------------------------------
 constexpr int kPlanThreads = 1024;
-constexpr int64_t kMaxChunkPerRound = int64_t(1) << 19;
 
 template <typename V>
 __device__ V block_exclusive_scan(V v, V* warp_tot, V& total)
@@ -769,6 +769,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
 {
     __shared__ int64_t s_tasks[33];
     __shared__ int s_act[33];
+    const int64_t tp = P.task_paths > 0 ? P.task_paths : kPathsPerTask;
+    const int64_t max_chunk = (int64_t)kTasksPerRound * tp;  // 2^19 paths at the default task size
     int64_t task_base = 0;
     int act_base = 0;
     for (int base = 0; base < P.M; base += kPlanThreads) {
@@ -777,10 +779,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
         int64_t cnt = 0;
         if (v < P.M) {
             cnt = P.next_total[m] - P.n_done[m];
-            if (cnt > kMaxChunkPerRound) cnt = kMaxChunkPerRound;
+            if (cnt > max_chunk) cnt = max_chunk;
             if (cnt < 0) cnt = 0;
         }
-        const int64_t tasks = cnt > 0 ? (cnt + kPathsPerTask - 1) / kPathsPerTask : 0;
+        const int64_t tasks = cnt > 0 ? (cnt + tp - 1) / tp : 0;
         int64_t task_tot;
         const int64_t t_ex = block_exclusive_scan<int64_t>(tasks, s_tasks, task_tot);
         // the cap excludes a suffix of this block's nodes, so t_ex is also the prefix over the

@@ -25,7 +25,11 @@ struct sdd_problem {
     cudaStream_t stream = nullptr;
     int M = 0;
     std::vector<int32_t> ij;
-    int mc_grid = 1;
+    int mc_grid = 1;                // persistent path-kernel grid: SMs x mc_blocks_per_sm
+    int mc_blocks_per_sm = 1;       // resident path-kernel blocks per SM (sdd_set_mc_config)
+    int mc_max_blocks_per_sm = 1;   // the register limit of the path kernel
+    int task_paths = sdd::kPathsPerTask;  // paths per warp task (sdd_set_mc_config)
+    int nsm = 1;
     bool fp64 = true;
     int acc_mode = sdd::kAcc64;
     int64_t step = 0;
@@ -62,6 +66,8 @@ struct sdd_problem {
     void *ce = nullptr, *cn = nullptr, *vec = nullptr;
     void* mg = nullptr;             // multigrid workspace, mg_stride bytes per subdomain
     size_t mg_stride = 0;
+    std::vector<sdd::SolveItem> h_items;  // cooperative solve items (empty: one CTA per subdomain)
+    sdd::SolveItem* solve_items = nullptr;
     int32_t *st_iters = nullptr, *st_outer = nullptr, *st_ok = nullptr;
     double* st_res = nullptr;
     double* quality = nullptr;      // (nx-1)(ny-1) cell qualities + 2 stats
@@ -101,6 +107,9 @@ struct sdd_problem {
         if (h_n_active) cudaFreeHost(h_n_active);
     }
 };
+
+// Task sizes a problem or batch may use (sdd_set_mc_config).
+inline bool sdd_valid_task_paths(int t) { return t == 1024 || t == 2048 || t == 4096; }
 
 // Sets the calling thread's sdd_last_error message and returns s.
 sdd_status sdd_fail(sdd_status s, const char* msg);

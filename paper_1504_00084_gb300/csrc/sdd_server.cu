@@ -395,7 +395,10 @@ sdd_status finish(sdd_server* s, Request* r)
     S.ce64 = p->ce64; S.cn64 = p->cn64; S.ce = p->ce; S.cn = p->cn; S.vec = p->vec;
     S.mg = p->mg; S.mg_stride = p->mg_stride;
     S.stat_iters = p->st_iters; S.stat_outer = p->st_outer; S.stat_ok = p->st_ok; S.stat_res = p->st_res;
-    S_CK(launch_solve(S, s->fp64, s->fin));
+    if (!p->h_items.empty())
+        S_CK(launch_solve_items(S, p->solve_items, (int)p->h_items.size(), s->fp64, s->fin));
+    else
+        S_CK(launch_solve(S, s->fp64, s->fin));
     s->st.kernel_launches += 2;
     S_CK(cudaEventRecord(r->done_ev, s->fin));
     r->state = kFinishing;

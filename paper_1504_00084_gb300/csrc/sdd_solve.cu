@@ -21,6 +21,7 @@
 // the coarsest level; zero rims on every level (the cycle acts on residual equations).  Inner vectors live in full-grid arrays whose rim
 // entries stay zero, so A p needs no rim special cases.  All reductions are fixed-order
 // block trees: the solve is deterministic.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include "sdd_internal.cuh"
@@ -44,19 +45,36 @@ template <typename TI> struct Pair {
 constexpr int kIlp = 1;
 constexpr int kIlpSweep = SDD_SOLVE_ILP;
 
-// Visits the nodes (i, j) of an nx x ny row-major array.  Warp w takes rows w, w + W, ...; in a
-// row, lane l takes columns c0 + s (l + 32 u) for u < U, with s = 1 and c0 = 0 (colour < 0), or
-// s = 2 and c0 = (j + colour) & 1 (the nodes with (i + j) % 2 == colour).  value(i, j) computes
-// a node's result from loads only and put(i, j, v) stores it: a lane issues the loads of its U
-// nodes before any store, so U nodes' memory requests are in flight together, and no index is
-// divided.
-template <int U, typename Value, typename Put>
-__device__ __forceinline__ void for_rows(int nx, int ny, int colour, Value value, Put put)
+// The CTAs that solve one subdomain together: one CTA (CW = 1), or the CW CTAs of a thread-block
+// cluster (a large subdomain).  Rows, loops and reductions are spread over all of the team's
+// threads; sync() is the CTA barrier or the cluster barrier, which also orders the team's global
+// memory writes before the reads that follow it.
+template <int CW> struct Team {
+    int rank;  // rank of this CTA in the team (0 when CW = 1)
+    __device__ __forceinline__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ __forceinline__ int nthreads() const { return CW * (int)blockDim.x; }
+    __device__ __forceinline__ int warp() const { return rank * (int)(blockDim.x >> 5) + (int)(threadIdx.x >> 5); }
+    __device__ __forceinline__ int nwarps() const { return CW * (int)(blockDim.x >> 5); }
+    __device__ __forceinline__ void sync() const
+    {
+        if constexpr (CW == 1) __syncthreads();
+        else cooperative_groups::this_cluster().sync();
+    }
+};
+
+// Visits the nodes (i, j) of an nx x ny row-major array.  Warp w of the team takes rows w, w + W,
+// ...; in a row, lane l takes columns c0 + s (l + 32 u) for u < U, with s = 1 and c0 = 0
+// (colour < 0), or s = 2 and c0 = (j + colour) & 1 (the nodes with (i + j) % 2 == colour).
+// value(i, j) computes a node's result from loads only and put(i, j, v) stores it: a lane issues
+// the loads of its U nodes before any store, so U nodes' memory requests are in flight together,
+// and no index is divided.
+template <int U, int CW, typename Value, typename Put>
+__device__ __forceinline__ void for_rows(const Team<CW>& tm, int nx, int ny, int colour, Value value, Put put)
 {
     using V = decltype(value(0, 0));
-    const int lane = threadIdx.x & 31, W = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, W = tm.nwarps();
     const int st = colour < 0 ? 1 : 2;
-    for (int j = threadIdx.x >> 5; j < ny; j += W) {
+    for (int j = tm.warp(); j < ny; j += W) {
         const int c0 = colour < 0 ? 0 : ((j + colour) & 1);
         for (int b = c0 + st * lane; b < nx; b += st * 32 * U) {
             V v[U];
@@ -70,7 +88,32 @@ __device__ __forceinline__ void for_rows(int nx, int ny, int colour, Value value
     }
 }
 
-// Sum of NV doubles over the block; every thread receives the totals.
+// Sum of NV doubles over the team; every thread receives the totals.  Within a CTA a fixed
+// warp tree; across the CTAs of a cluster the CTA totals in rank order (read from each CTA's
+// shared memory), so every thread of the team gets the same bits.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sh);
+
+template <int CW, int NV>
+__device__ __forceinline__ void team_sum(const Team<CW>& tm, double (&v)[NV], double* sh)
+{
+    if constexpr (CW == 1) {
+        block_sum<NV>(v, sh);
+    } else {
+        namespace cg = cooperative_groups;
+        block_sum<NV>(v, sh);                  // this CTA's totals, also left in sh[32 NV + 32 k]
+        cg::cluster_group cl = cg::this_cluster();
+        cl.sync();                             // every CTA's totals are in place
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = 0.0;
+            for (int r = 0; r < CW; ++r) t += *cl.map_shared_rank(sh + 32 * NV + 32 * k, r);
+            v[k] = t;
+        }
+        cl.sync();                             // nobody overwrites sh before all have read it
+    }
+}
+
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh)
 {
@@ -178,10 +221,10 @@ __device__ __forceinline__ Pair<TI> mg_offdiag(const MgLevel<TI>& L, int i, int 
 }
 
 // one Gauss-Seidel half-sweep over the nodes of one colour ((i + j) % 2 == colour)
-template <typename TI>
-__device__ __forceinline__ void mg_half_sweep(const MgLevel<TI>& L, int colour)
+template <typename TI, int CW>
+__device__ __forceinline__ void mg_half_sweep(const Team<CW>& tm, const MgLevel<TI>& L, int colour)
 {
-    for_rows<kIlpSweep>(
+    for_rows<kIlpSweep>(tm, 
         L.nx, L.ny, colour,
         [&](int i, int j) {
             const Pair<TI> o = mg_offdiag(L, i, j);
@@ -190,21 +233,21 @@ __device__ __forceinline__ void mg_half_sweep(const MgLevel<TI>& L, int colour)
             return Pair<TI>{(bb.x + o.x) / dg, (bb.y + o.y) / dg};
         },
         [&](int i, int j, const Pair<TI>& v) { L.x[j * L.nx + i] = v; });
-    __syncthreads();
+    tm.sync();
 }
 
-template <typename TI>
-__device__ __forceinline__ void mg_zero(const MgLevel<TI>& L)
+template <typename TI, int CW>
+__device__ __forceinline__ void mg_zero(const Team<CW>& tm, const MgLevel<TI>& L)
 {
-    for (int k = threadIdx.x; k < L.nx * L.ny; k += blockDim.x) L.x[k] = Pair<TI>{(TI)0, (TI)0};
-    __syncthreads();
+    for (int k = tm.tid(); k < L.nx * L.ny; k += tm.nthreads()) L.x[k] = Pair<TI>{(TI)0, (TI)0};
+    tm.sync();
 }
 
 // b_{l+1} = full weighting of the residual t_l = b_l - A_l x_l
-template <typename TI>
-__device__ __forceinline__ void mg_restrict(const MgLevel<TI>& F, const MgLevel<TI>& C)
+template <typename TI, int CW>
+__device__ __forceinline__ void mg_restrict(const Team<CW>& tm, const MgLevel<TI>& F, const MgLevel<TI>& C)
 {
-    for_rows<kIlp>(
+    for_rows<kIlp>(tm, 
         F.nx, F.ny, -1,
         [&](int i, int j) {
             const int k = j * F.nx + i;
@@ -214,8 +257,8 @@ __device__ __forceinline__ void mg_restrict(const MgLevel<TI>& F, const MgLevel<
             return Pair<TI>{bv.x - (dg * xv.x - o.x), bv.y - (dg * xv.y - o.y)};
         },
         [&](int i, int j, const Pair<TI>& v) { F.t[j * F.nx + i] = v; });
-    __syncthreads();
-    for_rows<kIlp>(
+    tm.sync();
+    for_rows<kIlp>(tm, 
         C.nx, C.ny, -1,
         [&](int I, int J) {
             const int i = 2 * I + 1, j = 2 * J + 1;
@@ -232,14 +275,14 @@ __device__ __forceinline__ void mg_restrict(const MgLevel<TI>& F, const MgLevel<
             return acc;
         },
         [&](int I, int J, const Pair<TI>& v) { C.b[J * C.nx + I] = v; });
-    __syncthreads();
+    tm.sync();
 }
 
 // x_l += bilinear interpolation of x_{l+1} (coarse rims are zero)
-template <typename TI>
-__device__ __forceinline__ void mg_prolong(const MgLevel<TI>& F, const MgLevel<TI>& C)
+template <typename TI, int CW>
+__device__ __forceinline__ void mg_prolong(const Team<CW>& tm, const MgLevel<TI>& F, const MgLevel<TI>& C)
 {
-    for_rows<kIlp>(F.nx, F.ny, -1, [&](int i, int j) {
+    for_rows<kIlp>(tm, F.nx, F.ny, -1, [&](int i, int j) {
         // coarse neighbours: odd fine index 2I+1 -> I; even fine index 2I -> I-1 and I
         const int Ia = (i & 1) ? (i - 1) / 2 : i / 2 - 1, Ib = (i & 1) ? Ia : i / 2;
         const int Ja = (j & 1) ? (j - 1) / 2 : j / 2 - 1, Jb = (j & 1) ? Ja : j / 2;
@@ -260,74 +303,74 @@ __device__ __forceinline__ void mg_prolong(const MgLevel<TI>& F, const MgLevel<T
         const Pair<TI> f = F.x[j * F.nx + i];
         return Pair<TI>{f.x + s.x, f.y + s.y};
     }, [&](int i, int j, const Pair<TI>& v) { F.x[j * F.nx + i] = v; });
-    __syncthreads();
+    tm.sync();
 }
 
 // Coefficients of every level from the fine face coefficients of the subdomain.
-template <typename TI>
-__device__ void mg_setup(const SolveParams& P, int i0, int j0, int nx0, int ny0, int levels)
+template <typename TI, int CW>
+__device__ void mg_setup(const Team<CW>& tm, const SolveParams& P, int i0, int j0, int nx0, int ny0, int levels)
 {
     const TI* ce = static_cast<const TI*>(P.ce);
     const TI* cn = static_cast<const TI*>(P.cn);
     const int nx = P.nx;
     const MgLevel<TI> L0 = mg_level<TI>(P.mg, nx0, ny0, 0);
-    for (int k = threadIdx.x; k < (nx0 + 1) * ny0; k += blockDim.x) {
+    for (int k = tm.tid(); k < (nx0 + 1) * ny0; k += tm.nthreads()) {
         const int f = k % (nx0 + 1), j = k / (nx0 + 1);
         L0.ce[k] = ce[(long)(j0 + 1 + j) * nx + (i0 + f)];
     }
-    for (int k = threadIdx.x; k < nx0 * (ny0 + 1); k += blockDim.x) {
+    for (int k = tm.tid(); k < nx0 * (ny0 + 1); k += tm.nthreads()) {
         const int i = k % nx0, g = k / nx0;
         L0.cn[k] = cn[(long)(j0 + g) * nx + (i0 + 1 + i)];
     }
-    for (int k = threadIdx.x; k < nx0 * ny0; k += blockDim.x) {
+    for (int k = tm.tid(); k < nx0 * ny0; k += tm.nthreads()) {
         const int i = k % nx0, j = k / nx0;
         L0.d[k] = P.form == 0 ? (TI)1 : (TI)P.om64[(long)(j0 + 1 + j) * nx + (i0 + 1 + i)];
     }
-    __syncthreads();
+    tm.sync();
     for (int l = 0; l + 1 < levels; ++l) {
         const MgLevel<TI> F = mg_level<TI>(P.mg, nx0, ny0, l), C = mg_level<TI>(P.mg, nx0, ny0, l + 1);
-        for (int k = threadIdx.x; k < (C.nx + 1) * C.ny; k += blockDim.x) {
+        for (int k = tm.tid(); k < (C.nx + 1) * C.ny; k += tm.nthreads()) {
             const int f = k % (C.nx + 1), J = k / (C.nx + 1);
             const TI a = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f], b = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f + 1];
             C.ce[k] = (TI)0.5 * a * b / (a + b);
         }
-        for (int k = threadIdx.x; k < C.nx * (C.ny + 1); k += blockDim.x) {
+        for (int k = tm.tid(); k < C.nx * (C.ny + 1); k += tm.nthreads()) {
             const int I = k % C.nx, g = k / C.nx;
             const TI a = F.cn[(2 * g) * F.nx + 2 * I + 1], b = F.cn[(2 * g + 1) * F.nx + 2 * I + 1];
             C.cn[k] = (TI)0.5 * a * b / (a + b);
         }
-        for (int k = threadIdx.x; k < C.nx * C.ny; k += blockDim.x) {
+        for (int k = tm.tid(); k < C.nx * C.ny; k += tm.nthreads()) {
             const int I = k % C.nx, J = k / C.nx;
             C.d[k] = F.d[(2 * J + 1) * F.nx + 2 * I + 1];
         }
-        __syncthreads();
+        tm.sync();
     }
 }
 
 // x_0 = V-cycle(b_0): one symmetric multigrid cycle.
-template <typename TI>
-__device__ __noinline__ void mg_vcycle(void* base, int nx0, int ny0, int levels)
+template <typename TI, int CW>
+__device__ __noinline__ void mg_vcycle(const Team<CW> tm, void* base, int nx0, int ny0, int levels)
 {
     for (int l = 0; l + 1 < levels; ++l) {
         const MgLevel<TI> F = mg_level<TI>(base, nx0, ny0, l);
-        mg_zero(F);
-        mg_half_sweep(F, 0);
-        mg_half_sweep(F, 1);
-        mg_restrict(F, mg_level<TI>(base, nx0, ny0, l + 1));
+        mg_zero(tm, F);
+        mg_half_sweep(tm, F, 0);
+        mg_half_sweep(tm, F, 1);
+        mg_restrict(tm, F, mg_level<TI>(base, nx0, ny0, l + 1));
     }
     const MgLevel<TI> Lc = mg_level<TI>(base, nx0, ny0, levels - 1);
-    mg_zero(Lc);
+    mg_zero(tm, Lc);
     for (int s = 0; s < kCoarseSweeps; ++s) {
-        mg_half_sweep(Lc, 0);
-        mg_half_sweep(Lc, 1);
-        mg_half_sweep(Lc, 1);
-        mg_half_sweep(Lc, 0);
+        mg_half_sweep(tm, Lc, 0);
+        mg_half_sweep(tm, Lc, 1);
+        mg_half_sweep(tm, Lc, 1);
+        mg_half_sweep(tm, Lc, 0);
     }
     for (int l = levels - 2; l >= 0; --l) {
         const MgLevel<TI> F = mg_level<TI>(base, nx0, ny0, l);
-        mg_prolong(F, mg_level<TI>(base, nx0, ny0, l + 1));
-        mg_half_sweep(F, 1);
-        mg_half_sweep(F, 0);
+        mg_prolong(tm, F, mg_level<TI>(base, nx0, ny0, l + 1));
+        mg_half_sweep(tm, F, 1);
+        mg_half_sweep(tm, F, 0);
     }
 }
 
@@ -432,8 +475,8 @@ __device__ void fe_body(const SolveParams& P, int sub, double* sh)
 }
 
 // Subdomain `sub` of the problem described by P, solved by the calling CTA.
-template <typename TI>
-__device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double* sh)
+template <typename TI, int CW>
+__device__ __forceinline__ void solve_body(const Team<CW>& tm, const SolveParams& P, int sub, double* sh)
 {
     const int nx = P.nx, ny = P.ny;
     const int I = sub % P.px, J = sub / P.px;
@@ -454,12 +497,12 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
     auto dP = [&](long id) -> double { return P.form == 0 ? 1.0 : P.om64[id]; };
 
     // initial guess: the previous mesh
-    for_rows<kIlp>(
+    for_rows<kIlp>(tm, 
         ni, nj, -1, [&](int ii, int jj) { const long id = gid(ii, jj); return Pair<double>{P.xcur[id], P.ycur[id]}; },
         [&](int ii, int jj, const Pair<double>& v) { const long id = gid(ii, jj); P.xnew[id] = v.x; P.ynew[id] = v.y; });
     // ||b||: b = d x^n + rim terms (rim values are the new Dirichlet data, not written here)
     double bn[2] = {0.0, 0.0};
-    for_rows<kIlp>(
+    for_rows<kIlp>(tm, 
         ni, nj, -1,
         [&](int ii, int jj) {
             const long id = gid(ii, jj);
@@ -473,23 +516,23 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
             return Pair<double>{bx, by};
         },
         [&](int, int, const Pair<double>& v) { bn[0] += v.x * v.x; bn[1] += v.y * v.y; });
-    __syncthreads();
-    block_sum<2>(bn, sh);
+    tm.sync();
+    team_sum<CW, 2>(tm, bn, sh);
 
     // multigrid hierarchy of this subdomain
     void* mgbase = static_cast<char*>(P.mg) + (size_t)sub * P.mg_stride;
     SolveParams Pm = P;
     Pm.mg = mgbase;
     const int levels = mg_levels(ni, nj);
-    if (nint > 0) mg_setup<TI>(Pm, i0, j0, ni, nj, levels);
+    if (nint > 0) mg_setup<TI>(tm, Pm, i0, j0, ni, nj, levels);
     const MgLevel<TI> L0 = mg_level<TI>(mgbase, ni, nj, 0);
     // z = V-cycle(r) into L0.x (interior-compact), from the full-grid residual r
     auto precondition = [&]() {
-        for_rows<kIlp>(
+        for_rows<kIlp>(tm, 
             ni, nj, -1, [&](int ii, int jj) { return r[gid(ii, jj)]; },
             [&](int ii, int jj, const Pair<TI>& v) { L0.b[jj * ni + ii] = v; });
-        __syncthreads();
-        mg_vcycle<TI>(mgbase, ni, nj, levels);
+        tm.sync();
+        mg_vcycle<TI>(tm, mgbase, ni, nj, levels);
     };
 
     const bool fp64_inner = sizeof(TI) == 8;
@@ -498,7 +541,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
     for (outer = 0; outer < kMaxOuter; ++outer) {
         // FP64 residual of the current iterate
         double rn[2] = {0.0, 0.0};
-        for_rows<kIlp>(
+        for_rows<kIlp>(tm, 
             ni, nj, -1,
             [&](int ii, int jj) {
                 const long id = gid(ii, jj);
@@ -516,8 +559,8 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
                 rn[0] += v.x * v.x;
                 rn[1] += v.y * v.y;
             });
-        __syncthreads();
-        block_sum<2>(rn, sh);
+        tm.sync();
+        team_sum<CW, 2>(tm, rn, sh);
         const double relx = bn[0] > 0 ? sqrt(rn[0] / bn[0]) : sqrt(rn[0]);
         const double rely = bn[1] > 0 ? sqrt(rn[1] / bn[1]) : sqrt(rn[1]);
         rel = relx > rely ? relx : rely;
@@ -538,7 +581,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
         // CG start: e = 0, p = z = M^-1 r (one V-cycle)
         precondition();
         double rz[2] = {0.0, 0.0}, rr0[2] = {0.0, 0.0};
-        for_rows<kIlp>(
+        for_rows<kIlp>(tm, 
             ni, nj, -1, [&](int ii, int jj) { return Pair<Pair<TI>>{r[gid(ii, jj)], L0.x[jj * ni + ii]}; },
             [&](int ii, int jj, const Pair<Pair<TI>>& v) {
                 const long id = gid(ii, jj);
@@ -550,17 +593,17 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
                 rr0[0] += (double)rv.x * (double)rv.x;
                 rr0[1] += (double)rv.y * (double)rv.y;
             });
-        __syncthreads();
+        tm.sync();
         {
             double v[4] = {rz[0], rz[1], rr0[0], rr0[1]};
-            block_sum<4>(v, sh);
+            team_sum<CW, 4>(tm, v, sh);
             rz[0] = v[0]; rz[1] = v[1]; rr0[0] = v[2]; rr0[1] = v[3];
         }
         bool done_c[2] = {rr0[0] == 0.0, rr0[1] == 0.0};
         while (iters < P.max_iter && !(done_c[0] && done_c[1])) {
             ++iters;
             double pq[2] = {0.0, 0.0};
-            for_rows<kIlp>(
+            for_rows<kIlp>(tm, 
                 ni, nj, -1,
                 [&](int ii, int jj) {
                     const long id = gid(ii, jj);
@@ -575,12 +618,12 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
                     pq[0] += (double)v.x.x * (double)v.y.x;
                     pq[1] += (double)v.x.y * (double)v.y.y;
                 });
-            __syncthreads();
-            block_sum<2>(pq, sh);
+            tm.sync();
+            team_sum<CW, 2>(tm, pq, sh);
             const TI ax = (!done_c[0] && pq[0] > 0) ? (TI)(rz[0] / pq[0]) : (TI)0;
             const TI ay = (!done_c[1] && pq[1] > 0) ? (TI)(rz[1] / pq[1]) : (TI)0;
             double v[4] = {0.0, 0.0, 0.0, 0.0};  // r.z (x, y), r.r (x, y)
-            for_rows<kIlp>(
+            for_rows<kIlp>(tm, 
                 ni, nj, -1,
                 [&](int ii, int jj) {
                     const long id = gid(ii, jj);
@@ -595,9 +638,9 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
                     e[id] = v.x;
                     r[id] = v.y;
                 });
-            __syncthreads();
+            tm.sync();
             precondition();
-            for_rows<kIlp>(
+            for_rows<kIlp>(tm, 
                 ni, nj, -1, [&](int ii, int jj) { return Pair<Pair<TI>>{r[gid(ii, jj)], L0.x[jj * ni + ii]}; },
                 [&](int, int, const Pair<Pair<TI>>& w) {
                     const Pair<TI> rv = w.x, z = w.y;
@@ -606,25 +649,25 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
                     v[2] += (double)rv.x * (double)rv.x;
                     v[3] += (double)rv.y * (double)rv.y;
                 });
-            __syncthreads();
-            block_sum<4>(v, sh);
+            tm.sync();
+            team_sum<CW, 4>(tm, v, sh);
             for (int c = 0; c < 2; ++c)
                 if (!done_c[c] && v[2 + c] <= tol_rel[c] * tol_rel[c] * rr0[c]) done_c[c] = true;
             const TI bx = (!done_c[0] && rz[0] > 0) ? (TI)(v[0] / rz[0]) : (TI)0;
             const TI by = (!done_c[1] && rz[1] > 0) ? (TI)(v[1] / rz[1]) : (TI)0;
             rz[0] = v[0];
             rz[1] = v[1];
-            for_rows<kIlp>(
+            for_rows<kIlp>(tm, 
                 ni, nj, -1,
                 [&](int ii, int jj) {
                     const Pair<TI> z = L0.x[jj * ni + ii], pc = p[gid(ii, jj)];
                     return Pair<TI>{z.x + bx * pc.x, z.y + by * pc.y};
                 },
                 [&](int ii, int jj, const Pair<TI>& w) { p[gid(ii, jj)] = w; });
-            __syncthreads();
+            tm.sync();
         }
         // x += e
-        for_rows<kIlp>(
+        for_rows<kIlp>(tm, 
             ni, nj, -1,
             [&](int ii, int jj) {
                 const long id = gid(ii, jj);
@@ -636,9 +679,9 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
                 P.xnew[id] = w.x;
                 P.ynew[id] = w.y;
             });
-        __syncthreads();
+        tm.sync();
     }
-    if (threadIdx.x == 0) {
+    if (tm.tid() == 0) {
         P.stat_iters[sub] = iters;
         P.stat_outer[sub] = outer;
         P.stat_ok[sub] = ok;
@@ -646,11 +689,14 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, int sub, double
     }
 }
 
+template <typename TI, int CW>
+__device__ __noinline__ void solve_sub(const Team<CW> tm, const SolveParams& P, int sub, double* sh);
+
 template <typename TI>
 __global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_constant__ SolveParams P)
 {
     __shared__ double sh[32 * 8 + 8];
-    solve_body<TI>(P, blockIdx.x, sh);
+    solve_sub<TI, 1>(Team<1>{0}, P, blockIdx.x, sh);
 }
 
 __global__ void __launch_bounds__(kSolveThreads) fe_kernel(const __grid_constant__ SolveParams P)
@@ -706,10 +752,108 @@ __global__ void __launch_bounds__(kSolveThreads, 1) solve_batch_kernel(const Sol
     __shared__ int sub;
     if (threadIdx.x == 0) batch_lookup(probs, sub_off, order, n, sp, sub);
     __syncthreads();
-    if (sp.scheme == 0) solve_body<TI>(sp, sub, sh);  // forward-Euler problems: fe_batch_kernel
+    if (sp.scheme == 0) solve_sub<TI, 1>(Team<1>{0}, sp, sub, sh);  // forward-Euler problems: fe_batch_kernel
+}
+
+// The solve of one subdomain as a function of its own, called by every solve kernel: each team
+// width is compiled once, so a subdomain runs the same instructions in a single-problem launch, a
+// batch and a served request (bitwise the same results), and the two widths of the cooperative
+// kernels do not share one register allocation.
+template <typename TI, int CW>
+__device__ __noinline__ void solve_sub(const Team<CW> tm, const SolveParams& P, int sub, double* sh)
+{
+    solve_body<TI, CW>(tm, P, sub, sh);
+}
+
+// Subdomains with at least kCoopUnknowns interior unknowns are solved by the kCoopWidth CTAs of
+// a thread-block cluster, each on its own SM (1024 threads, the whole register file): rows,
+// loops and reductions are spread over the cluster and every pass ends in a cluster barrier.  The
+// team width is a function of the subdomain's size alone, so a subdomain gives the same bits in a
+// single-problem launch, a batch and a served request.
+template <typename TI>
+__device__ __forceinline__ void solve_item(const SolveParams& sp, const SolveItem& it, double* sh)
+{
+    if (it.width == kCoopWidth) {
+        const unsigned rank = cooperative_groups::this_cluster().block_rank();
+        solve_sub<TI, kCoopWidth>(Team<kCoopWidth>{(int)rank}, sp, it.sub, sh);
+    } else if (it.width == 1) {
+        solve_sub<TI, 1>(Team<1>{0}, sp, it.sub, sh);
+    }
+}
+
+// One work item per CTA (launch: items.size() CTAs in clusters of kCoopWidth).  A cooperative
+// item fills a whole cluster (its kCoopWidth entries are the same); otherwise each CTA of the
+// cluster solves its own subdomain, or none (width 0).
+template <typename TI>
+__global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThreads, 1)
+    solve_items_kernel(const __grid_constant__ SolveParams P, const SolveItem* items)
+{
+    __shared__ double sh[32 * 8 + 8];
+    solve_item<TI>(P, items[blockIdx.x], sh);
+}
+
+template <typename TI>
+__global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThreads, 1)
+    solve_batch_items_kernel(const SolveParams* probs, const SolveItem* items)
+{
+    __shared__ double sh[32 * 8 + 8];
+    __shared__ SolveParams sp;
+    const SolveItem it = items[blockIdx.x];
+    if (threadIdx.x == 0 && it.width > 0) sp = probs[it.prob];
+    __syncthreads();
+    if (it.width > 0 && sp.scheme == 0) solve_item<TI>(sp, it, sh);
 }
 
 }  // namespace
+
+std::vector<SolveItem> solve_items(const std::vector<std::pair<int64_t, int2>>& subs)
+{
+    std::vector<SolveItem> items;
+    bool any = false;
+    for (const auto& v : subs) any = any || v.first >= kCoopUnknowns;
+    if (!any) return items;
+    std::vector<SolveItem> pend;  // subdomains of one CTA each, waiting to fill a cluster
+    for (const auto& v : subs) {
+        if (v.first >= kCoopUnknowns) {
+            for (int r = 0; r < kCoopWidth; ++r) items.push_back(SolveItem{v.second.x, v.second.y, kCoopWidth, 0});
+        } else {
+            pend.push_back(SolveItem{v.second.x, v.second.y, 1, 0});
+            if ((int)pend.size() == kCoopWidth) {
+                items.insert(items.end(), pend.begin(), pend.end());
+                pend.clear();
+            }
+        }
+    }
+    if (!pend.empty()) {
+        while ((int)pend.size() < kCoopWidth) pend.push_back(SolveItem{0, 0, 0, 0});
+        items.insert(items.end(), pend.begin(), pend.end());
+    }
+    return items;
+}
+
+cudaError_t launch_solve_items(const SolveParams& P, const SolveItem* items, int n_items, bool fp64_inner,
+                               cudaStream_t s)
+{
+    const long n = (long)P.nx * P.ny;
+    faces_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(P, fp64_inner ? 1 : 0);
+    if (n_items <= 0) return cudaGetLastError();
+    if (fp64_inner)
+        solve_items_kernel<double><<<n_items, kSolveThreads, 0, s>>>(P, items);
+    else
+        solve_items_kernel<float><<<n_items, kSolveThreads, 0, s>>>(P, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve_batch_items(const SolveParams* probs, const SolveItem* items, int n_items,
+                                     bool fp64_inner, cudaStream_t s)
+{
+    if (n_items <= 0) return cudaSuccess;
+    if (fp64_inner)
+        solve_batch_items_kernel<double><<<n_items, kSolveThreads, 0, s>>>(probs, items);
+    else
+        solve_batch_items_kernel<float><<<n_items, kSolveThreads, 0, s>>>(probs, items);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s)
 {

@@ -1,5 +1,5 @@
 """The ctypes mirrors of the C ABI's structs (sdd_params, sdd_stats, sdd_server_params,
-sdd_server_stats) have the C layout: a C program compiled against include/sdd.h prints the
+sdd_server_stats, sdd_mc_config) have the C layout: a C program compiled against include/sdd.h prints the
 size of each struct and the offset of each field, and the binding's structures match them."""
 import ctypes
 import os
@@ -11,7 +11,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 STRUCTS = {"sdd_params": "SddParams", "sdd_stats": "SddStats", "sdd_server_params": "SddServerParams",
-           "sdd_server_stats": "SddServerStats"}
+           "sdd_server_stats": "SddServerStats", "sdd_mc_config": "SddMcConfig"}
 
 
 def test_struct_layouts_match_the_header(tmp_path):

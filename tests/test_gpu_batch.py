@@ -192,3 +192,27 @@ def test_batch_fp64_matches_oracle():
         assert h.stats()["step_index"] == 2
     for h in hs:
         h.close()
+
+
+def test_batch_with_cluster_solved_subdomains_equals_alone():
+    """A batch holding a 513 x 513 problem split 2 x 2 (255^2 interior unknowns per subdomain,
+    solved by clusters of CTAs) beside small problems: every mesh is bitwise the mesh of stepping
+    the problem alone (the small subdomains run the same one-CTA solve in either launch)."""
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    big = W.c3_mix(64)[0].replace(nx=513, ny=513, px=2, py=2, precision=W.PREC_FP32_KAHAN, paths_per_node=1024,
+                                  seed=41)
+    probs = [big] + small_mix(W.PREC_FP32_KAHAN, paths=1024, n=3)
+    ref = meshes_alone(probs, 1)
+    hs = [gpu_problem(p) for p in probs]
+    stream = torch.cuda.Stream()
+    with S.SddBatch(hs, stream=stream) as b:
+        b.step()
+        st = b.stats()
+    stream.synchronize()
+    assert st["solve_rel_residual"] <= max(p.solve_rtol for p in probs)
+    for h, (rx, ry) in zip(hs, ref):
+        gx, gy = h.mesh()
+        assert np.array_equal(gx, rx) and np.array_equal(gy, ry)
+        h.close()

@@ -455,3 +455,24 @@ def test_twenty_steps_fp32_matches_fp64(S):
     bound = prob.steps * 0.5 * max(ses)
     assert np.abs(meshes[0][0] - meshes[1][0]).max() <= bound
     assert np.abs(meshes[0][1] - meshes[1][1]).max() <= bound
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32_ACC64])
+def test_cluster_solved_subdomain_matches_oracle(S, precision):
+    """A subdomain of 255 x 255 interior unknowns (above the cooperative threshold) is solved by a
+    cluster of CTAs; one Dirichlet subdomain (px = py = 1, no interface) on a 257 x 257 sine mesh
+    with the Gaussian monitor, against the oracle's direct single-domain solve, within the solver
+    bound (FP32 inner iterations with FP64 refinement reach the same target)."""
+    prob = W.c0_small_fp64().replace(nx=257, ny=257, px=1, py=1, precision=precision, solve_rtol=1e-11)
+    x, y = W.sine_mode_mesh(prob, amp=0.03)
+    h = gpu_problem(prob, x, y)
+    assert h.M == 0
+    gx, gy, status = h.step()
+    assert status == 0 and h.stats()["solve_rel_residual"] <= prob.solve_rtol
+    h.close()
+    from oracle.solve import single_domain_step
+    om = ostep.monitor_on_mesh(prob, x, y, prob.t0)
+    ox, oy = single_domain_step(om, x, y, prob.dt, prob.tau, prob.form)
+    bx, by = ostep.scatter(prob, np.zeros((0, 2), np.int32), np.zeros((0, 2)))
+    tol = mesh_tolerance(prob, om, bx, by, x, y, 0.0)
+    assert np.abs(gx - ox).max() <= tol and np.abs(gy - oy).max() <= tol
