@@ -7,7 +7,9 @@
 // the task (ballot + popc), so the 32 lanes stay busy through paths of very different
 // lengths.  A path that completes its K substeps parks its final point in a per-warp
 // shared-memory queue; the warp evaluates the bicubic terminal values 32 at a time, one per
-// lane, instead of stalling on that long branch whenever any single lane finishes.  The
+// lane, instead of stalling on that long branch whenever any single lane finishes.  Exits are
+// queued the same way (proposed point and bridge side), and their exit points, boundary values
+// and sums are formed 32 at a time rather than on the few lanes whose path just ended.  The
 // assignment of path indices to lanes depends only on the paths' own lengths,
 // so a task's partial sums are a deterministic function of (node, path range) and are
 // independent of scheduling and of which other problems or nodes share the launch.
@@ -378,10 +380,43 @@ template <> struct BridgeP<float> {
     }
 };
 
-// One substep k of path p at node m.  Returns 0 while the path goes on; 1 when it exits
-// at this substep ((vx, vy) = boundary mesh at the exit point, side = exit side); 2 when it
-// completes its K-th substep ((xi, eta) = final point; its value, the previous mesh there,
-// is evaluated later for 32 such paths at once).
+// Exit of a path whose proposed point (xn, en) left the unit square or whose bridge crossed side
+// s (s < 0: the endpoint test fired; the side is the deepest violation, ties to the lower
+// index): the exit point keeps the other coordinate of (xn, en), clamped to [0, 1], and the value
+// is the boundary mesh there (the new boundary mesh along the side with a moving boundary).
+// Returns the side.
+template <typename T>
+__device__ __forceinline__ int exit_value(const McProblem<T>& P, T xn, T en, int s, T& vx, T& vy)
+{
+    if (s < 0) {  // deepest violation
+        T vmax = -xn;
+        s = 0;
+        if (xn - 1 > vmax) { vmax = xn - 1; s = 1; }
+        if (-en > vmax) { vmax = -en; s = 2; }
+        if (en - 1 > vmax) { vmax = en - 1; s = 3; }
+    }
+    T xe = clamp01(xn), ee = clamp01(en);
+    if (s == 0) xe = 0;
+    if (s == 1) xe = 1;
+    if (s == 2) ee = 0;
+    if (s == 3) ee = 1;
+    if (P.bnd) {  // moving boundary: the new boundary mesh along the exit side
+        if (s == 0) { vx = (T)0; vy = side_lerp(P.bnd + 2 * P.nx, P.ny, ee); }
+        else if (s == 1) { vx = P.Lx; vy = side_lerp(P.bnd + 2 * P.nx + P.ny, P.ny, ee); }
+        else if (s == 2) { vx = side_lerp(P.bnd, P.nx, xe); vy = (T)0; }
+        else { vx = side_lerp(P.bnd + P.nx, P.nx, xe); vy = P.Ly; }
+    } else {
+        vx = P.Lx * xe;
+        vy = P.Ly * ee;
+    }
+    return s;
+}
+
+// One substep k of path p at node m.  Returns 0 while the path goes on; 1 when it exits at this
+// substep ((vx, vy) = the proposed point outside the square or across the bridge, side = the
+// bridge's side or -1; exit_value turns them into the exit point and value later, for 32 exits at
+// once); 2 when it completes its K-th substep ((xi, eta) = final point; its value, the previous
+// mesh there, is evaluated later for 32 such paths at once).
 // RK: the problem record holds the round keys in the launch's parameter block (single-problem
 // launches); otherwise the keys are stepped inside the generator.
 // The parts of Philox rounds 0 and 1 that do not depend on the substep k (counter (k, p, m, n)):
@@ -472,27 +507,10 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
             }
         }
         if (exited) {
-            if (s < 0) {  // deepest violation
-                T vmax = -xn;
-                s = 0;
-                if (xn - 1 > vmax) { vmax = xn - 1; s = 1; }
-                if (-en > vmax) { vmax = -en; s = 2; }
-                if (en - 1 > vmax) { vmax = en - 1; s = 3; }
-            }
-            T xe = clamp01(xn), ee = clamp01(en);
-            if (s == 0) xe = 0;
-            if (s == 1) xe = 1;
-            if (s == 2) ee = 0;
-            if (s == 3) ee = 1;
-            if (P.bnd) {  // moving boundary: the new boundary mesh along the exit side
-                if (s == 0) { vx = (T)0; vy = side_lerp(P.bnd + 2 * P.nx, P.ny, ee); }
-                else if (s == 1) { vx = P.Lx; vy = side_lerp(P.bnd + 2 * P.nx + P.ny, P.ny, ee); }
-                else if (s == 2) { vx = side_lerp(P.bnd, P.nx, xe); vy = (T)0; }
-                else { vx = side_lerp(P.bnd + P.nx, P.nx, xe); vy = P.Ly; }
-            } else {
-                vx = P.Lx * xe;
-                vy = P.Ly * ee;
-            }
+            // the exit point, its value and its sums are formed later, for 32 exits at a time
+            // (exit_value): here only the proposed point and the bridge side (-1: endpoint test)
+            vx = xn;
+            vy = en;
             side = s;
             return 1;
         }
@@ -560,11 +578,21 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
 };
 
 // Paths pb .. pe-1 of local node m of problem R (global node g): one warp, one task.
+// Per-warp shared-memory queues of ended paths: survivors (final point) wait for their bicubic
+// terminal value, exits (proposed point and bridge side) for their boundary value; each is
+// evaluated 32 at a time, one path per lane.
+template <typename T> struct PathQueues {
+    T* s_xi; T* s_eta; uint32_t* s_path;               // survivors
+    T* e_xn; T* e_en; int32_t* e_side; int32_t* e_k; uint32_t* e_path;  // exits (k, path: debug)
+};
+
 template <typename T, int ACC, bool DEBUG, bool RK>
 __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T>& R, int m, int g,
-                                         int task, int64_t pb, int64_t pe, T* q_xi, T* q_eta,
-                                         uint32_t* q_path)
+                                         int task, int64_t pb, int64_t pe, const PathQueues<T>& Q)
 {
+    T* q_xi = Q.s_xi;
+    T* q_eta = Q.s_eta;
+    uint32_t* q_path = Q.s_path;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int2 ij = R.nodes[m];
@@ -613,30 +641,39 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
         qn -= count;
         __syncwarp();
     };
+    int qe = 0;  // exited paths waiting for their boundary value (warp-uniform)
+    auto drain_exits = [&](int count) {
+        __syncwarp();
+        if (lane < count) {
+            const int pos = checked(qe - count + lane, 64);
+            T vx, vy;
+            const int side = exit_value(R, Q.e_xn[pos], Q.e_en[pos], (int)Q.e_side[pos], vx, vy);
+            acc.add(vx, vy);
+            if (DEBUG) {
+                const int64_t qd = (int64_t)Q.e_path[pos] - P.dbg_p0;  // debug only
+                P.dbg_val[2 * qd] = (double)vx;
+                P.dbg_val[2 * qd + 1] = (double)vy;
+                P.dbg_steps[qd] = Q.e_k[pos];
+                P.dbg_side[qd] = (int8_t)side;
+            }
+        }
+        qe -= count;
+        __syncwarp();
+    };
     while (__any_sync(kFull, live)) {
         int st = 0;
+        T vx, vy;
+        int side = 0;
         if (live) {
-            T vx, vy;
-            int side;
             st = path_substep<T, RK>(R, (uint32_t)m, path, k, xi, eta, vx, vy, side, ph);
             ++k;
             if (st != 0) {
                 steps += (uint32_t)k;
                 paths += 1;
             }
-            if (st == 1) {
-                acc.add(vx, vy);
-                if (DEBUG) {
-                    const int64_t qd = (int64_t)path - P.dbg_p0;
-                    P.dbg_val[2 * qd] = (double)vx;
-                    P.dbg_val[2 * qd + 1] = (double)vy;
-                    P.dbg_steps[qd] = k;
-                    P.dbg_side[qd] = (int8_t)side;
-                }
-            }
         }
         const unsigned dm = __ballot_sync(kFull, st != 0);
-        if (dm) {  // some lane's path ended: queue survivors, hand out the next path indices
+        if (dm) {  // some lane's path ended: queue survivors (and exits), hand out the next path indices
             const unsigned sm = __ballot_sync(kFull, st == 2);
             if (st == 2) {
                 const int pos = checked(qn + __popc(sm & lt), 64);
@@ -645,6 +682,18 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
                 if (DEBUG) q_path[pos] = path;
             }
             qn += __popc(sm);
+            const unsigned em = dm & ~sm;  // exits
+            if (st == 1) {
+                const int pos = checked(qe + __popc(em & lt), 64);
+                Q.e_xn[pos] = vx;
+                Q.e_en[pos] = vy;
+                Q.e_side[pos] = side;
+                if (DEBUG) {
+                    Q.e_k[pos] = k;
+                    Q.e_path[pos] = path;
+                }
+            }
+            qe += __popc(em);
             if (st != 0) {
                 path = next + __popc(dm & lt);
                 if constexpr (RK) {
@@ -659,9 +708,11 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
             }
             next += __popc(dm);
             if (qn >= 32) drain(32);
+            if (qe >= 32) drain_exits(32);
         }
     }
     if (qn > 0) drain(qn);
+    if (qe > 0) drain_exits(qe);
     double a, b, c, d;
     acc.finish(a, b, c, d, paths, P.shift[2 * g], P.shift[2 * g + 1]);
 #pragma unroll
@@ -683,9 +734,16 @@ template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB = kMcThreads>
 __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(const __grid_constant__ McParams<T> P)
 {
     constexpr int kWarps = TPB / 32;
+    constexpr int kD = DEBUG ? 64 : 1;  // debug-only entries per warp
     __shared__ T q_xi[kWarps][64], q_eta[kWarps][64];
-    __shared__ uint32_t q_path[kWarps][64];
+    __shared__ uint32_t q_path[kWarps][kD];
+    __shared__ T e_xn[kWarps][64], e_en[kWarps][64];
+    __shared__ int32_t e_side[kWarps][64];
+    __shared__ int32_t e_k[kWarps][kD];
+    __shared__ uint32_t e_path[kWarps][kD];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const PathQueues<T> Q{q_xi[warp], q_eta[warp], q_path[warp], e_xn[warp], e_en[warp], e_side[warp], e_k[warp],
+                          e_path[warp]};
     const int n_active = *P.n_active;
     const int64_t n_tasks = P.task_off[n_active];
     for (;;) {
@@ -705,10 +763,9 @@ __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(cons
         const int64_t pe = pb + tp < chunk_end ? pb + tp : chunk_end;
         if constexpr (BATCH) {
             const McProblem<T> R = P.probs[P.node_prob[g]];
-            run_task<T, ACC, DEBUG, false>(P, R, g - R.node_offset, g, task, pb, pe, q_xi[warp], q_eta[warp],
-                                           q_path[warp]);
+            run_task<T, ACC, DEBUG, false>(P, R, g - R.node_offset, g, task, pb, pe, Q);
         } else {
-            run_task<T, ACC, DEBUG, true>(P, P.prob, g, g, task, pb, pe, q_xi[warp], q_eta[warp], q_path[warp]);
+            run_task<T, ACC, DEBUG, true>(P, P.prob, g, g, task, pb, pe, Q);
         }
     }
 }
