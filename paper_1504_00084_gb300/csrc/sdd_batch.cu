@@ -70,6 +70,12 @@ struct sdd_batch {
     int2* order_dev = nullptr;       // solve CTAs: (problem, subdomain), largest subdomains first
     SolveItem* items_dev = nullptr;  // cooperative solve items (n_items > 0: large subdomains present)
     int n_items = 0;
+    // batched per-problem launches: records (refreshed every step) and per-problem block offsets
+    BatchRec* rec_dev = nullptr;
+    BatchRec* rec_host = nullptr;
+    int32_t* blk_off_dev = nullptr;
+    int total_blocks = 0;
+    bool any_moving = false;
     int32_t* h_n_active = nullptr;
     // graph
     cudaGraphExec_t graph = nullptr;
@@ -162,6 +168,22 @@ void refresh_records(sdd_batch* b)
         }
         b->solve_host[i] = solve_params(p);
         b->t_host[i] = p->prm.t0 + (double)p->step * p->prm.dt;
+        BatchRec& r = b->rec_host[i];
+        r = BatchRec{};
+        PrepParams& P = r.prep;
+        P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic;
+        P.kind = p->mon_kind; P.n_params = p->n_params; P.precision = p->prm.precision;
+        P.Lx = p->prm.Lx; P.Ly = p->prm.Ly; P.t = 0.0; P.t_dev = b->t_dev + i;
+        P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
+        memcpy(P.params, p->mon_params, sizeof(P.params));
+        P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
+        P.bad = p->bad;
+        P.moving_boundary = p->prm.moving_boundary; P.form = p->prm.form; P.r = p->prm.dt / p->prm.tau;
+        P.bnd64 = p->bnd64; P.bnd = p->bnd; P.bnd_scratch = p->bnd_scratch;
+        r.nodes = p->nodes;
+        r.node_offset = b->node_off[i];
+        r.xnew = p->xn;
+        r.ynew = p->yn;
     }
 }
 
@@ -200,26 +222,13 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
     B_CK(cudaMemcpyAsync(b->solve_dev, b->solve_host, sizeof(SolveParams) * b->n, cudaMemcpyHostToDevice,
                          b->stream));
     B_CK(cudaMemcpyAsync(b->t_dev, b->t_host, sizeof(double) * b->n, cudaMemcpyHostToDevice, b->stream));
-    for (int i = 0; i < b->n; ++i) {
-        sdd_problem* p = b->probs[i];
-        PrepParams P{};
-        P.nx = p->prm.nx; P.ny = p->prm.ny; P.periodic = p->prm.periodic;
-        P.kind = p->mon_kind; P.n_params = p->n_params; P.precision = p->prm.precision;
-        P.Lx = p->prm.Lx; P.Ly = p->prm.Ly; P.t = 0.0; P.t_dev = b->t_dev + i;
-        P.x = p->x; P.y = p->y; P.omega_in = p->omega_nodal;
-        memcpy(P.params, p->mon_params, sizeof(P.params));
-        P.om64 = p->om64; P.wxi64 = p->wxi64; P.weta64 = p->weta64; P.mon = p->mon; P.disp = p->disp;
-        P.bad = p->bad;
-        P.moving_boundary = p->prm.moving_boundary; P.form = p->prm.form; P.r = p->prm.dt / p->prm.tau;
-        P.bnd64 = p->bnd64; P.bnd = p->bnd; P.bnd_scratch = p->bnd_scratch;
-        B_CK(cudaMemsetAsync(p->bad, 0, 4, b->stream));
-        B_CK(launch_prep(P, b->stream));
-        launches += 2;
-        if (p->M > 0) {
-            B_CK(launch_shift(p->nodes, p->M, p->prm.nx, p->x, p->y, b->shift + 2 * (size_t)b->node_off[i],
-                              b->stream));
-            launches += 1;
-        }
+    B_CK(cudaMemcpyAsync(b->rec_dev, b->rec_host, sizeof(BatchRec) * b->n, cudaMemcpyHostToDevice, b->stream));
+    // monitor, packing and moving boundary of every problem, then the estimator shifts: one launch each
+    B_CK(launch_prep_batch(b->rec_dev, b->blk_off_dev, b->n, b->total_blocks, b->fp64, b->any_moving, b->stream));
+    launches += 2 + (b->any_moving ? 1 : 0);
+    if (b->M > 0) {
+        B_CK(launch_shift_batch(b->rec_dev, b->node_prob, b->M, b->shift, b->stream));
+        launches += 1;
     }
     if (b->M > 0) {
         const sdd_params& q = b->probs[0]->prm;
@@ -289,15 +298,12 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
         }
     }
     const bool fp64_inner = b->fp64;
-    for (int i = 0; i < b->n; ++i) {
-        sdd_problem* p = b->probs[i];
-        B_CK(launch_scatter(p->prm.nx, p->prm.ny, p->prm.periodic, p->prm.Lx, p->prm.Ly, p->nodes, p->M,
-                            b->est + 2 * (size_t)b->node_off[i], p->xn, p->yn, b->stream,
-                            p->prm.moving_boundary ? p->bnd64 : nullptr));
-        launches += (p->prm.periodic ? 0 : 1) + (p->M > 0 ? 1 : 0);
-        B_CK(launch_faces(b->solve_host[i], fp64_inner, b->stream));
-        launches += 1;
-    }
+    // Dirichlet rims and interface estimates into every new mesh, then the face coefficients
+    B_CK(launch_scatter_batch(b->rec_dev, b->blk_off_dev, b->n, b->total_blocks, b->node_prob, b->M, b->est,
+                              b->stream));
+    launches += 1 + (b->M > 0 ? 1 : 0);
+    B_CK(launch_faces_batch(b->solve_dev, b->blk_off_dev, b->n, b->total_blocks, fp64_inner, b->stream));
+    launches += 1;
     bool any_be = false, any_fe = false;
     for (const sdd_problem* p : b->probs) {
         any_be = any_be || p->prm.subdomain_scheme == 0;
@@ -315,12 +321,8 @@ sdd_status record_step(sdd_batch* b, bool first_plan = false)
     }
     B_CK(cudaEventRecord(b->sev1, b->stream));
     launches += (any_be ? 1 : 0) + (any_fe ? 1 : 0);
-    for (int i = 0; i < b->n; ++i) {
-        sdd_problem* p = b->probs[i];
-        const size_t bytes = (size_t)p->prm.nx * p->prm.ny * 8;
-        B_CK(cudaMemcpyAsync(p->x, p->xn, bytes, cudaMemcpyDeviceToDevice, b->stream));
-        B_CK(cudaMemcpyAsync(p->y, p->yn, bytes, cudaMemcpyDeviceToDevice, b->stream));
-    }
+    B_CK(launch_copy_back_batch(b->rec_dev, b->blk_off_dev, b->n, b->total_blocks, b->stream));
+    launches += 1;
     b->launches_per_step = launches;
     return SDD_OK;
 }
@@ -387,10 +389,11 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
     ALLOC(b->task_counter, 16); ALLOC(b->slots, M * kSlotsPerNode * sizeof(TaskSlot));
     ALLOC(b->mcprob_dev, rec * n); ALLOC(b->solve_dev, sizeof(SolveParams) * n); ALLOC(b->t_dev, 8 * n);
     ALLOC(b->sub_off_dev, 4 * (n + 1));
+    ALLOC(b->rec_dev, sizeof(BatchRec) * n); ALLOC(b->blk_off_dev, 4 * (n + 1));
     ALLOC(b->order_dev, sizeof(int2) * (size_t)(b->total_subs > 0 ? b->total_subs : 1));
     if (sampled_any) ALLOC(b->node_role, M * 4);
     HALLOC(b->mcprob_host, rec * n); HALLOC(b->solve_host, sizeof(SolveParams) * n); HALLOC(b->t_host, 8 * n);
-    HALLOC(b->h_n_active, 32);
+    HALLOC(b->h_n_active, 32); HALLOC(b->rec_host, sizeof(BatchRec) * n);
 #undef ALLOC
 #undef HALLOC
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev0);
@@ -403,6 +406,15 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
         e = cudaMemcpy(b->node_prob, node_prob.data(), 4 * (size_t)b->M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->sub_off_dev, b->sub_off.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        std::vector<int32_t> blk_off(1, 0);
+        for (int i = 0; i < n; ++i) {
+            blk_off.push_back(blk_off.back() + batch_blocks((long)problems[i]->prm.nx * problems[i]->prm.ny));
+            b->any_moving = b->any_moving || (problems[i]->prm.moving_boundary && !problems[i]->prm.periodic);
+        }
+        b->total_blocks = blk_off.back();
+        e = cudaMemcpy(b->blk_off_dev, blk_off.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && b->total_subs > 0) {
         // longest-first: subdomains by interior size, descending (ties in problem, subdomain order)
         std::vector<std::pair<int64_t, int2>> subs;

@@ -216,6 +216,16 @@ struct PrepParams {
     double* bnd_scratch;       // 2 (2 nx + 2 ny) doubles
 };
 
+// Per-problem record of a batch step's batched launches (monitor and packing, moving boundary,
+// estimator shifts, Dirichlet scatter, copy of the new mesh).
+struct BatchRec {
+    PrepParams prep;           // prep.x, prep.y: the current mesh (written by the copy-back)
+    const int2* nodes;         // the problem's interface nodes
+    int node_offset;           // global index of its node 0 in the batch's node arrays
+    double* xnew;              // the new mesh: rims in, interiors out
+    double* ynew;
+};
+
 struct SolveParams {
     int nx, ny, px, py, form;
     int scheme;                // 0 backward Euler, 1 forward Euler substeps
@@ -270,14 +280,16 @@ struct SolveItem {
 // kCoopWidth to a cluster.  Empty when no subdomain is cooperative (the one-CTA kernels serve).
 std::vector<SolveItem> solve_items(const std::vector<std::pair<int64_t, int2>>& subs);
 
-// Multigrid hierarchy of an n x m subdomain interior: levels while both sizes stay odd and
-// >= 3 (n -> (n-1)/2), and the bytes of its per-level arrays (x, b, t pairs; faces; identity).
+// Multigrid hierarchy of an n x m subdomain interior: the coarse grid keeps the nodes of odd
+// index, (n - 1) / 2 of them for odd n and n / 2 for even n (then the last coarse node lies one
+// fine spacing from the rim); levels while both sizes are >= 3.
+__host__ __device__ inline int mg_coarse(int n) { return (n & 1) ? (n - 1) / 2 : n / 2; }
 __host__ __device__ inline int mg_levels(int n, int m)
 {
     int l = 1;
-    while (n >= 3 && m >= 3 && (n & 1) && (m & 1) && l < 16) {
-        n = (n - 1) / 2;
-        m = (m - 1) / 2;
+    while (n >= 3 && m >= 3 && l < 16) {
+        n = mg_coarse(n);
+        m = mg_coarse(m);
         ++l;
     }
     return l;
@@ -291,8 +303,8 @@ __host__ __device__ inline size_t mg_bytes(int n, int m, size_t real_bytes)
         const size_t nn = (size_t)n * m;
         total += 3 * mg_align(nn * 2 * real_bytes) + mg_align((size_t)(n + 1) * m * real_bytes) +
                  mg_align((size_t)n * (m + 1) * real_bytes) + mg_align(nn * real_bytes);
-        n = (n - 1) / 2;
-        m = (m - 1) / 2;
+        n = mg_coarse(n);
+        m = mg_coarse(m);
     }
     return total;
 }
@@ -330,6 +342,17 @@ cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const
                           double* est, double* se, cudaStream_t s);
 cudaError_t launch_solve(const SolveParams& P, bool fp64_inner, cudaStream_t s);
 cudaError_t launch_faces(const SolveParams& P, bool fp64_inner, cudaStream_t s);
+// Batched launches of a batch step (blk_off: per-problem block offsets of grid-sized work, n + 1
+// entries, blocks of 256 threads as batch_blocks gives them; node work over the concatenated nodes).
+int batch_blocks(long n_nodes);
+cudaError_t launch_prep_batch(const BatchRec* R, const int32_t* blk_off, int n, int total_blocks, bool fp64,
+                              bool any_moving, cudaStream_t s);
+cudaError_t launch_shift_batch(const BatchRec* R, const int32_t* node_prob, int M, double* shift, cudaStream_t s);
+cudaError_t launch_scatter_batch(const BatchRec* R, const int32_t* blk_off, int n, int total_blocks,
+                                 const int32_t* node_prob, int M, const double* est, cudaStream_t s);
+cudaError_t launch_copy_back_batch(const BatchRec* R, const int32_t* blk_off, int n, int total_blocks, cudaStream_t s);
+cudaError_t launch_faces_batch(const SolveParams* probs, const int32_t* blk_off, int n, int total_blocks,
+                               bool fp64_inner, cudaStream_t s);
 // order (nullable): (problem, subdomain) of each CTA
 cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off, int n, int total_subs,
                                bool fp64_inner, cudaStream_t s, bool any_be = true, bool any_fe = false,

@@ -66,11 +66,12 @@ __device__ double monitor_value(const PrepParams& P, double x, double y, double 
     return w;
 }
 
-__global__ void prep_omega_kernel(const PrepParams P)
+// Monitor on the current mesh at every node (the body of one block of blocks nb).
+__device__ __forceinline__ void prep_omega_body(const PrepParams& P, int blk, int nb)
 {
     const int n = P.nx * P.ny;
     const double t = P.t_dev ? *P.t_dev : P.t;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+    for (int id = blk * blockDim.x + threadIdx.x; id < n; id += nb * blockDim.x) {
         const int i = id % P.nx, j = id / P.nx;
         const int ci = P.periodic ? i % (P.nx - 1) : i;
         const int cj = P.periodic ? j % (P.ny - 1) : j;
@@ -78,6 +79,8 @@ __global__ void prep_omega_kernel(const PrepParams P)
         P.om64[id] = P.kind == 0 ? P.omega_in[c] : monitor_value(P, P.x[c], P.y[c], t);
     }
 }
+
+__global__ void prep_omega_kernel(const PrepParams P) { prep_omega_body(P, blockIdx.x, gridDim.x); }
 
 // d f / d s along one grid line at index i of n nodes: central differences in the interior,
 // one-sided second order at Dirichlet ends, wrapped when periodic; factor c = (n - 1) / 2.
@@ -101,12 +104,12 @@ __device__ __forceinline__ double fd_line(const double* f, long stride, int i, i
 }
 
 template <typename T>
-__global__ void prep_pack_kernel(const PrepParams P)
+__device__ __forceinline__ void prep_pack_body(const PrepParams& P, int blk, int nb)
 {
     const int n = P.nx * P.ny;
     Mon4<T>* mon = static_cast<Mon4<T>*>(P.mon);
     Disp2<T>* disp = static_cast<Disp2<T>*>(P.disp);
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+    for (int id = blk * blockDim.x + threadIdx.x; id < n; id += nb * blockDim.x) {
         const int i = id % P.nx, j = id / P.nx;
         const double w = P.om64[id];
         const double wx = fd_line(P.om64 + (long)j * P.nx, 1, i, P.nx, P.periodic);
@@ -128,6 +131,9 @@ __global__ void prep_pack_kernel(const PrepParams P)
     }
 }
 
+template <typename T>
+__global__ void prep_pack_kernel(const PrepParams P) { prep_pack_body<T>(P, blockIdx.x, gridDim.x); }
+
 __global__ void shift_kernel(const int2* nodes, int M, int nx, const double* x, const double* y,
                              double* shift)
 {
@@ -138,11 +144,11 @@ __global__ void shift_kernel(const int2* nodes, int M, int nx, const double* x, 
     shift[2 * m + 1] = y[(long)ij.y * nx + ij.x];
 }
 
-__global__ void scatter_boundary_kernel(int nx, int ny, double Lx, double Ly, double* xnew,
-                                        double* ynew, const double* bnd)
+__device__ __forceinline__ void scatter_boundary_body(int nx, int ny, double Lx, double Ly, double* xnew,
+                                                      double* ynew, const double* bnd, int blk, int nb)
 {
     const int n = nx * ny;
-    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < n; id += gridDim.x * blockDim.x) {
+    for (int id = blk * blockDim.x + threadIdx.x; id < n; id += nb * blockDim.x) {
         const int i = id % nx, j = id / nx;
         if (i == 0 || j == 0 || i == nx - 1 || j == ny - 1) {
             double vx = Lx * ((double)i / (double)(nx - 1));
@@ -159,6 +165,12 @@ __global__ void scatter_boundary_kernel(int nx, int ny, double Lx, double Ly, do
     }
 }
 
+__global__ void scatter_boundary_kernel(int nx, int ny, double Lx, double Ly, double* xnew,
+                                        double* ynew, const double* bnd)
+{
+    scatter_boundary_body(nx, ny, Lx, Ly, xnew, ynew, bnd, blockIdx.x, gridDim.x);
+}
+
 // One backward-Euler step of the 1-D generator along each side of a Dirichlet domain (Sec. 2):
 // side s (thread s) carries the tangential coordinate b_k at its n nodes -- x along eta = 0
 // (s = 0) and eta = 1 (s = 1), y along xi = 0 (s = 2) and xi = 1 (s = 3) -- and solves
@@ -167,7 +179,7 @@ __global__ void scatter_boundary_kernel(int nx, int ny, double Lx, double Ly, do
 // with the corner values fixed, by the tridiagonal (Thomas) sweeps; the system is a
 // diagonally dominant M-matrix.
 template <typename T>
-__global__ void boundary_kernel(const PrepParams P)
+__device__ __forceinline__ void boundary_body(const PrepParams& P)
 {
     const int s = threadIdx.x;
     if (s >= 4) return;
@@ -204,12 +216,13 @@ __global__ void boundary_kernel(const PrepParams P)
     for (int k = 0; k < n; ++k) bt[k] = (T)b[k];
 }
 
-__global__ void scatter_iface_kernel(int nx, int ny, int periodic, double Lx, double Ly,
-                                     const int2* nodes, int M, const double* est, double* xnew,
-                                     double* ynew)
+template <typename T>
+__global__ void boundary_kernel(const PrepParams P) { boundary_body<T>(P); }
+
+__device__ __forceinline__ void scatter_iface_one(int nx, int ny, int periodic, double Lx, double Ly,
+                                                  const int2* nodes, int m, const double* est, double* xnew,
+                                                  double* ynew)
 {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
     const int2 ij = nodes[m];
     const double vx = est[2 * m], vy = est[2 * m + 1];
     const long id = (long)ij.y * nx + ij.x;
@@ -230,6 +243,97 @@ __global__ void scatter_iface_kernel(int nx, int ny, int periodic, double Lx, do
             xnew[w] = vx + Lx;
             ynew[w] = vy + Ly;
         }
+    }
+}
+
+__global__ void scatter_iface_kernel(int nx, int ny, int periodic, double Lx, double Ly,
+                                     const int2* nodes, int M, const double* est, double* xnew,
+                                     double* ynew)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    scatter_iface_one(nx, ny, periodic, Lx, Ly, nodes, m, est, xnew, ynew);
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched forms: one launch over the problems of a batch.  Grid-sized work gives problem i the
+// blocks blk_off[i] .. blk_off[i + 1] - 1 (each problem its own block count, as its single-problem
+// launch would have); node work runs over the batch's concatenated nodes.  Every node computes
+// what the single-problem kernels compute for it.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int batch_problem_of_block(const int32_t* blk_off, int n, int b)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_off[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void prep_omega_batch_kernel(const BatchRec* R, const int32_t* blk_off, int n)
+{
+    const int i = batch_problem_of_block(blk_off, n, blockIdx.x);
+    const int blk = blockIdx.x - blk_off[i], nb = blk_off[i + 1] - blk_off[i];
+    if (blk == 0 && threadIdx.x == 0 && R[i].prep.bad) *R[i].prep.bad = 0;  // before the pack launch
+    prep_omega_body(R[i].prep, blk, nb);
+}
+
+template <typename T>
+__global__ void prep_pack_batch_kernel(const BatchRec* R, const int32_t* blk_off, int n)
+{
+    const int i = batch_problem_of_block(blk_off, n, blockIdx.x);
+    prep_pack_body<T>(R[i].prep, blockIdx.x - blk_off[i], blk_off[i + 1] - blk_off[i]);
+}
+
+template <typename T>
+__global__ void boundary_batch_kernel(const BatchRec* R)
+{
+    const PrepParams& P = R[blockIdx.x].prep;
+    if (P.moving_boundary && !P.periodic) boundary_body<T>(P);
+}
+
+__global__ void shift_batch_kernel(const BatchRec* R, const int32_t* node_prob, int M, double* shift)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M) return;
+    const BatchRec& r = R[node_prob[g]];
+    const int2 ij = r.nodes[g - r.node_offset];
+    shift[2 * g] = r.prep.x[(long)ij.y * r.prep.nx + ij.x];
+    shift[2 * g + 1] = r.prep.y[(long)ij.y * r.prep.nx + ij.x];
+}
+
+__global__ void scatter_boundary_batch_kernel(const BatchRec* R, const int32_t* blk_off, int n)
+{
+    const int i = batch_problem_of_block(blk_off, n, blockIdx.x);
+    const BatchRec& r = R[i];
+    if (r.prep.periodic) return;
+    scatter_boundary_body(r.prep.nx, r.prep.ny, r.prep.Lx, r.prep.Ly, r.xnew, r.ynew,
+                          r.prep.moving_boundary ? r.prep.bnd64 : nullptr, blockIdx.x - blk_off[i],
+                          blk_off[i + 1] - blk_off[i]);
+}
+
+__global__ void scatter_iface_batch_kernel(const BatchRec* R, const int32_t* node_prob, int M, const double* est)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M) return;
+    const BatchRec& r = R[node_prob[g]];
+    scatter_iface_one(r.prep.nx, r.prep.ny, r.prep.periodic, r.prep.Lx, r.prep.Ly, r.nodes, g - r.node_offset,
+                      est + 2 * (size_t)r.node_offset, r.xnew, r.ynew);
+}
+
+// x <- x^{n+1}, y <- y^{n+1} of every problem (the step's last launch)
+__global__ void copy_back_batch_kernel(const BatchRec* R, const int32_t* blk_off, int n)
+{
+    const int i = batch_problem_of_block(blk_off, n, blockIdx.x);
+    const BatchRec& r = R[i];
+    const int nb = blk_off[i + 1] - blk_off[i];
+    const long N = (long)r.prep.nx * r.prep.ny;
+    double* x = const_cast<double*>(r.prep.x);
+    double* y = const_cast<double*>(r.prep.y);
+    for (long id = (long)(blockIdx.x - blk_off[i]) * blockDim.x + threadIdx.x; id < N; id += (long)nb * blockDim.x) {
+        x[id] = r.xnew[id];
+        y[id] = r.ynew[id];
     }
 }
 
@@ -321,6 +425,50 @@ cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, c
     if (M > 0)
         scatter_iface_kernel<<<blocks_for(M, 256), 256, 0, s>>>(nx, ny, periodic, Lx, Ly, nodes, M, est,
                                                                 xnew, ynew);
+    return cudaGetLastError();
+}
+
+}  // namespace sdd
+
+namespace sdd {
+
+int batch_blocks(long n_nodes) { return blocks_for(n_nodes, 256); }
+
+cudaError_t launch_prep_batch(const BatchRec* R, const int32_t* blk_off, int n, int total_blocks, bool fp64,
+                              bool any_moving, cudaStream_t s)
+{
+    prep_omega_batch_kernel<<<total_blocks, 256, 0, s>>>(R, blk_off, n);
+    if (fp64)
+        prep_pack_batch_kernel<double><<<total_blocks, 256, 0, s>>>(R, blk_off, n);
+    else
+        prep_pack_batch_kernel<float><<<total_blocks, 256, 0, s>>>(R, blk_off, n);
+    if (any_moving) {
+        if (fp64)
+            boundary_batch_kernel<double><<<n, 32, 0, s>>>(R);
+        else
+            boundary_batch_kernel<float><<<n, 32, 0, s>>>(R);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shift_batch(const BatchRec* R, const int32_t* node_prob, int M, double* shift, cudaStream_t s)
+{
+    if (M <= 0) return cudaSuccess;
+    shift_batch_kernel<<<blocks_for(M, 256), 256, 0, s>>>(R, node_prob, M, shift);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_batch(const BatchRec* R, const int32_t* blk_off, int n, int total_blocks,
+                                 const int32_t* node_prob, int M, const double* est, cudaStream_t s)
+{
+    scatter_boundary_batch_kernel<<<total_blocks, 256, 0, s>>>(R, blk_off, n);
+    if (M > 0) scatter_iface_batch_kernel<<<blocks_for(M, 256), 256, 0, s>>>(R, node_prob, M, est);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_back_batch(const BatchRec* R, const int32_t* blk_off, int n, int total_blocks, cudaStream_t s)
+{
+    copy_back_batch_kernel<<<total_blocks, 256, 0, s>>>(R, blk_off, n);
     return cudaGetLastError();
 }
 

@@ -12,8 +12,9 @@
 // conjugate gradients in the inner precision (FP32 for the FP32 modes, FP64 otherwise),
 // preconditioned by one symmetric multigrid V-cycle, then x += e (iterative refinement).
 //
-// Multigrid: the subdomain's interior (n x m nodes, n and m odd) coarsens to the nodes of odd
-// index, ((n-1)/2) x ((m-1)/2), for as long as both stay odd and >= 3.  Coarse face
+// Multigrid: the subdomain's interior (n x m nodes) coarsens to the nodes of odd index,
+// (n-1)/2 of them for odd n and n/2 for even n (the last coarse node then lies one fine spacing
+// from the rim), for as long as both sizes stay >= 3.  Coarse face
 // coefficients are a quarter of the series combination 2ab/(a+b) of the two fine faces a
 // coarse face spans (the operator rediscretised at twice the spacing); the identity term is
 // injected.  Red-black Gauss-Seidel smoothing (red-black before, black-red after: a symmetric
@@ -141,13 +142,13 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* sh)
     __syncthreads();
 }
 
-__global__ void faces_kernel(const SolveParams P, int inner_fp64)
+__device__ __forceinline__ void faces_body(const SolveParams& P, int inner_fp64, int blk, int nb)
 {
     const int nx = P.nx, ny = P.ny;
     const double hx2 = (double)(nx - 1) * (double)(nx - 1);
     const double hy2 = (double)(ny - 1) * (double)(ny - 1);
     const long n = (long)nx * ny;
-    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < n; id += (long)gridDim.x * blockDim.x) {
+    for (long id = blk * (long)blockDim.x + threadIdx.x; id < n; id += (long)nb * blockDim.x) {
         const int i = (int)(id % nx), j = (int)(id / nx);
         const double w = P.om64[id];
         double e = 0.0, no = 0.0;
@@ -163,6 +164,19 @@ __global__ void faces_kernel(const SolveParams P, int inner_fp64)
             static_cast<float*>(P.cn)[id] = (float)no;
         }
     }
+}
+
+__global__ void faces_kernel(const SolveParams P, int inner_fp64) { faces_body(P, inner_fp64, blockIdx.x, gridDim.x); }
+
+// Face coefficients of every problem of a batch in one launch (problem i: blocks blk_off[i] ..).
+__global__ void faces_batch_kernel(const SolveParams* probs, const int32_t* blk_off, int n, int inner_fp64)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (blk_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    faces_body(probs[lo], inner_fp64, blockIdx.x - blk_off[lo], blk_off[lo + 1] - blk_off[lo]);
 }
 
 
@@ -195,8 +209,8 @@ __device__ __forceinline__ MgLevel<TI> mg_level(void* base, int nx0, int ny0, in
         L.cn = reinterpret_cast<TI*>(ptr); ptr += mg_align((size_t)nx * (ny + 1) * sizeof(TI));
         L.d = reinterpret_cast<TI*>(ptr); ptr += mg_align(nn * sizeof(TI));
         if (k == l) return L;
-        nx = (nx - 1) / 2;
-        ny = (ny - 1) / 2;
+        nx = mg_coarse(nx);
+        ny = mg_coarse(ny);
     }
 }
 
@@ -284,6 +298,9 @@ __device__ __forceinline__ void mg_restrict(const Team<CW>& tm, const MgLevel<TI
             for (int dj = -1; dj <= 1; ++dj)
 #pragma unroll
                 for (int di = -1; di <= 1; ++di) {
+                    // an even fine size puts the last coarse node's outer neighbours on the rim,
+                    // whose residual is zero
+                    if (i + di >= F.nx || j + dj >= F.ny) continue;
                     const TI w = (TI)((di == 0 ? 2 : 1) * (dj == 0 ? 2 : 1)) * (TI)0.0625;
                     const Pair<TI> tv = F.t[(j + dj) * F.nx + (i + di)];
                     acc.x += w * tv.x;
@@ -346,14 +363,21 @@ __device__ void mg_setup(const Team<CW>& tm, const SolveParams& P, int i0, int j
     tm.sync();
     for (int l = 0; l + 1 < levels; ++l) {
         const MgLevel<TI> F = mg_level<TI>(P.mg, nx0, ny0, l), C = mg_level<TI>(P.mg, nx0, ny0, l + 1);
+        // a coarse face spans two fine faces (a quarter of their series combination), except the
+        // face to the rim after an even fine size, which spans one fine face at one fine spacing
+        // from the rim: half of it
         for (int k = tm.tid(); k < (C.nx + 1) * C.ny; k += tm.nthreads()) {
             const int f = k % (C.nx + 1), J = k / (C.nx + 1);
-            const TI a = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f], b = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f + 1];
+            const TI a = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f];
+            if (2 * f + 1 > F.nx) { C.ce[k] = (TI)0.5 * a; continue; }
+            const TI b = F.ce[(2 * J + 1) * (F.nx + 1) + 2 * f + 1];
             C.ce[k] = (TI)0.5 * a * b / (a + b);
         }
         for (int k = tm.tid(); k < C.nx * (C.ny + 1); k += tm.nthreads()) {
             const int I = k % C.nx, g = k / C.nx;
-            const TI a = F.cn[(2 * g) * F.nx + 2 * I + 1], b = F.cn[(2 * g + 1) * F.nx + 2 * I + 1];
+            const TI a = F.cn[(2 * g) * F.nx + 2 * I + 1];
+            if (2 * g + 1 > F.ny) { C.cn[k] = (TI)0.5 * a; continue; }
+            const TI b = F.cn[(2 * g + 1) * F.nx + 2 * I + 1];
             C.cn[k] = (TI)0.5 * a * b / (a + b);
         }
         for (int k = tm.tid(); k < C.nx * C.ny; k += tm.nthreads()) {
@@ -870,6 +894,13 @@ cudaError_t launch_solve_batch_items(const SolveParams* probs, const SolveItem* 
         solve_batch_items_kernel<double><<<n_items, kSolveThreads, 0, s>>>(probs, items);
     else
         solve_batch_items_kernel<float><<<n_items, kSolveThreads, 0, s>>>(probs, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_faces_batch(const SolveParams* probs, const int32_t* blk_off, int n, int total_blocks,
+                               bool fp64_inner, cudaStream_t s)
+{
+    faces_batch_kernel<<<total_blocks, 256, 0, s>>>(probs, blk_off, n, fp64_inner ? 1 : 0);
     return cudaGetLastError();
 }
 
