@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default path-kernel launch configuration instead of running the autotuner "
                          "(sdd_tune / sdd_batch_tune_mc) before the warm-up steps")
+    ap.add_argument("--mc-config", default="",
+                    help="fixed path-kernel launch configuration 'threads_per_block,blocks_per_sm,paths_per_task' "
+                         "(0 keeps a field's default) in place of the autotuner")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -375,7 +378,11 @@ def run_ours(args):
         h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
         # launch configuration: tuned once on the first problem's first round (outside any timed
         # region), then given to every later problem so both timed runs do the same work
-        if not args.no_tune and not tuned:
+        if args.mc_config and not tuned:
+            _, bps, tp = (int(v) for v in args.mc_config.split(","))
+            h.set_mc_config(blocks_per_sm=bps, paths_per_task=tp)
+            tuned.update(h.mc_config())
+        elif not args.no_tune and not tuned:
             tuned.update(h.tune_mc(True))
         elif tuned:
             h.set_mc_config(blocks_per_sm=tuned["blocks_per_sm"], paths_per_task=tuned["paths_per_task"])
@@ -555,7 +562,12 @@ def run_mix(args):
     b = S.SddBatch(hs, stream=stream, use_graph=True)
     # launch configuration timed on the first round: block size and blocks per SM change no
     # result; the task size changes the grouping of the sums (and is set on every problem)
-    cfg = b.mc_config() if args.no_tune else b.tune_mc(True)
+    if args.mc_config:
+        tpb, bps, tp = (int(v) for v in args.mc_config.split(","))
+        b.set_mc_config(threads_per_block=tpb, blocks_per_sm=bps, paths_per_task=tp)
+        cfg = b.mc_config()
+    else:
+        cfg = b.mc_config() if args.no_tune else b.tune_mc(True)
     for _ in range(args.warmup):
         b.step()
     stream.synchronize()

@@ -399,12 +399,18 @@ __device__ __noinline__ void mg_vcycle(const Team<CW> tm, void* base, int nx0, i
         mg_restrict(tm, F, mg_level<TI>(base, nx0, ny0, l + 1));
     }
     const MgLevel<TI> Lc = mg_level<TI>(base, nx0, ny0, levels - 1);
-    for (int s = 0; s < kCoarseSweeps; ++s) {
-        if (s == 0) mg_first_sweep(tm, Lc);
-        else mg_half_sweep(tm, Lc, 0);
-        mg_half_sweep(tm, Lc, 1);
-        mg_half_sweep(tm, Lc, 1);
-        mg_half_sweep(tm, Lc, 0);
+    if (Lc.nx * Lc.ny == 1) {
+        // one node, no neighbours: the first half-sweep solves it exactly (b / diag), and every
+        // further sweep would recompute the same bits
+        mg_first_sweep(tm, Lc);
+    } else {
+        for (int s = 0; s < kCoarseSweeps; ++s) {
+            if (s == 0) mg_first_sweep(tm, Lc);
+            else mg_half_sweep(tm, Lc, 0);
+            mg_half_sweep(tm, Lc, 1);
+            mg_half_sweep(tm, Lc, 1);
+            mg_half_sweep(tm, Lc, 0);
+        }
     }
     for (int l = levels - 2; l >= 0; --l) {
         const MgLevel<TI> F = mg_level<TI>(base, nx0, ny0, l);
