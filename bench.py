@@ -48,7 +48,7 @@ L2_FLUSH_BYTES = 256 << 20
 # capture of the current kernel on a full round (2^19 paths per node): the cold fill of the packed
 # monitor and mesh records (~1.6 MB of FP32 data per 257x257 grid), which does not grow with the
 # number of paths.
-MC_TRAFFIC_BYTES_PER_LAUNCH = 1.96e6
+MC_TRAFFIC_BYTES_PER_LAUNCH = 1.66e6
 
 
 def parse():
