@@ -596,7 +596,7 @@ def run_mix(args):
              "launch_config": cfg,
              "solve_iters_max": st["solve_iters_max"], "solve_outer_max": st["solve_outer_max"],
              "solve_rel_residual": st["solve_rel_residual"],
-             "solve_roofline": {"bound": "hbm", "kernel": "solve_batch_items_kernel (clusters of 2 CTAs for subdomains of >= 32768 unknowns) or solve_batch_kernel", "ms": solve_ms,
+             "solve_roofline": {"bound": "hbm", "kernel": "solve_batch_items_kernel (512-thread CTAs; clusters of 4 for subdomains of >= 32768 unknowns) or solve_batch_kernel", "ms": solve_ms,
                                 "unknowns": U, "algorithmic_bytes": solve_bytes, "achieved": solve_gbs,
                                 "peak": peak, "unit": "GB/s", "peak_basis": basis,
                                 "frac": solve_gbs / peak if solve_gbs else None}}

@@ -260,14 +260,8 @@ __host__ __device__ inline int split_line(int I, int n, int P)
 
 // Large subdomains are solved by a cluster of kCoopWidth CTAs (sdd_solve.cu): those with at
 // least kCoopUnknowns interior unknowns.
-#ifndef SDD_SOLVE_COOP
-#define SDD_SOLVE_COOP 2
-#endif
-#ifndef SDD_SOLVE_COOP_MIN
-#define SDD_SOLVE_COOP_MIN 32768
-#endif
-constexpr int kCoopWidth = SDD_SOLVE_COOP;
-constexpr int64_t kCoopUnknowns = SDD_SOLVE_COOP_MIN;
+constexpr int kCoopWidth = 4;
+constexpr int64_t kCoopUnknowns = 32768;
 
 // One CTA's work in a cooperative solve launch: subdomain `sub` of problem `prob`, solved by a
 // team of `width` CTAs (kCoopWidth: this CTA's cluster; 1: this CTA alone; 0: idle).

@@ -7,7 +7,8 @@
 //   d_P = 1 (tau x_t = div(omega grad x))  or  omega_P (the paper's Eq. 4 form),
 // a symmetric positive-definite system, for both mesh components at once.
 //
-// One CTA per subdomain.  Outer loop in FP64: residual b - A x of the current iterate (rims
+// One CTA of 512 threads per subdomain, two per SM, or a cluster of CTAs for a large subdomain
+// (solve_item).  Outer loop in FP64: residual b - A x of the current iterate (rims
 // included), stop when ||r||_2 <= rtol ||b||_2 for both components.  Inner solve A e = r by
 // conjugate gradients in the inner precision (FP32 for the FP32 modes, FP64 otherwise),
 // preconditioned by one symmetric multigrid V-cycle, then x += e (iterative refinement).
@@ -31,7 +32,12 @@ namespace sdd {
 
 namespace {
 
-constexpr int kSolveThreads = 1024;  // one CTA per SM: a large subdomain gets the whole SM
+// 512 threads per CTA, two CTAs per SM (64 registers each): a subdomain gets 16 warps, and an SM
+// keeps two subdomains' passes in flight; a large subdomain gets a cluster of kCoopWidth CTAs.
+// Measured on the 64-problem mix: 10.9-12.4 ms per batched solve, against 15.4-17.3 ms with one
+// 1024-thread CTA per SM (and clusters of 2) and 12.1-13.7 ms with 256-thread CTAs.
+constexpr int kSolveThreads = 512;
+constexpr int kSolveMinBlocks = 1024 / kSolveThreads;
 constexpr int kMaxOuter = 12;
 constexpr int kCoarseSweeps = 4;  // symmetric Gauss-Seidel sweeps on the coarsest level
 constexpr unsigned kFull = 0xffffffffu;
@@ -740,7 +746,7 @@ template <typename TI, int CW>
 __device__ SDD_SOLVE_SUB_ATTR void solve_sub(const Team<CW> tm, const SolveParams& P, int sub, double* sh);
 
 template <typename TI>
-__global__ void __launch_bounds__(kSolveThreads) solve_kernel(const __grid_constant__ SolveParams P)
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) solve_kernel(const __grid_constant__ SolveParams P)
 {
     __shared__ double sh[32 * 8 + 8];
     solve_sub<TI, 1>(Team<1>{0}, P, blockIdx.x, sh);
@@ -785,12 +791,10 @@ __global__ void __launch_bounds__(kSolveThreads) fe_batch_kernel(const SolvePara
     if (sp.scheme == 1) fe_body(sp, sub, sh);
 }
 
-// Batched: CTA b solves the subdomain batch_lookup assigns it.  One CTA of 1024 threads per SM
-// (64 registers): the launch lasts as long as its largest subdomains, and their sweeps are bound
-// by one SM's load bandwidth and latency, so each CTA gets a whole SM (measured on the 64-problem
-// mix: 17.5 ms, against 21.2 ms with two CTAs of 512 threads and 31 ms with four of 256).
+// Batched: CTA b solves the subdomain batch_lookup assigns it (launches without large subdomains;
+// with them, solve_batch_items_kernel below).
 template <typename TI>
-__global__ void __launch_bounds__(kSolveThreads, 1) solve_batch_kernel(const SolveParams* probs,
+__global__ void __launch_bounds__(kSolveThreads, kSolveMinBlocks) solve_batch_kernel(const SolveParams* probs,
                                                                        const int32_t* sub_off, const int2* order,
                                                                        int n)
 {
@@ -814,8 +818,8 @@ __device__ SDD_SOLVE_SUB_ATTR void solve_sub(const Team<CW> tm, const SolveParam
 }
 
 // Subdomains with at least kCoopUnknowns interior unknowns are solved by the kCoopWidth CTAs of
-// a thread-block cluster, each on its own SM (1024 threads, the whole register file): rows,
-// loops and reductions are spread over the cluster and every pass ends in a cluster barrier.  The
+// a thread-block cluster (2048 threads on at least two SMs): rows, loops and reductions are spread
+// over the cluster and every pass ends in a cluster barrier.  The
 // team width is a function of the subdomain's size alone, so a subdomain gives the same bits in a
 // single-problem launch, a batch and a served request.
 template <typename TI>
@@ -833,7 +837,7 @@ __device__ __forceinline__ void solve_item(const SolveParams& sp, const SolveIte
 // item fills a whole cluster (its kCoopWidth entries are the same); otherwise each CTA of the
 // cluster solves its own subdomain, or none (width 0).
 template <typename TI>
-__global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThreads, 1)
+__global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThreads, kSolveMinBlocks)
     solve_items_kernel(const __grid_constant__ SolveParams P, const SolveItem* items)
 {
     __shared__ double sh[32 * 8 + 8];
@@ -841,7 +845,7 @@ __global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThrea
 }
 
 template <typename TI>
-__global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThreads, 1)
+__global__ void __cluster_dims__(kCoopWidth, 1, 1) __launch_bounds__(kSolveThreads, kSolveMinBlocks)
     solve_batch_items_kernel(const SolveParams* probs, const SolveItem* items)
 {
     __shared__ double sh[32 * 8 + 8];
