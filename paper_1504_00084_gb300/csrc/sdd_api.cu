@@ -265,15 +265,15 @@ McParams<T> mc_params(const sdd_problem* p)
 }
 
 sdd_status launch_mc_round(sdd_problem* p, bool debug, double* dval, int32_t* dsteps, int8_t* dside,
-                           int64_t dp0)
+                           int64_t dp0, int64_t dn)
 {
     if (p->fp64) {
         McParams<double> P = mc_params<double>(p);
-        P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0;
+        P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0; P.dbg_n = dn;
         SDD_CK(launch_mc<double>(P, p->acc_mode, debug, false, p->mc_grid, p->stream));
     } else {
         McParams<float> P = mc_params<float>(p);
-        P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0;
+        P.dbg_val = dval; P.dbg_steps = dsteps; P.dbg_side = dside; P.dbg_p0 = dp0; P.dbg_n = dn;
         SDD_CK(launch_mc<float>(P, p->acc_mode, debug, false, p->mc_grid, p->stream));
     }
     return SDD_OK;
@@ -288,7 +288,7 @@ sdd_status timed_mc_round(sdd_problem* p, int slot)
         p->ev.push_back(e);
     }
     SDD_CK(cudaEventRecord(p->ev[2 * slot], p->stream));
-    SDD_TRY(launch_mc_round(p, false, nullptr, nullptr, nullptr, 0));
+    SDD_TRY(launch_mc_round(p, false, nullptr, nullptr, nullptr, 0, 0));
     SDD_CK(cudaEventRecord(p->ev[2 * slot + 1], p->stream));
     return SDD_OK;
 }
@@ -1143,7 +1143,7 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
         ck(cudaMemcpyAsync(p->n_active, &h_act, 4, cudaMemcpyHostToDevice, p->stream));
         ck(cudaMemcpyAsync(p->task_counter, &h_zero, 4, cudaMemcpyHostToDevice, p->stream));
     }
-    if (s == SDD_OK) s = launch_mc_round(p, true, dval, dst, dsd, p_begin);
+    if (s == SDD_OK) s = launch_mc_round(p, true, dval, dst, dsd, p_begin, n_paths);
     if (s == SDD_OK) s = copy_out(p, val_xy, dval, (size_t)n_paths * 16);
     if (s == SDD_OK) s = copy_out(p, exit_step, dst, (size_t)n_paths * 4);
     if (s == SDD_OK) s = copy_out(p, exit_side, dsd, (size_t)n_paths);

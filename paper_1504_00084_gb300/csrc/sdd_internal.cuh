@@ -134,8 +134,21 @@ template <typename T> struct McProblem {
     int32_t node_offset;       // global index of the problem's node 0 in the launch's node arrays
     uint32_t rk[20];           // Philox round keys of (key0, key1) (single-problem launches)
     uint32_t cell_bias;        // (nx + 1) * 0x4B000000 mod 2^32: see monitor_at
+    float gs[2];               // FP32 Dirichlet cell location: nx - 1, ny - 1 (see monitor_at)
+    float gc[2];               // and the clamp nx - 3/2, ny - 3/2
     const T* bnd;              // moving boundary: tangential boundary coordinates (null: identity)
 };
+
+// Grid constants of a problem record for the FP32 cell location (set_grid_consts).
+template <typename T>
+inline void set_grid_consts(McProblem<T>& R)
+{
+    R.cell_bias = (uint32_t)(R.nx + 1) * 0x4B000000u;
+    R.gs[0] = (float)(R.nx - 1);
+    R.gs[1] = (float)(R.ny - 1);
+    R.gc[0] = (float)(R.nx - 1) - 0.5f;
+    R.gc[1] = (float)(R.ny - 1) - 0.5f;
+}
 
 template <typename T> struct McParams {
     McProblem<T> prob;         // single-problem launches
@@ -155,7 +168,8 @@ template <typename T> struct McParams {
     double* dbg_val;
     int32_t* dbg_steps;
     int8_t* dbg_side;
-    int64_t dbg_p0;
+    int64_t dbg_p0;            // first recorded path index
+    int64_t dbg_n;             // recorded paths
 };
 
 struct PlanParams {

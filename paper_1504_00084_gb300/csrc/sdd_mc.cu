@@ -27,6 +27,11 @@
 // in task order.  No floating-point atomics: results are bitwise reproducible.
 #include <math.h>
 
+#include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
+
 #include "sdd_internal.cuh"
 
 namespace sdd {
@@ -106,25 +111,65 @@ __device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs)
     const int qint = __float_as_int(big);
     const float r = t - q;
     const float r2 = r * r;
-    float ps = 0x1.507834p-13f;                 // (pi/2)^9 / 9!
-    ps = fmaf(ps, r2, -0x1.32d2ccp-8f);         // -(pi/2)^7 / 7!
-    ps = fmaf(ps, r2, 0x1.466bc6p-4f);          // (pi/2)^5 / 5!
-    ps = fmaf(ps, r2, -0x1.4abbcep-1f);         // -(pi/2)^3 / 3!
-    ps = fmaf(ps, r2, 0x1.921fb6p+0f);          // pi/2
-    ps *= r;
-    float pc = -0x1.a6d1f2p-16f;                // -(pi/2)^10 / 10!
-    pc = fmaf(pc, r2, 0x1.e1f506p-11f);         // (pi/2)^8 / 8!
-    pc = fmaf(pc, r2, -0x1.55d3c8p-6f);         // -(pi/2)^6 / 6!
-    pc = fmaf(pc, r2, 0x1.03c1f0p-2f);          // (pi/2)^4 / 4!
-    pc = fmaf(pc, r2, -0x1.3bd3ccp+0f);         // -(pi/2)^2 / 2!
-    pc = fmaf(pc, r2, 1.0f);
-    const int qi = qint & 3;
-    float s_ = (qi & 1) ? pc : ps;
-    float c_ = (qi & 1) ? ps : pc;
-    if (qi & 2) s_ = -s_;           // quadrants 2, 3
-    if ((qi + 1) & 2) c_ = -c_;     // quadrants 1, 2
-    *sn = s_;
-    *cs = c_;
+    // the sine (x) and cosine (y) series side by side, one paired instruction per degree:
+    // coefficients (pi/2)^9/9!, -(pi/2)^10/10! down to pi/2, -(pi/2)^2/2!; then x r and y r2 + 1
+    float2 pp = __ffma2_rn(make_float2(0x1.507834p-13f, -0x1.a6d1f2p-16f), make_float2(r2, r2),
+                           make_float2(-0x1.32d2ccp-8f, 0x1.e1f506p-11f));
+    pp = __ffma2_rn(pp, make_float2(r2, r2), make_float2(0x1.466bc6p-4f, -0x1.55d3c8p-6f));
+    pp = __ffma2_rn(pp, make_float2(r2, r2), make_float2(-0x1.4abbcep-1f, 0x1.03c1f0p-2f));
+    pp = __ffma2_rn(pp, make_float2(r2, r2), make_float2(0x1.921fb6p+0f, -0x1.3bd3ccp+0f));
+    pp = __ffma2_rn(pp, make_float2(r, r2), make_float2(0.0f, 1.0f));
+    // quadrant q mod 4: odd quadrants swap sine and cosine; the sine is negative in quadrants
+    // 2, 3 (bit 1 of q), the cosine in quadrants 1, 2 (bit 1 of q + 1): set as the sign bit
+    const bool odd = qint & 1;
+    const float s_ = odd ? pp.y : pp.x;
+    const float c_ = odd ? pp.x : pp.y;
+    *sn = __int_as_float(__float_as_int(s_) ^ ((uint32_t)qint << 30 & 0x80000000u));
+    *cs = __int_as_float(__float_as_int(c_) ^ ((uint32_t)(qint + 1) << 30 & 0x80000000u));
+}
+
+// Square roots of two positive normal FP32 numbers (here -2 ln u1 >= 1.2e-7 and 2 q > 0): the
+// hardware reciprocal square root estimate r of a, then one Newton correction of y = a r,
+// y + (a - y^2) r / 2, with the residual a - y^2 formed exactly by the fused multiply-add
+// (Markstein's scheme for square roots).  The estimate's relative error near 2^-23 leaves the
+// correction's error far below half an ulp, so the result is the rounded square root except
+// where that lies within that error of a rounding boundary (checked against sqrtf over every
+// float in [2^-24, 2^8]).  No zero, infinity, NaN or subnormal handling: the arguments exclude them.
+__device__ __forceinline__ float2 sqrt_pos2(float2 a)
+{
+    float r0, r1;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r0) : "f"(a.x));
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r1) : "f"(a.y));
+    const float2 y = __fmul2_rn(a, make_float2(r0, r1));
+    const float2 h = __fmul2_rn(make_float2(r0, r1), make_float2(0.5f, 0.5f));
+    const float2 e = __ffma2_rn(make_float2(-y.x, -y.y), y, a);
+    return __ffma2_rn(e, h, y);
+}
+
+// Natural logarithm of a uniform u in [2^-24, 1) (the FP32 deviates of uniform_open): with
+// u = 2^e m, m in [sqrt(1/2), sqrt(2)) and f = m - 1 (exact), ln u = e ln 2 + ln(1 + f), and
+// ln(1 + f) = f + f^2 P(f) with P the degree-8 polynomial fitted to (ln(1 + f) - f) / f^2 on that
+// range (weighted least squares on Chebyshev nodes, coefficients rounded to FP32); e ln 2 is added
+// as e ln2_hi + (e ln2_lo + ...), ln2_hi = ln 2 rounded to FP32.  Checked over all 2^23 such
+// uniforms against the rounded FP64 logarithm: within 1 ulp, rounded correctly for 93 % of them.
+// No zero, negative, infinite or subnormal arguments (uniform_open makes none).
+__device__ __forceinline__ float log_unit(float u)
+{
+    const int i = __float_as_int(u);
+    const int e = (i - 0x3F3504F3) >> 23;                             // 0x3F3504F3: sqrt(1/2)
+    const float f = __int_as_float(i - (int)((uint32_t)e << 23)) - 1.0f;
+    const float ef = __int_as_float(e + 0x4B400000) - 0x1.8p23f;      // e, exactly
+    float p = -0x1.3997c2p-4f;
+    p = fmaf(p, f, 0x1.04605ep-3f);
+    p = fmaf(p, f, -0x1.0ce6acp-3f);
+    p = fmaf(p, f, 0x1.22f1e8p-3f);
+    p = fmaf(p, f, -0x1.54830ap-3f);
+    p = fmaf(p, f, 0x1.999fb8p-3f);
+    p = fmaf(p, f, -0x1.00020cp-2f);
+    p = fmaf(p, f, 0x1.555554p-2f);
+    p = fmaf(p, f, -0x1.fffffep-2f);
+    const float t = fmaf(f * f, p, f);
+    return fmaf(ef, 0x1.62e430p-1f, fmaf(ef, -0x1.05c610p-29f, t));
 }
 
 template <typename T> struct Consts;
@@ -177,39 +222,70 @@ __device__ __forceinline__ void locate(int n, int periodic, T s, int& cell, T& f
     cell = c;
 }
 
-// Bilinear interpolation of the packed monitor at (xi, eta) (Sec. 3.4).
-// FP32 cell and offset of coordinate s in [0, 1] on a Dirichlet n-node line, without
-// conversions: v = min(s (n - 1), n - 3/2) has floor(v) = the clamped cell (cell n - 2 for
-// s = 1), and v + 2^23 rounded down holds floor(v) in its low mantissa bits (unit spacing
-// there), so it is the float 2^23 + cell, exactly; the returned bits are 0x4B000000 + cell.
-// Paths inside the unit square only (a Dirichlet path leaves at its first step outside).
-__device__ __forceinline__ uint32_t locate_dirichlet(int n, float s, float& frac)
-{
-    const float u = s * (float)(n - 1);
-    const float v = fminf(u, (float)(n - 1) - 0.5f);
-    const float t = __fadd_rd(v, 0x1.0p23f);
-    frac = u - (t - 0x1.0p23f);
-    return (uint32_t)__float_as_int(t);
-}
+// Products and sums that no build fuses into a multiply-add: where the path's decisions follow
+// the oracle's arithmetic operation for operation (the oracle itself is compiled without fused
+// multiply-adds).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
-template <typename T>
+// The problem switches a substep reads: from the problem record (FL < 0), or fixed at compile
+// time (FL >= 0: bit 0 periodic, bit 1 the paper's generator form, bit 2 the bridge test), so
+// that the common configurations run without their per-substep branches.
+template <int FL> struct Mode {
+    template <typename T> __device__ __forceinline__ static bool periodic(const McProblem<T>& P)
+    {
+        if constexpr (FL < 0) return P.periodic != 0; else return (FL & 1) != 0;
+    }
+    template <typename T> __device__ __forceinline__ static bool form1(const McProblem<T>& P)
+    {
+        if constexpr (FL < 0) return P.form != 0; else return (FL & 2) != 0;
+    }
+    template <typename T> __device__ __forceinline__ static bool bridge(const McProblem<T>& P)
+    {
+        if constexpr (FL < 0) return P.bb != 0; else return (FL & 4) != 0;
+    }
+};
+constexpr int kModeDirichletBridge = 4;       // Dirichlet, generator form tau x_t = div(w grad x)
+constexpr int kModeDirichletBridgeForm1 = 6;  // Dirichlet, the paper's generator form
+
+// Bilinear interpolation of the packed monitor at (xi, eta) (Sec. 3.4).
+// FP32 Dirichlet grids locate the cell without conversions: for a coordinate s in [0, 1] on an
+// n-node line, u = s (n - 1) and v = min(u, n - 3/2) has floor(v) = the clamped cell (cell
+// n - 2 for s = 1); v + 2^23 rounded down holds floor(v) in its low mantissa bits (unit spacing
+// there), so it is the float 2^23 + cell exactly, with bits 0x4B000000 + cell, and the offset
+// u - cell is exact.  Both coordinates run as paired FP32 instructions.  Paths inside the unit
+// square only (a Dirichlet path leaves at its first step outside).
+template <typename T, bool PARAM, int FL>
 __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T& w, T& wx, T& we)
 {
     T fx, fy;
     int base;  // grids hold at most 2^28 nodes
     bool done = false;
     if constexpr (sizeof(T) == 4) {
-        if (!P.periodic) {
-            const uint32_t bi = locate_dirichlet(P.nx, xi, fx);
-            const uint32_t bj = locate_dirichlet(P.ny, eta, fy);
-            base = (int)(bj * (uint32_t)P.nx + bi - P.cell_bias);
+        if (!Mode<FL>::periodic(P)) {
+            float2 u, v;
+            if constexpr (PARAM) {  // the record lives in the parameter block: its constants are operands
+                u = __fmul2_rn(make_float2(xi, eta), make_float2(P.gs[0], P.gs[1]));
+                v = make_float2(fminf(u.x, P.gc[0]), fminf(u.y, P.gc[1]));
+            } else {                // a record in registers: convert rather than hold four more values
+                u = __fmul2_rn(make_float2(xi, eta), make_float2((float)(P.nx - 1), (float)(P.ny - 1)));
+                v = make_float2(fminf(u.x, (float)(P.nx - 1) - 0.5f), fminf(u.y, (float)(P.ny - 1) - 0.5f));
+            }
+            const float2 t = __fadd2_rd(v, make_float2(0x1.0p23f, 0x1.0p23f));
+            const float2 c = __fadd2_rn(t, make_float2(-0x1.0p23f, -0x1.0p23f));  // the cells, exactly
+            const float2 f = __ffma2_rn(c, make_float2(-1.0f, -1.0f), u);          // u - cell, exactly
+            fx = f.x;
+            fy = f.y;
+            base = (int)((uint32_t)__float_as_int(t.y) * (uint32_t)P.nx + (uint32_t)__float_as_int(t.x) - P.cell_bias);
             done = true;
         }
     }
     if (!done) {
         int i, j;
-        locate(P.nx, P.periodic, xi, i, fx);
-        locate(P.ny, P.periodic, eta, j, fy);
+        locate(P.nx, (int)Mode<FL>::periodic(P), xi, i, fx);
+        locate(P.ny, (int)Mode<FL>::periodic(P), eta, j, fy);
         base = j * P.nx + i;
     }
     const long N = (long)P.nx * P.ny;
@@ -230,29 +306,42 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
         wx = t.y;
         we = fmaf(wb.y, d.we, fmaf(wb.x, c.we, fmaf(wa.x, a.we, wa.y * b.we)));
     } else {
-        const T gx = 1 - fx, gy = 1 - fy;
-        const T w00 = gx * gy, w10 = fx * gy, w01 = gx * fy, w11 = fx * fy;
-        w = w00 * a.w + w10 * b.w + w01 * c.w + w11 * d.w;
-        wx = w00 * a.wx + w10 * b.wx + w01 * c.wx + w11 * d.wx;
-        we = w00 * a.we + w10 * b.we + w01 * c.we + w11 * d.we;
+        // w00 f00 + w10 f10 + w01 f01 + w11 f11 from the left, each operation rounded (as the oracle)
+        const T gx = add_rn((T)1, -fx), gy = add_rn((T)1, -fy);
+        const T w00 = mul_rn(gx, gy), w10 = mul_rn(fx, gy), w01 = mul_rn(gx, fy), w11 = mul_rn(fx, fy);
+        auto bil = [&](T f00, T f10, T f01, T f11) {
+            return add_rn(add_rn(add_rn(mul_rn(w00, f00), mul_rn(w10, f10)), mul_rn(w01, f01)), mul_rn(w11, f11));
+        };
+        w = bil(a.w, b.w, c.w, d.w);
+        wx = bil(a.wx, b.wx, c.wx, d.wx);
+        we = bil(a.we, b.we, c.we, d.we);
     }
 }
 
-// Keys (1981) cubic-convolution kernel, a = -1/2.
+// Keys (1981) cubic-convolution kernel, a = -1/2: 3/2 s^3 - 5/2 s^2 + 1 on [0, 1],
+// -1/2 s^3 + 5/2 s^2 - 4 s + 2 on [1, 2], in Horner form.  The arithmetic here and below is
+// written as explicit fused multiply-adds, so that every build and every kernel instantiation
+// rounds alike (a batched problem then reproduces the same problem stepped alone bit for bit).
 template <typename T>
 __device__ __forceinline__ T keys_kernel(T s)
 {
-    const T a = (T)-0.5;
     s = dabs(s);
-    if (s <= 1) return (a + 2) * s * s * s - (a + 3) * s * s + 1;
-    if (s < 2) return a * s * s * s - 5 * a * s * s + 8 * a * s - 4 * a;
+    if (s <= 1) return fma(fma((T)1.5, s, (T)-2.5), s * s, (T)1);
+    if (s < 2) return fma(fma(fma((T)-0.5, s, (T)2.5), s, (T)-4), s, (T)2);
     return 0;
 }
 
 template <typename T>
 __device__ __forceinline__ T keys_combine(const T g[4], const T k[4])
 {
-    return g[0] * k[0] + g[1] * k[1] + g[2] * k[2] + g[3] * k[3];
+    return fma(g[3], k[3], fma(g[2], k[2], fma(g[1], k[1], g[0] * k[0])));
+}
+
+// Keys' boundary extrapolation 3 f0 - 3 f1 + f2.
+template <typename T>
+__device__ __forceinline__ T keys_extrap(T f0, T f1, T f2)
+{
+    return fma((T)3, f0, fma((T)-3, f1, f2));
 }
 
 // Previous mesh displacement (X, Y) at (xi, eta): Keys bicubic with Keys' boundary
@@ -273,8 +362,9 @@ __device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
         const Disp2<T> a = ld(r0), b = ld(r0 + 1);
         const Disp2<T> c = ld(r0 + nx), d = ld(r0 + nx + 1);
         const T gx = 1 - tx, gy = 1 - ty;
-        ix = gx * gy * a.X + tx * gy * b.X + gx * ty * c.X + tx * ty * d.X;
-        iy = gx * gy * a.Y + tx * gy * b.Y + gx * ty * c.Y + tx * ty * d.Y;
+        const T w00 = gx * gy, w10 = tx * gy, w01 = gx * ty, w11 = tx * ty;
+        ix = fma(w11, d.X, fma(w01, c.X, fma(w00, a.X, w10 * b.X)));
+        iy = fma(w11, d.Y, fma(w01, c.Y, fma(w00, a.Y, w10 * b.Y)));
         return;
     }
     const T kx[4] = {keys_kernel<T>(1 + tx), keys_kernel<T>(tx), keys_kernel<T>(1 - tx),
@@ -304,12 +394,12 @@ __device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
                 cY[a] = v.Y;
             } else if (c < 0) {
                 const Disp2<T> v0 = ld(row), v1 = ld(row + 1), v2 = ld(row + 2);
-                cX[a] = 3 * v0.X - 3 * v1.X + v2.X;
-                cY[a] = 3 * v0.Y - 3 * v1.Y + v2.Y;
+                cX[a] = keys_extrap(v0.X, v1.X, v2.X);
+                cY[a] = keys_extrap(v0.Y, v1.Y, v2.Y);
             } else if (c > nx - 1) {
                 const Disp2<T> v0 = ld(row + nx - 1), v1 = ld(row + nx - 2), v2 = ld(row + nx - 3);
-                cX[a] = 3 * v0.X - 3 * v1.X + v2.X;
-                cY[a] = 3 * v0.Y - 3 * v1.Y + v2.Y;
+                cX[a] = keys_extrap(v0.X, v1.X, v2.X);
+                cY[a] = keys_extrap(v0.Y, v1.Y, v2.Y);
             } else {
                 const Disp2<T> v = ld(row + c);
                 cX[a] = v.X;
@@ -321,12 +411,12 @@ __device__ void mesh_at(const McProblem<T>& P, T xi, T eta, T& ix, T& iy)
     }
     if (!P.periodic) {
         if (j - 1 < 0) {
-            gX[0] = 3 * gX[1] - 3 * gX[2] + gX[3];
-            gY[0] = 3 * gY[1] - 3 * gY[2] + gY[3];
+            gX[0] = keys_extrap(gX[1], gX[2], gX[3]);
+            gY[0] = keys_extrap(gY[1], gY[2], gY[3]);
         }
         if (j + 2 > ny - 1) {
-            gX[3] = 3 * gX[2] - 3 * gX[1] + gX[0];
-            gY[3] = 3 * gY[2] - 3 * gY[1] + gY[0];
+            gX[3] = keys_extrap(gX[2], gX[1], gX[0]);
+            gY[3] = keys_extrap(gY[2], gY[1], gY[0]);
         }
     }
     ix = keys_combine(gX, ky);
@@ -344,7 +434,7 @@ __device__ __forceinline__ T side_lerp(const T* b, int n, T s)
     int c = (int)dfloor(u);
     c = c < 0 ? 0 : (c > n - 2 ? n - 2 : c);
     const T f = u - (T)c;
-    return ((T)1 - f) * b[checked(c, n)] + f * b[checked(c + 1, n)];
+    return fma(f, b[checked(c + 1, n)], ((T)1 - f) * b[checked(c, n)]);
 }
 
 // Brownian-bridge crossing probability of one side, exp(-d0 d1 / (D ds)) with q = D ds; in FP64
@@ -406,8 +496,8 @@ __device__ __forceinline__ int exit_value(const McProblem<T>& P, T xn, T en, int
         else if (s == 2) { vx = side_lerp(P.bnd, P.nx, xe); vy = (T)0; }
         else { vx = side_lerp(P.bnd + P.nx, P.nx, xe); vy = P.Ly; }
     } else {
-        vx = P.Lx * xe;
-        vy = P.Ly * ee;
+        vx = mul_rn(P.Lx, xe);
+        vy = mul_rn(P.Ly, ee);
     }
     return s;
 }
@@ -444,42 +534,103 @@ __device__ __forceinline__ U4 philox_hoisted(const uint32_t* rk, const PhiloxHoi
     return c;
 }
 
-template <typename T, bool RK>
+template <typename T, bool RK, int FL>
 __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, uint32_t p, int k,
                                              T& xi, T& eta, T& vx, T& vy, int& side, const PhiloxHoist& ph)
 {
     // the monitor gather first: its loads are in flight while Philox runs
     T wv, wx, we;
-    monitor_at(P, xi, eta, wv, wx, we);
+    monitor_at<T, RK, FL>(P, xi, eta, wv, wx, we);
     const U4 c{(uint32_t)k, p, m, P.tstep};
     U4 w;
     if constexpr (RK) w = philox_hoisted(P.rk, ph, (uint32_t)k);
     else w = philox4x32_10(c, P.key0, P.key1);
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the operations of the generic form below in the same order and rounding, with
+        // the x and y (and paired bridge-side) work as paired FP32 instructions
+        const float2 u12 = __fadd2_rn(make_float2(__int_as_float((w.x >> 9) + 0x3F800000u),
+                                                  __int_as_float((w.y >> 9) + 0x3F800000u)),
+                                      make_float2(-0x1.fffffep-1f, -0x1.fffffep-1f));
+        const float ub = uniform_open(w.z, 0.0f);
+        const float lgu = log_unit(u12.x);
+        float sn, cs;
+        sincos_2pi(u12.y, &sn, &cs);
+        float q;
+        float2 b;  // drift * ds, each product rounded as in the oracle (never fused into the add below)
+        if (!Mode<FL>::form1(P)) {
+            q = wv * P.cb;
+            b = make_float2(__fmul_rn(wx, P.cb), __fmul_rn(we, P.cb));
+        } else {
+            q = P.cb;
+            b = make_float2(__fmul_rn(wx / wv, P.cb), __fmul_rn(we / wv, P.cb));
+        }
+        const float2 a2 = __fmul2_rn(make_float2(lgu, q), make_float2(-2.0f, 2.0f));
+        const float2 rs = sqrt_pos2(a2);  // (r, sd) = (sqrt(-2 ln u1), sqrt(2 q))
+        const float r = rs.x, sd = rs.y;
+        const float2 z = __fmul2_rn(make_float2(r, r), make_float2(cs, sn));
+        // (xn, en) = ((xi, eta) + b) + sd z, the noise term fused
+        const float2 n = __ffma2_rn(make_float2(sd, sd), z, __fadd2_rn(make_float2(xi, eta), b));
+        if (!Mode<FL>::periodic(P)) {
+            const float2 o = __ffma2_rn(n, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - xn, 1 - en
+            bool exited = fminf(fminf(n.x, o.x), fminf(n.y, o.y)) < 0.0f;
+            int s = -1;
+            if (!exited && Mode<FL>::bridge(P)) {
+                const float sc = __fdividef(-1.4426950408889634f, q);
+                const float2 oi = __ffma2_rn(make_float2(xi, eta), make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+                const float2 a02 = __fmul2_rn(__fmul2_rn(make_float2(xi, eta), n), make_float2(sc, sc));
+                const float2 a13 = __fmul2_rn(__fmul2_rn(oi, o), make_float2(sc, sc));
+                float p0, p1, p2, p3;
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p0) : "f"(a02.x));
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p2) : "f"(a02.y));
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p1) : "f"(a13.x));
+                asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(p3) : "f"(a13.y));
+                const float2 s01 = __ffma2_rn(make_float2(p0, p1), make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+                const float2 s23 = __ffma2_rn(make_float2(p2, p3), make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
+                float surv = s01.x * s01.y;
+                surv *= s23.x;
+                surv *= s23.y;
+                if (ub > surv) {
+                    exited = true;
+                    float pm = p0;
+                    s = 0;
+                    if (p1 > pm) { pm = p1; s = 1; }
+                    if (p2 > pm) { pm = p2; s = 2; }
+                    if (p3 > pm) { pm = p3; s = 3; }
+                }
+            }
+            if (exited) {
+                vx = n.x;
+                vy = n.y;
+                side = s;
+                return 1;
+            }
+        }
+        xi = n.x;
+        eta = n.y;
+        return k + 1 == P.K ? 2 : 0;
+    } else {
     const T u1 = uniform_open(w.x, T()), u2 = uniform_open(w.y, T()), ub = uniform_open(w.z, T());
     const T lgu = dlog(u1);
     T sn, cs;
-    if constexpr (sizeof(T) == 4)
-        sincos_2pi(u2, &sn, &cs);  // FP32: polynomial form (below 0.75 ulp)
-    else
-        sincos(Consts<T>::two_pi * u2, &sn, &cs);
+    sincos(Consts<T>::two_pi * u2, &sn, &cs);
     T q, bx, by;  // q = D ds, (bx, by) = drift * ds
-    if (P.form == 0) {
+    if (!Mode<FL>::form1(P)) {
         q = wv * P.cb;
-        bx = wx * P.cb;
-        by = we * P.cb;
+        bx = mul_rn(wx, P.cb);
+        by = mul_rn(we, P.cb);
     } else {
         q = P.cb;
-        bx = wx / wv * P.cb;
-        by = we / wv * P.cb;
+        bx = mul_rn(wx / wv, P.cb);
+        by = mul_rn(we / wv, P.cb);
     }
     // Eq. 7: increment sqrt(2 q) z with the Box-Muller normals z = sqrt(-2 ln u1) (cos, sin)(2 pi u2),
-    // in the oracle's order of operations
+    // operation for operation as the oracle: (xi + bx) + sd (r cos), each rounded
     const T r = dsqrt((T)-2 * lgu);
     const T sd = dsqrt(2 * q);
-    const T xn = xi + bx + sd * (r * cs);
-    const T en = eta + by + sd * (r * sn);
+    const T xn = add_rn(add_rn(xi, bx), mul_rn(sd, mul_rn(r, cs)));
+    const T en = add_rn(add_rn(eta, by), mul_rn(sd, mul_rn(r, sn)));
 
-    if (!P.periodic) {
+    if (!Mode<FL>::periodic(P)) {
         // outside the unit square: the largest violation is positive, i.e. the smallest of the
         // distances xn, 1 - xn, en, 1 - en is negative (1 - v is exactly -(v - 1) in floating
         // point, so the two forms decide alike); the distances serve the bridge test as well.
@@ -488,7 +639,7 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
         const T oxn = 1 - xn, oen = 1 - en;
         bool exited = dmin(dmin(xn, oxn), dmin(en, oen)) < 0;
         int s = -1;
-        if (!exited && P.bb) {
+        if (!exited && Mode<FL>::bridge(P)) {
             const BridgeP<T> bridge_p(q);
             const T p0 = bridge_p(xi, xn), p1 = bridge_p(1 - xi, oxn);
             const T p2 = bridge_p(eta, en), p3 = bridge_p(1 - eta, oen);
@@ -518,6 +669,7 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
     xi = xn;
     eta = en;
     return k + 1 == P.K ? 2 : 0;
+    }
 }
 
 // Per-lane estimator sums of the shifted path values (shift = the node's previous position).
@@ -530,9 +682,9 @@ template <typename T> struct LaneAcc<T, kAcc64> {
     {
         const double dx = (double)vx - sx, dy = (double)vy - sy;
         s1x += dx;
-        s2x += dx * dx;
+        s2x = fma(dx, dx, s2x);
         s1y += dy;
-        s2y += dy * dy;
+        s2y = fma(dy, dy, s2y);
     }
     __device__ __forceinline__ void finish(double& a, double& b, double& c, double& d, unsigned long long, double,
                                            double) const
@@ -559,7 +711,11 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
     {
         const float2 d = __fadd2_rn(make_float2((float)vx, (float)vy), nshift);
         kahan(s1, c1, d);
-        kahan(s2, c2, __fmul2_rn(d, d));
+        // the square's compensated add: y = d^2 - c as one explicit fused operation
+        const float2 y = __ffma2_rn(d, d, neg(c2));
+        const float2 t = __fadd2_rn(s2, y);
+        c2 = __fadd2_rn(__fadd2_rn(t, neg(s2)), neg(y));
+        s2 = t;
     }
     // sx, sy: the shifts again (read at the end of the task, so that they hold no registers while
     // paths run)
@@ -570,10 +726,10 @@ template <typename T> struct LaneAcc<T, kAccKahan32> {
         const double S1x = (double)s1.x - (double)c1.x, S2x = (double)s2.x - (double)c2.x;
         const double S1y = (double)s1.y - (double)c1.y, S2y = (double)s2.y - (double)c2.y;
         const double nn = (double)n;
-        a = S1x - nn * ex;
-        b = S2x - 2.0 * ex * S1x + nn * ex * ex;
-        c = S1y - nn * ey;
-        d = S2y - 2.0 * ey * S1y + nn * ey * ey;
+        a = fma(-nn, ex, S1x);
+        b = fma(nn * ex, ex, fma(-2.0 * ex, S1x, S2x));
+        c = fma(-nn, ey, S1y);
+        d = fma(nn * ey, ey, fma(-2.0 * ey, S1y, S2y));
     }
 };
 
@@ -586,7 +742,7 @@ template <typename T> struct PathQueues {
     T* e_xn; T* e_en; int32_t* e_side; int32_t* e_k; uint32_t* e_path;  // exits (k, path: debug)
 };
 
-template <typename T, int ACC, bool DEBUG, bool RK>
+template <typename T, int ACC, bool DEBUG, bool RK, int FL>
 __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T>& R, int m, int g,
                                          int task, int64_t pb, int64_t pe, const PathQueues<T>& Q)
 {
@@ -628,10 +784,10 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
             const T fx = q_xi[pos], fy = q_eta[pos];
             T ix, iy;
             mesh_at(R, fx, fy, ix, iy);
-            const T vx = R.Lx * fx + ix, vy = R.Ly * fy + iy;
+            const T vx = fma(R.Lx, fx, ix), vy = fma(R.Ly, fy, iy);
             acc.add(vx, vy);
             if (DEBUG) {
-                const int64_t qd = (int64_t)q_path[pos] - P.dbg_p0;  // debug only
+                const int64_t qd = checked((int64_t)q_path[pos] - P.dbg_p0, P.dbg_n);  // debug only
                 P.dbg_val[2 * qd] = (double)vx;
                 P.dbg_val[2 * qd + 1] = (double)vy;
                 P.dbg_steps[qd] = R.K;
@@ -650,7 +806,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
             const int side = exit_value(R, Q.e_xn[pos], Q.e_en[pos], (int)Q.e_side[pos], vx, vy);
             acc.add(vx, vy);
             if (DEBUG) {
-                const int64_t qd = (int64_t)Q.e_path[pos] - P.dbg_p0;  // debug only
+                const int64_t qd = checked((int64_t)Q.e_path[pos] - P.dbg_p0, P.dbg_n);  // debug only
                 P.dbg_val[2 * qd] = (double)vx;
                 P.dbg_val[2 * qd + 1] = (double)vy;
                 P.dbg_steps[qd] = Q.e_k[pos];
@@ -660,31 +816,32 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
         qe -= count;
         __syncwarp();
     };
-    while (__any_sync(kFull, live)) {
-        int st = 0;
+    // Every lane runs a substep each iteration: a lane past the task's last path (live false)
+    // runs a stale path whose results are masked, which keeps the loop free of a per-substep
+    // vote and divergent branch.  Such a lane stays at its node or inside the domain (an exit
+    // leaves its position unchanged), so its gathers stay in bounds.
+    for (;;) {
         T vx, vy;
         int side = 0;
-        if (live) {
-            st = path_substep<T, RK>(R, (uint32_t)m, path, k, xi, eta, vx, vy, side, ph);
-            ++k;
-            if (st != 0) {
-                steps += (uint32_t)k;
-                paths += 1;
-            }
+        int st = path_substep<T, RK, FL>(R, (uint32_t)m, path, k, xi, eta, vx, vy, side, ph);
+        ++k;
+        st = live ? st : 0;
+        if (st != 0) {
+            steps += (uint32_t)k;
+            paths += 1;
         }
         const unsigned dm = __ballot_sync(kFull, st != 0);
-        if (dm) {  // some lane's path ended: queue survivors (and exits), hand out the next path indices
+        if (dm) {  // some lane's path ended: queue survivors and exits, hand out the next path indices
             const unsigned sm = __ballot_sync(kFull, st == 2);
+            const int before = __popc(dm & lt);  // ended lanes below this one
+            const int sbefore = __popc(sm & lt);  // of them, survivors
             if (st == 2) {
-                const int pos = checked(qn + __popc(sm & lt), 64);
+                const int pos = checked(qn + sbefore, 64);
                 q_xi[pos] = xi;
                 q_eta[pos] = eta;
                 if (DEBUG) q_path[pos] = path;
-            }
-            qn += __popc(sm);
-            const unsigned em = dm & ~sm;  // exits
-            if (st == 1) {
-                const int pos = checked(qe + __popc(em & lt), 64);
+            } else if (st == 1) {
+                const int pos = checked(qe + before - sbefore, 64);
                 Q.e_xn[pos] = vx;
                 Q.e_en[pos] = vy;
                 Q.e_side[pos] = side;
@@ -693,9 +850,8 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
                     Q.e_path[pos] = path;
                 }
             }
-            qe += __popc(em);
             if (st != 0) {
-                path = next + __popc(dm & lt);
+                path = next + (uint32_t)before;
                 if constexpr (RK) {
                     const uint32_t x1 = x1base ^ path;
                     ph.H = __umulhi(0xD2511F53u, x1);
@@ -706,9 +862,15 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
                 eta = eta0;
                 k = 0;
             }
-            next += __popc(dm);
-            if (qn >= 32) drain(32);
-            if (qe >= 32) drain_exits(32);
+            const int ns = __popc(sm), nd = __popc(dm);
+            qn += ns;
+            qe += nd - ns;
+            next += (uint32_t)nd;
+            if ((qn | qe) >= 32) {  // both below 64
+                if (qn >= 32) drain(32);
+                if (qe >= 32) drain_exits(32);
+            }
+            if (!__any_sync(kFull, live)) break;
         }
     }
     if (qn > 0) drain(qn);
@@ -730,7 +892,8 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
 // Persistent path kernel.  BATCH: tasks of several problems share the launch; each task reads
 // its problem's record (the Philox counter uses the problem-local node id, so a problem's
 // results do not depend on what else shares the launch).
-template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB = kMcThreads>
+// FL: the problem switches compiled in (Mode; single-problem launches), or -1.
+template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB = kMcThreads, int FL = -1>
 __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(const __grid_constant__ McParams<T> P)
 {
     constexpr int kWarps = TPB / 32;
@@ -763,9 +926,9 @@ __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(cons
         const int64_t pe = pb + tp < chunk_end ? pb + tp : chunk_end;
         if constexpr (BATCH) {
             const McProblem<T> R = P.probs[P.node_prob[g]];
-            run_task<T, ACC, DEBUG, false>(P, R, g - R.node_offset, g, task, pb, pe, Q);
+            run_task<T, ACC, DEBUG, false, -1>(P, R, g - R.node_offset, g, task, pb, pe, Q);
         } else {
-            run_task<T, ACC, DEBUG, true>(P, P.prob, g, g, task, pb, pe, Q);
+            run_task<T, ACC, DEBUG, true, FL>(P, P.prob, g, g, task, pb, pe, Q);
         }
     }
 }
@@ -1008,11 +1171,77 @@ const void* select_mc(int acc_mode, bool debug, bool batch, int tpb)
 
 }  // namespace
 
+// The path kernels gather the packed grids through L1.  Each kernel asks, once per device, for
+// the smallest shared-memory carve-out that holds the per-warp queues of the blocks its registers
+// let reside on an SM, so that the rest of the SM's unified L1 / shared memory serves as cache
+// (left to itself the driver may pick a larger carve-out).
+void prefer_l1(const void* fn, int tpb)
+{
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!done.insert({fn, dev}).second) return;
+    }
+    cudaFuncAttributes fa{};
+    int reserved = 0, max_smem = 0, max_threads = 0, regs_per_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        max_smem <= 0 || fa.numRegs <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    int blocks = regs_per_sm / (fa.numRegs * tpb);
+    blocks = std::max(1, std::min(blocks, max_threads / tpb));
+    const long need = (long)blocks * ((long)fa.sharedSizeBytes + reserved);
+    const int pct = (int)std::min(100L, (100 * need + max_smem - 1) / max_smem);
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, pct) != cudaSuccess)
+        cudaGetLastError();  // a hint: the launch goes ahead with the driver's choice
+}
+
+template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB, int FL>
+void prefer_l1_for()
+{
+    prefer_l1(reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG, BATCH, TPB, FL>), TPB);
+}
+
 template <typename T, int TPB>
 void launch_batch_mc_kernel(const McParams<T>& P, bool kahan, int grid, cudaStream_t s)
 {
-    if (kahan) mc_kernel<T, kAccKahan32, false, true, TPB><<<grid, TPB, 0, s>>>(P);
-    else mc_kernel<T, kAcc64, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+    if (kahan) {
+        prefer_l1_for<T, kAccKahan32, false, true, TPB, -1>();
+        mc_kernel<T, kAccKahan32, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+    } else {
+        prefer_l1_for<T, kAcc64, false, true, TPB, -1>();
+        mc_kernel<T, kAcc64, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+    }
+}
+
+// Single-problem FP32 launches of the common switch settings run a kernel with them compiled in
+// (the same arithmetic without the per-substep branches); the rest the general kernel.
+template <typename T, int ACC>
+void launch_single_mc(const McParams<T>& P, int grid, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        const int mode = (P.prob.periodic ? 1 : 0) | (P.prob.form ? 2 : 0) | (P.prob.bb ? 4 : 0);
+        if (mode == kModeDirichletBridge) {
+            prefer_l1_for<T, ACC, false, false, kMcThreads, kModeDirichletBridge>();
+            mc_kernel<T, ACC, false, false, kMcThreads, kModeDirichletBridge><<<grid, kMcThreads, 0, s>>>(P);
+            return;
+        }
+        if (mode == kModeDirichletBridgeForm1) {
+            prefer_l1_for<T, ACC, false, false, kMcThreads, kModeDirichletBridgeForm1>();
+            mc_kernel<T, ACC, false, false, kMcThreads, kModeDirichletBridgeForm1><<<grid, kMcThreads, 0, s>>>(P);
+            return;
+        }
+    }
+    prefer_l1_for<T, ACC, false, false, kMcThreads, -1>();
+    mc_kernel<T, ACC, false, false><<<grid, kMcThreads, 0, s>>>(P);
 }
 
 template <typename T>
@@ -1025,11 +1254,16 @@ cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch
         else if (tpb == 512) launch_batch_mc_kernel<T, 512>(P, kahan, grid, s);
         else launch_batch_mc_kernel<T, kMcThreads>(P, kahan, grid, s);
     } else if (debug) {
-        if (kahan) mc_kernel<T, kAccKahan32, true, false><<<grid, kMcThreads, 0, s>>>(P);
-        else mc_kernel<T, kAcc64, true, false><<<grid, kMcThreads, 0, s>>>(P);
+        if (kahan) {
+            prefer_l1_for<T, kAccKahan32, true, false, kMcThreads, -1>();
+            mc_kernel<T, kAccKahan32, true, false><<<grid, kMcThreads, 0, s>>>(P);
+        } else {
+            prefer_l1_for<T, kAcc64, true, false, kMcThreads, -1>();
+            mc_kernel<T, kAcc64, true, false><<<grid, kMcThreads, 0, s>>>(P);
+        }
     } else {
-        if (kahan) mc_kernel<T, kAccKahan32, false, false><<<grid, kMcThreads, 0, s>>>(P);
-        else mc_kernel<T, kAcc64, false, false><<<grid, kMcThreads, 0, s>>>(P);
+        if (kahan) launch_single_mc<T, kAccKahan32>(P, grid, s);
+        else launch_single_mc<T, kAcc64>(P, grid, s);
     }
     return cudaGetLastError();
 }

@@ -206,7 +206,7 @@ sdd_status run(const sdd_params* P, const Buffers& b, int M, int acc_mode, int32
     R.key0 = (uint32_t)(P->seed & 0xFFFFFFFFu);
     R.key1 = (uint32_t)(P->seed >> 32);
     philox_round_keys(P->seed, R.rk);
-    R.cell_bias = (uint32_t)(P->nx + 1) * 0x4B000000u;
+    set_grid_consts(R);
     R.tstep = (uint32_t)step_index;
     R.node_offset = 0;
     mp.shift = b.shift;

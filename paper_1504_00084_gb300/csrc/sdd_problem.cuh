@@ -143,7 +143,7 @@ inline sdd::McProblem<T> mc_problem(const sdd_problem* p)
     R.key0 = (uint32_t)(p->prm.seed & 0xFFFFFFFFu);
     R.key1 = (uint32_t)(p->prm.seed >> 32);
     sdd::philox_round_keys(p->prm.seed, R.rk);
-    R.cell_bias = (uint32_t)(p->prm.nx + 1) * 0x4B000000u;
+    sdd::set_grid_consts(R);
     R.tstep = (uint32_t)p->step;
     R.node_offset = 0;
     R.bnd = p->prm.moving_boundary ? static_cast<const T*>(p->bnd) : nullptr;
