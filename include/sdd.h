@@ -300,6 +300,12 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
  * on the legacy default stream; returns after `out` is written. */
 sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out);
 
+/* Test hook: the FP32 Box-Muller pieces the path kernel evaluates (Sec. 3.4, the N(0,1) draws of
+ * Eq. 7), on n given Philox words w (host or device, n words): out (n x 5 floats) holds, per
+ * word, the uniform u = (floor(w / 2^9) + 1/2) 2^-23, the kernel's ln u, its sqrt(-2 ln u) and
+ * sin 2 pi u, cos 2 pi u.  On the legacy default stream; returns after `out` is written. */
+sdd_status sdd_debug_unit_math(const uint32_t* w, int64_t n, float* out);
+
 /* Test hook: the number of out-of-range gather indices the path kernel met since the library
  * was loaded, in a build compiled with -DSDD_BOUNDS_CHECK.  Such a build checks every monitor,
  * mesh, boundary and queue index before its load; an index outside its array is counted and
@@ -478,10 +484,10 @@ void sdd_server_destroy(sdd_server* s);
  *            without waiting for the GPU.
  * Intermediates live in one 16 MiB device array inside the library, held by every GPU that
  * loads it until the process exits.  Requests needing more are rejected with
- * SDD_ERR_INVALID_ARG: the requirement is 48 B per grid node (FP32; 72 B in FP64), 116 B per
- * interface node and 48 B per task of 2048 paths, min(N, 2^19)/2048 tasks per interface node
- * (rounded up), each block aligned to 256 B -- e.g. a 257x257 grid with 1521 interface nodes
- * fits in FP32 for N <= 3.7e5.  Host pointers are rejected.  A problem without interface nodes
+ * SDD_ERR_INVALID_ARG: the requirement is 32 B per grid node plus 64 B per grid cell (FP32;
+ * 72 B per grid node in FP64), 116 B per interface node and 48 B per task of 2048 paths,
+ * min(N, 2^19)/2048 tasks per interface node (rounded up), each block aligned to 256 B -- e.g. a
+ * 257x257 grid with 1521 interface nodes fits in FP32 for N <= 2.8e5.  Host pointers are rejected.  A problem without interface nodes
  * (one Dirichlet subdomain) returns SDD_OK and writes nothing (est_xy and se_xy may be NULL).
  * The inputs are not validated on the device: the estimates are undefined unless omega is
  * finite and > 0, x and y are finite, and on Dirichlet grids the boundary nodes of (x, y) are

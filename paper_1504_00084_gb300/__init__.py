@@ -91,6 +91,7 @@ EXPORTS = [
     "sdd_set_monitor", "sdd_set_monitor_analytic", "sdd_interface_mc", "sdd_subdomain_solve",
     "sdd_step", "sdd_get_stats", "sdd_get_interface_nodes", "sdd_interface_layout",
     "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
+    "sdd_debug_unit_math",
     "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
     "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy", "sdd_batch_tune",
     "sdd_mesh_quality",
@@ -126,6 +127,7 @@ def _load():
         "sdd_get_monitor": ([P, P, P, P], I32),
         "sdd_debug_paths": ([P, I32, I64, I64, P, P, P], I32),
         "sdd_debug_philox": ([P, P, I64, P], I32),
+        "sdd_debug_unit_math": ([P, I64, P], I32),
         "sdd_debug_bounds_violations": ([], I64),
         "sdd_interface_mc_noalloc": ([ctypes.POINTER(SddParams), P, P, P, I32, P, P, P], I32),
         "sdd_batch_create": ([P, I32, P, I32, ctypes.POINTER(P)], I32),
@@ -336,6 +338,15 @@ def sdd_debug_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
     out = np.zeros_like(ctr)
     _check(lib.sdd_debug_philox(ctr.ctypes.data, key.ctypes.data, len(ctr), out.ctypes.data),
            "sdd_debug_philox")
+    return out
+
+
+def sdd_debug_unit_math(w: np.ndarray) -> np.ndarray:
+    """(u, ln u, sqrt(-2 ln u), sin 2 pi u, cos 2 pi u) of the path kernel's FP32 Box-Muller
+    pieces for each Philox word (n x 5 float32)."""
+    w = np.ascontiguousarray(w, dtype=np.uint32).reshape(-1)
+    out = np.zeros((len(w), 5), dtype=np.float32)
+    _check(lib.sdd_debug_unit_math(w.ctypes.data, len(w), out.ctypes.data), "sdd_debug_unit_math")
     return out
 
 

@@ -469,7 +469,7 @@ void problem_arrays(sdd_problem* p, bool with_mc, F&& f)
     f((void**)&p->x, N * 8); f((void**)&p->y, N * 8); f((void**)&p->xn, N * 8); f((void**)&p->yn, N * 8);
     f((void**)&p->om64, N * 8); f((void**)&p->wxi64, N * 8); f((void**)&p->weta64, N * 8);
     f((void**)&p->omega_nodal, N * 8);
-    f((void**)&p->mon, N * 4 * rs); f((void**)&p->disp, N * 2 * rs);
+    f((void**)&p->mon, mon_bytes(q.nx, q.ny, q.precision == SDD_FP64)); f((void**)&p->disp, N * 2 * rs);
     f((void**)&p->nodes, (M + 1) * sizeof(int2));
     f((void**)&p->iface_role, (M + 1) * 4);
     f((void**)&p->interp, (size_t)(p->n_interp > 0 ? p->n_interp : 1) * sizeof(InterpRule));
@@ -1152,6 +1152,23 @@ sdd_status sdd_debug_paths(sdd_problem* p, int32_t node, int64_t p_begin, int64_
     if (dst) cudaFree(dst);
     if (dsd) cudaFree(dsd);
     return s;
+}
+
+sdd_status sdd_debug_unit_math(const uint32_t* w, int64_t n, float* out)
+{
+    if (n < 0 || (n > 0 && (!w || !out))) return fail(SDD_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return SDD_OK;
+    uint32_t* dw = nullptr;
+    float* dout = nullptr;
+    SDD_CK(cudaMalloc(&dw, (size_t)n * 4));
+    cudaError_t e = cudaMalloc(&dout, (size_t)n * 20);
+    if (e == cudaSuccess) e = cudaMemcpy(dw, w, (size_t)n * 4, cudaMemcpyDefault);
+    if (e == cudaSuccess) e = launch_unit_math(dw, n, dout, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, (size_t)n * 20, cudaMemcpyDefault);
+    cudaFree(dw);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return fail(SDD_ERR_CUDA, cudaGetErrorString(e));
+    return SDD_OK;
 }
 
 sdd_status sdd_debug_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out)

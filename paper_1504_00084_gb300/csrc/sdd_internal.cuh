@@ -100,6 +100,14 @@ __device__ __forceinline__ double uniform_open(uint32_t w, double)
 template <typename T> struct alignas(4 * sizeof(T)) Mon4 {
     T w, wx, we, pad;  // omega, d omega / d xi, d omega / d eta
 };
+// Packed monitor of the path kernel.  FP64: one Mon4 per grid node (j nx + i).  FP32: one 64-byte
+// cell record per grid cell (j (nx - 1) + i, i < nx - 1, j < ny - 1) holding the Mon4 of its four
+// corners (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1), so that a bilinear gather is two aligned
+// 32-byte loads of one cache line.
+inline size_t mon_bytes(int nx, int ny, bool fp64)
+{
+    return fp64 ? (size_t)nx * ny * sizeof(Mon4<double>) : (size_t)(nx - 1) * (ny - 1) * 4 * sizeof(Mon4<float>);
+}
 template <typename T> struct alignas(2 * sizeof(T)) Disp2 {
     T X, Y;            // previous mesh minus the identity: x - Lx xi, y - Ly eta
 };
@@ -124,7 +132,7 @@ constexpr int64_t kAdaptiveGranule = 1024;
 
 // Per-problem inputs of the path kernel.
 template <typename T> struct McProblem {
-    const Mon4<T>* mon;        // nx*ny packed monitor
+    const Mon4<T>* mon;        // packed monitor (mon_bytes: node records, or FP32 cell records)
     const Disp2<T>* disp;      // nx*ny packed displacement of the previous mesh
     const int2* nodes;         // the problem's interface nodes (i, j), by local node id
     int nx, ny, periodic, form, K, bicubic, bb;
@@ -133,7 +141,7 @@ template <typename T> struct McProblem {
     uint32_t key0, key1, tstep;
     int32_t node_offset;       // global index of the problem's node 0 in the launch's node arrays
     uint32_t rk[20];           // Philox round keys of (key0, key1) (single-problem launches)
-    uint32_t cell_bias;        // (nx + 1) * 0x4B000000 mod 2^32: see monitor_at
+    uint32_t cell_bias;        // nx * 0x4B000000 mod 2^32: see monitor_at
     float gs[2];               // FP32 Dirichlet cell location: nx - 1, ny - 1 (see monitor_at)
     float gc[2];               // and the clamp nx - 3/2, ny - 3/2
     const T* bnd;              // moving boundary: tangential boundary coordinates (null: identity)
@@ -143,7 +151,7 @@ template <typename T> struct McProblem {
 template <typename T>
 inline void set_grid_consts(McProblem<T>& R)
 {
-    R.cell_bias = (uint32_t)(R.nx + 1) * 0x4B000000u;
+    R.cell_bias = (uint32_t)R.nx * 0x4B000000u;
     R.gs[0] = (float)(R.nx - 1);
     R.gs[1] = (float)(R.ny - 1);
     R.gc[0] = (float)(R.nx - 1) - 0.5f;
@@ -367,6 +375,7 @@ cudaError_t launch_solve_batch(const SolveParams* probs, const int32_t* sub_off,
                                const int2* order = nullptr);
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, int64_t n, uint32_t* out,
                           cudaStream_t s);
+cudaError_t launch_unit_math(const uint32_t* w, int64_t n, float* out, cudaStream_t s);
 // Cooperative solve launches (items from solve_items); the single-problem one also computes the
 // face coefficients first, as launch_solve does.
 cudaError_t launch_solve_items(const SolveParams& P, const SolveItem* items, int n_items, bool fp64_inner,

@@ -185,6 +185,13 @@ __device__ __forceinline__ Mon4<float> load_mon(const Mon4<float>* p)
     const float4 v = __ldg(reinterpret_cast<const float4*>(p));
     return Mon4<float>{v.x, v.y, v.z, v.w};
 }
+// Two consecutive Mon4<float> records (32 bytes, 32-byte aligned) in one read-only 256-bit load.
+__device__ __forceinline__ void ld_cell_half(const float* p, Mon4<float>& r0, Mon4<float>& r1)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r0.w), "=f"(r0.wx), "=f"(r0.we), "=f"(r0.pad), "=f"(r1.w), "=f"(r1.wx), "=f"(r1.we), "=f"(r1.pad)
+        : "l"(p));
+}
 __device__ __forceinline__ Mon4<double> load_mon(const Mon4<double>* p)
 {
     const double2 a = __ldg(reinterpret_cast<const double2*>(p));
@@ -255,8 +262,9 @@ constexpr int kModeDirichletBridgeForm1 = 6;  // Dirichlet, the paper's generato
 // n-node line, u = s (n - 1) and v = min(u, n - 3/2) has floor(v) = the clamped cell (cell
 // n - 2 for s = 1); v + 2^23 rounded down holds floor(v) in its low mantissa bits (unit spacing
 // there), so it is the float 2^23 + cell exactly, with bits 0x4B000000 + cell, and the offset
-// u - cell is exact.  Both coordinates run as paired FP32 instructions.  Paths inside the unit
-// square only (a Dirichlet path leaves at its first step outside).
+// u - cell is exact; the cell record j (nx - 1) + i is then bits_j (nx - 1) + bits_i - nx 0x4B000000
+// (mod 2^32).  Both coordinates run as paired FP32 instructions.  Paths inside the unit square
+// only (a Dirichlet path leaves at its first step outside).
 template <typename T, bool PARAM, int FL>
 __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T& w, T& wx, T& we)
 {
@@ -278,7 +286,7 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
             const float2 f = __ffma2_rn(c, make_float2(-1.0f, -1.0f), u);          // u - cell, exactly
             fx = f.x;
             fy = f.y;
-            base = (int)((uint32_t)__float_as_int(t.y) * (uint32_t)P.nx + (uint32_t)__float_as_int(t.x) - P.cell_bias);
+            base = (int)((uint32_t)__float_as_int(t.y) * (uint32_t)(P.nx - 1) + (uint32_t)__float_as_int(t.x) - P.cell_bias);
             done = true;
         }
     }
@@ -286,12 +294,21 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
         int i, j;
         locate(P.nx, (int)Mode<FL>::periodic(P), xi, i, fx);
         locate(P.ny, (int)Mode<FL>::periodic(P), eta, j, fy);
-        base = j * P.nx + i;
+        base = j * (sizeof(T) == 4 ? P.nx - 1 : P.nx) + i;  // FP32: cell record, FP64: node record
     }
-    const long N = (long)P.nx * P.ny;
-    const Mon4<T> a = load_mon(P.mon + checked(base, N)), b = load_mon(P.mon + checked(base + 1, N));
-    const Mon4<T> c = load_mon(P.mon + checked(base + P.nx, N));
-    const Mon4<T> d = load_mon(P.mon + checked(base + P.nx + 1, N));
+    Mon4<T> a, b, c, d;
+    if constexpr (sizeof(T) == 4) {  // the cell's four corner records: two 32-byte loads
+        const long cells = (long)(P.nx - 1) * (P.ny - 1);
+        const float* q = reinterpret_cast<const float*>(P.mon) + 16 * (long)checked(base, cells);
+        ld_cell_half(q, a, b);
+        ld_cell_half(q + 8, c, d);
+    } else {
+        const long N = (long)P.nx * P.ny;
+        a = load_mon(P.mon + checked(base, N));
+        b = load_mon(P.mon + checked(base + 1, N));
+        c = load_mon(P.mon + checked(base + P.nx, N));
+        d = load_mon(P.mon + checked(base + P.nx + 1, N));
+    }
     if constexpr (sizeof(T) == 4) {
         // paired FP32 arithmetic (one instruction for two lanes of work), operation for
         // operation the contraction of the plain expressions below: bit-identical results
@@ -1142,6 +1159,25 @@ __global__ void philox_kernel(const uint32_t* ctr, const uint32_t* key, int64_t 
     out[4 * i + 3] = r.w;
 }
 
+// The FP32 Box-Muller pieces of the path kernel on given Philox words: for each word w,
+// u = uniform_open(w), ln u (log_unit), sqrt(-2 ln u) (sqrt_pos2), sin 2 pi u and cos 2 pi u.
+__global__ void unit_math_kernel(const uint32_t* w, int64_t n, float* out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float u = uniform_open(w[i], 0.0f);
+    const float l = log_unit(u);
+    const float r = sqrt_pos2(make_float2(-2.0f * l, u)).x;
+    float sn, cs;
+    sincos_2pi(u, &sn, &cs);
+    float* o = out + 5 * i;
+    o[0] = u;
+    o[1] = l;
+    o[2] = r;
+    o[3] = sn;
+    o[4] = cs;
+}
+
 template <typename T, int ACC, bool DEBUG, bool BATCH, int TPB = kMcThreads>
 const void* mc_kernel_ptr()
 {
@@ -1318,6 +1354,13 @@ cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const
                           double* est, double* se, cudaStream_t s)
 {
     output_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, acc, n_done, shift, est, se);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_math(const uint32_t* w, int64_t n, float* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    unit_math_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, n, out);
     return cudaGetLastError();
 }
 

@@ -124,12 +124,12 @@ struct Buffers {
     TaskSlot* slots;
 };
 
-size_t carve(Carve& c, Buffers& b, size_t N, size_t M, size_t slots, size_t real_bytes)
+size_t carve(Carve& c, Buffers& b, size_t N, size_t M, size_t slots, size_t real_bytes, size_t monb)
 {
     b.om64 = c.take<double>(N);
     b.wxi64 = c.take<double>(N);
     b.weta64 = c.take<double>(N);
-    b.mon = c.take<unsigned char>(N * 4 * real_bytes);
+    b.mon = c.take<unsigned char>(monb);
     b.disp = c.take<unsigned char>(N * 2 * real_bytes);
     b.nodes = c.take<int2>(M);
     b.shift = c.take<double>(2 * M);
@@ -266,7 +266,7 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
     const bool fp64 = P->precision == SDD_FP64;
     Buffers b{};
     Carve sizing{nullptr};
-    if (carve(sizing, b, (size_t)N, (size_t)M, (size_t)slots, fp64 ? 8 : 4) > kScratchBytes)
+    if (carve(sizing, b, (size_t)N, (size_t)M, (size_t)slots, fp64 ? 8 : 4, mon_bytes(P->nx, P->ny, fp64)) > kScratchBytes)
         return SDD_ERR_INVALID_ARG;  // larger than the fixed scratch array
     if (!on_device(x) || !on_device(y) || !on_device(omega)) return SDD_ERR_INVALID_ARG;
     if (M == 0) return SDD_OK;  // one Dirichlet subdomain: no interface node, nothing to write
@@ -275,7 +275,7 @@ extern "C" sdd_status sdd_interface_mc_noalloc(const sdd_params* P, const double
     const sdd_status st = scratch_for_current_device(&base);
     if (st != SDD_OK) return st;
     Carve c{static_cast<unsigned char*>(base)};
-    carve(c, b, (size_t)N, (size_t)M, (size_t)slots, fp64 ? 8 : 4);
+    carve(c, b, (size_t)N, (size_t)M, (size_t)slots, fp64 ? 8 : 4, mon_bytes(P->nx, P->ny, fp64));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     noalloc_nodes_kernel<<<(int)((M + 255) / 256), 256, 0, s>>>(P->nx, P->ny, P->px, P->py, P->periodic,

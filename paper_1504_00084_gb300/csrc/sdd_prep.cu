@@ -116,7 +116,16 @@ __device__ __forceinline__ void prep_pack_body(const PrepParams& P, int blk, int
         const double we = fd_line(P.om64 + i, P.nx, j, P.ny, P.periodic);
         P.wxi64[id] = wx;
         P.weta64[id] = we;
-        mon[id] = Mon4<T>{(T)w, (T)wx, (T)we, (T)0};
+        const Mon4<T> rec{(T)w, (T)wx, (T)we, (T)0};
+        if constexpr (sizeof(T) == 8) {
+            mon[id] = rec;
+        } else {  // FP32 cell records: this node is corner (a, b, c, d) of cells (i, j), (i-1, j), (i, j-1), (i-1, j-1)
+            const int cx = P.nx - 1, cy = P.ny - 1;
+            if (i < cx && j < cy) mon[4 * ((long)j * cx + i)] = rec;
+            if (i > 0 && j < cy) mon[4 * ((long)j * cx + i - 1) + 1] = rec;
+            if (i < cx && j > 0) mon[4 * ((long)(j - 1) * cx + i) + 2] = rec;
+            if (i > 0 && j > 0) mon[4 * ((long)(j - 1) * cx + i - 1) + 3] = rec;
+        }
         const int ci = P.periodic ? i % (P.nx - 1) : i;
         const int cj = P.periodic ? j % (P.ny - 1) : j;
         const int c = cj * P.nx + ci;
