@@ -484,10 +484,10 @@ void sdd_server_destroy(sdd_server* s);
  *            without waiting for the GPU.
  * Intermediates live in one 16 MiB device array inside the library, held by every GPU that
  * loads it until the process exits.  Requests needing more are rejected with
- * SDD_ERR_INVALID_ARG: the requirement is 32 B per grid node plus 64 B per grid cell (FP32;
- * 72 B per grid node in FP64), 116 B per interface node and 48 B per task of 2048 paths,
- * min(N, 2^19)/2048 tasks per interface node (rounded up), each block aligned to 256 B -- e.g. a
- * 257x257 grid with 1521 interface nodes fits in FP32 for N <= 2.8e5.  Host pointers are rejected.  A problem without interface nodes
+ * SDD_ERR_INVALID_ARG: the requirement is 96 B per grid node (FP32; 72 B in FP64), 116 B per
+ * interface node and 48 B per task of 2048 paths, min(N, 2^19)/2048 tasks per interface node
+ * (rounded up), each block aligned to 256 B -- e.g. a 257x257 grid with 1521 interface nodes
+ * fits in FP32 for N <= 2.8e5.  Host pointers are rejected.  A problem without interface nodes
  * (one Dirichlet subdomain) returns SDD_OK and writes nothing (est_xy and se_xy may be NULL).
  * The inputs are not validated on the device: the estimates are undefined unless omega is
  * finite and > 0, x and y are finite, and on Dirichlet grids the boundary nodes of (x, y) are

@@ -101,12 +101,14 @@ template <typename T> struct alignas(4 * sizeof(T)) Mon4 {
     T w, wx, we, pad;  // omega, d omega / d xi, d omega / d eta
 };
 // Packed monitor of the path kernel.  FP64: one Mon4 per grid node (j nx + i).  FP32: one 64-byte
-// cell record per grid cell (j (nx - 1) + i, i < nx - 1, j < ny - 1) holding the Mon4 of its four
-// corners (i, j), (i + 1, j), (i, j + 1), (i + 1, j + 1), so that a bilinear gather is two aligned
-// 32-byte loads of one cache line.
+// cell record per grid node (j nx + i) holding the Mon4 of the corners (i, j), (i + 1, j),
+// (i, j + 1), (i + 1, j + 1) of the cell to its upper right, corner indices clamped to the grid
+// (the records of the last column and row serve coordinates exactly on the far sides, where the
+// clamped corners carry zero weight), so that a bilinear gather is two aligned 32-byte loads of
+// one cache line and needs no clamp of the cell index.
 inline size_t mon_bytes(int nx, int ny, bool fp64)
 {
-    return fp64 ? (size_t)nx * ny * sizeof(Mon4<double>) : (size_t)(nx - 1) * (ny - 1) * 4 * sizeof(Mon4<float>);
+    return (size_t)nx * ny * (fp64 ? sizeof(Mon4<double>) : 4 * sizeof(Mon4<float>));
 }
 template <typename T> struct alignas(2 * sizeof(T)) Disp2 {
     T X, Y;            // previous mesh minus the identity: x - Lx xi, y - Ly eta
@@ -141,9 +143,9 @@ template <typename T> struct McProblem {
     uint32_t key0, key1, tstep;
     int32_t node_offset;       // global index of the problem's node 0 in the launch's node arrays
     uint32_t rk[20];           // Philox round keys of (key0, key1) (single-problem launches)
-    uint32_t cell_bias;        // nx * 0x4B000000 mod 2^32: see monitor_at
+    uint32_t cell_bias;        // (nx + 1) * 0x4B000000 mod 2^32: see monitor_at
     float gs[2];               // FP32 Dirichlet cell location: nx - 1, ny - 1 (see monitor_at)
-    float gc[2];               // and the clamp nx - 3/2, ny - 3/2
+    uint32_t cell_last;        // nx ny - 1: the last FP32 cell record
     const T* bnd;              // moving boundary: tangential boundary coordinates (null: identity)
 };
 
@@ -151,11 +153,10 @@ template <typename T> struct McProblem {
 template <typename T>
 inline void set_grid_consts(McProblem<T>& R)
 {
-    R.cell_bias = (uint32_t)R.nx * 0x4B000000u;
+    R.cell_bias = (uint32_t)(R.nx + 1) * 0x4B000000u;
     R.gs[0] = (float)(R.nx - 1);
     R.gs[1] = (float)(R.ny - 1);
-    R.gc[0] = (float)(R.nx - 1) - 0.5f;
-    R.gc[1] = (float)(R.ny - 1) - 0.5f;
+    R.cell_last = (uint32_t)R.nx * (uint32_t)R.ny - 1u;
 }
 
 template <typename T> struct McParams {

@@ -259,10 +259,10 @@ constexpr int kModeDirichletBridgeForm1 = 6;  // Dirichlet, the paper's generato
 
 // Bilinear interpolation of the packed monitor at (xi, eta) (Sec. 3.4).
 // FP32 Dirichlet grids locate the cell without conversions: for a coordinate s in [0, 1] on an
-// n-node line, u = s (n - 1) and v = min(u, n - 3/2) has floor(v) = the clamped cell (cell
-// n - 2 for s = 1); v + 2^23 rounded down holds floor(v) in its low mantissa bits (unit spacing
-// there), so it is the float 2^23 + cell exactly, with bits 0x4B000000 + cell, and the offset
-// u - cell is exact; the cell record j (nx - 1) + i is then bits_j (nx - 1) + bits_i - nx 0x4B000000
+// n-node line, u = s (n - 1) + 2^23 rounded down holds floor(u) in its low mantissa bits (unit
+// spacing there), so it is the float 2^23 + cell exactly, with bits 0x4B000000 + cell, and the
+// offset u - cell is exact; s = 1 gives cell n - 1 with offset 0, whose clamped corner records
+// carry zero weight.  The cell record j nx + i is then bits_j nx + bits_i - (nx + 1) 0x4B000000
 // (mod 2^32).  Both coordinates run as paired FP32 instructions.  Paths inside the unit square
 // only (a Dirichlet path leaves at its first step outside).
 template <typename T, bool PARAM, int FL>
@@ -273,20 +273,20 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
     bool done = false;
     if constexpr (sizeof(T) == 4) {
         if (!Mode<FL>::periodic(P)) {
-            float2 u, v;
-            if constexpr (PARAM) {  // the record lives in the parameter block: its constants are operands
+            float2 u;
+            if constexpr (PARAM)  // the record lives in the parameter block: its constants are operands
                 u = __fmul2_rn(make_float2(xi, eta), make_float2(P.gs[0], P.gs[1]));
-                v = make_float2(fminf(u.x, P.gc[0]), fminf(u.y, P.gc[1]));
-            } else {                // a record in registers: convert rather than hold four more values
+            else                  // a record in registers: convert rather than hold two more values
                 u = __fmul2_rn(make_float2(xi, eta), make_float2((float)(P.nx - 1), (float)(P.ny - 1)));
-                v = make_float2(fminf(u.x, (float)(P.nx - 1) - 0.5f), fminf(u.y, (float)(P.ny - 1) - 0.5f));
-            }
-            const float2 t = __fadd2_rd(v, make_float2(0x1.0p23f, 0x1.0p23f));
+            const float2 t = __fadd2_rd(u, make_float2(0x1.0p23f, 0x1.0p23f));
             const float2 c = __fadd2_rn(t, make_float2(-0x1.0p23f, -0x1.0p23f));  // the cells, exactly
             const float2 f = __ffma2_rn(c, make_float2(-1.0f, -1.0f), u);          // u - cell, exactly
             fx = f.x;
             fy = f.y;
-            base = (int)((uint32_t)__float_as_int(t.y) * (uint32_t)(P.nx - 1) + (uint32_t)__float_as_int(t.x) - P.cell_bias);
+            // the cell of a position in the unit square; any other value (a NaN from invalid input,
+            // which the step reports afterwards) is held to the last record by one unsigned minimum
+            base = (int)min((uint32_t)__float_as_int(t.y) * (uint32_t)P.nx + (uint32_t)__float_as_int(t.x) - P.cell_bias,
+                            P.cell_last);
             done = true;
         }
     }
@@ -294,11 +294,11 @@ __device__ __forceinline__ void monitor_at(const McProblem<T>& P, T xi, T eta, T
         int i, j;
         locate(P.nx, (int)Mode<FL>::periodic(P), xi, i, fx);
         locate(P.ny, (int)Mode<FL>::periodic(P), eta, j, fy);
-        base = j * (sizeof(T) == 4 ? P.nx - 1 : P.nx) + i;  // FP32: cell record, FP64: node record
+        base = j * P.nx + i;  // FP32 cell record, FP64 node record
     }
     Mon4<T> a, b, c, d;
     if constexpr (sizeof(T) == 4) {  // the cell's four corner records: two 32-byte loads
-        const long cells = (long)(P.nx - 1) * (P.ny - 1);
+        const long cells = (long)P.nx * P.ny;
         const float* q = reinterpret_cast<const float*>(P.mon) + 16 * (long)checked(base, cells);
         ld_cell_half(q, a, b);
         ld_cell_half(q + 8, c, d);
@@ -589,7 +589,10 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
         const float2 n = __ffma2_rn(make_float2(sd, sd), z, __fadd2_rn(make_float2(xi, eta), b));
         if (!Mode<FL>::periodic(P)) {
             const float2 o = __ffma2_rn(n, make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));  // 1 - xn, 1 - en
-            bool exited = fminf(fminf(n.x, o.x), fminf(n.y, o.y)) < 0.0f;
+            // outside the square: v < 0 or 1 - v < 0 for v = xn or en, i.e. v (1 - v) < 0 (the two
+            // cannot both be negative, and no product of these magnitudes rounds to zero)
+            const float2 pr = __fmul2_rn(n, o);
+            bool exited = fminf(pr.x, pr.y) < 0.0f;
             int s = -1;
             if (!exited && Mode<FL>::bridge(P)) {
                 const float sc = __fdividef(-1.4426950408889634f, q);
@@ -882,6 +885,7 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
             const int ns = __popc(sm), nd = __popc(dm);
             qn += ns;
             qe += nd - ns;
+            // the nd ended lanes took paths next .. next + nd - 1, of which those below pend are live
             next += (uint32_t)nd;
             if ((qn | qe) >= 32) {  // both below 64
                 if (qn >= 32) drain(32);

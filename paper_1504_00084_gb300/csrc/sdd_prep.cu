@@ -119,12 +119,25 @@ __device__ __forceinline__ void prep_pack_body(const PrepParams& P, int blk, int
         const Mon4<T> rec{(T)w, (T)wx, (T)we, (T)0};
         if constexpr (sizeof(T) == 8) {
             mon[id] = rec;
-        } else {  // FP32 cell records: this node is corner (a, b, c, d) of cells (i, j), (i-1, j), (i, j-1), (i-1, j-1)
-            const int cx = P.nx - 1, cy = P.ny - 1;
-            if (i < cx && j < cy) mon[4 * ((long)j * cx + i)] = rec;
-            if (i > 0 && j < cy) mon[4 * ((long)j * cx + i - 1) + 1] = rec;
-            if (i < cx && j > 0) mon[4 * ((long)(j - 1) * cx + i) + 2] = rec;
-            if (i > 0 && j > 0) mon[4 * ((long)(j - 1) * cx + i - 1) + 3] = rec;
+        } else {  // FP32 cell records (corners clamped to the grid): every slot whose corner is this node
+            const int nx = P.nx, ny = P.ny;
+            const bool lx = i == nx - 1, ly = j == ny - 1;
+            Mon4<T>* c0 = mon + 4 * (long)id;  // cell (i, j)
+            c0[0] = rec;
+            if (lx) c0[1] = rec;
+            if (ly) c0[2] = rec;
+            if (lx && ly) c0[3] = rec;
+            if (i > 0) {
+                Mon4<T>* cl = c0 - 4;  // cell (i - 1, j)
+                cl[1] = rec;
+                if (ly) cl[3] = rec;
+            }
+            if (j > 0) {
+                Mon4<T>* cd = c0 - 4 * (long)nx;  // cell (i, j - 1)
+                cd[2] = rec;
+                if (lx) cd[3] = rec;
+                if (i > 0) cd[-4 + 3] = rec;  // cell (i - 1, j - 1)
+            }
         }
         const int ci = P.periodic ? i % (P.nx - 1) : i;
         const int cj = P.periodic ? j % (P.ny - 1) : j;
