@@ -138,7 +138,7 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -148,7 +148,18 @@ class ClockSampler:
         except OSError:
             self.p = None
 
-    def stop(self):
+    @staticmethod
+    def warm():
+        """One query before anything is timed: a fresh machine pages nvidia-smi and its driver
+        library in on first use, which must not fall inside a timed region."""
+        try:
+            subprocess.run(["nvidia-smi", "-L"], capture_output=True, timeout=60)
+        except (OSError, subprocess.SubprocessError):
+            pass
+
+    def stop(self, window=None):
+        """Median SM clock and throttle reasons of the samples taken inside window = (t0, t1)
+        (time.time() seconds; all samples when None)."""
         if self.p is None:
             return None
         self.p.terminate()
@@ -160,10 +171,19 @@ class ClockSampler:
         self.f.seek(0)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        rows = []
         for line in self.f.read().splitlines():
             c = [v.strip() for v in line.split(",")]
-            if len(c) < 9:
+            if len(c) < 10:
                 continue
+            try:
+                ts = datetime.datetime.strptime(c[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            rows.append((ts, c[1:]))
+        inside = [r for r in rows if window is None or (r[0] is not None and window[0] <= r[0] <= window[1])]
+        for _, c in inside or rows:
             try:
                 sm.append(float(c[1]))
                 mx.append(float(c[2]))
@@ -357,6 +377,7 @@ def run_ours(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    ClockSampler.warm()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -416,15 +437,18 @@ def run_ours(args):
                "d2h_bytes_per_step": nb}
         h.close()
 
+    # clocks sampled from before the timed problem's warm-up steps; only the samples inside the
+    # timed window are reported
+    sampler = ClockSampler(local)
     h = fresh_problem()
     M = h.M
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     launches0 = h.stats()["kernel_launches"]
     path_steps, mc_ms, mc_launches, paths = 0, 0.0, 0, 0
     max_se, not_reached = 0.0, 0
-    sampler = ClockSampler(local)
     barrier()
     torch.cuda.synchronize()
+    w0 = time.time()
     t0 = time.perf_counter()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -442,7 +466,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     wall = time.perf_counter() - t0
-    clocks = sampler.stop()
+    clocks = sampler.stop((w0, time.time()))
     dev_s = ev0.elapsed_time(ev1) / 1e3
     T = max(dev_s, 1e-9)
     launches = h.stats()["kernel_launches"] - launches0
