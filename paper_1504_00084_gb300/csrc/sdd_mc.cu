@@ -15,11 +15,11 @@
 // independent of scheduling and of which other problems or nodes share the launch.
 //
 // Per substep and lane: one Philox4x32-10 call keyed by the seed with counter
-// (k, p, m, n) -> Box-Muller normals (words 0, 1; FP32 angle through sincos_2pi) and the
-// bridge uniform (word 2); bilinear
-// gather of {omega, omega_xi, omega_eta} from the packed monitor (read-only cache; the
-// record of a node is one 16-byte (FP32) or 32-byte (FP64) load); Euler-Maruyama update
-// (Eq. 7); endpoint and Brownian-bridge exit tests.  Terminal values: the boundary mesh at
+// (k, p, m, n) -> Box-Muller normals (words 0, 1; FP32: log_unit, sqrt_pos2, sincos_2pi) and
+// the bridge uniform (word 2); bilinear gather of {omega, omega_xi, omega_eta} from the packed
+// monitor (read-only cache; FP32: one 64-byte cell record of the four corners, two 32-byte
+// loads; FP64: four 32-byte node records); Euler-Maruyama update (Eq. 7); endpoint and
+// Brownian-bridge exit tests.  Terminal values: the boundary mesh at
 // the exit point, or the Keys-bicubic previous mesh at the final point (Eq. 5a, Eq. 6).
 //
 // Reductions: per-lane sums of the shifted values (FP64, or Kahan-compensated FP32), a
@@ -563,8 +563,9 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
     if constexpr (RK) w = philox_hoisted(P.rk, ph, (uint32_t)k);
     else w = philox4x32_10(c, P.key0, P.key1);
     if constexpr (sizeof(T) == 4) {
-        // FP32: the operations of the generic form below in the same order and rounding, with
-        // the x and y (and paired bridge-side) work as paired FP32 instructions
+        // FP32: the generic form's steps below, with the kernel's own logarithm, square roots and
+        // sin/cos, the noise term of the update fused, and the x and y (and paired bridge-side)
+        // work as paired FP32 instructions
         const float2 u12 = __fadd2_rn(make_float2(__int_as_float((w.x >> 9) + 0x3F800000u),
                                                   __int_as_float((w.y >> 9) + 0x3F800000u)),
                                       make_float2(-0x1.fffffep-1f, -0x1.fffffep-1f));
@@ -885,7 +886,6 @@ __device__ __forceinline__ void run_task(const McParams<T>& P, const McProblem<T
             const int ns = __popc(sm), nd = __popc(dm);
             qn += ns;
             qe += nd - ns;
-            // the nd ended lanes took paths next .. next + nd - 1, of which those below pend are live
             next += (uint32_t)nd;
             if ((qn | qe) >= 32) {  // both below 64
                 if (qn >= 32) drain(32);
