@@ -618,11 +618,12 @@ __device__ __forceinline__ void solve_body(const Team<CW>& tm, const SolveParams
             break;
         }
         if (iters >= P.max_iter) break;
-        // inner relative tolerance: straight to the target in FP64, 1e-4 per sweep in FP32
+        // inner relative tolerance: straight to the target in FP64, 1e-5 per sweep in FP32 (two
+        // sweeps reach 1e-10 from the previous mesh; 1e-4 took three, 1e-6 meets FP32 stagnation)
         double tol_rel[2];
         for (int c = 0; c < 2; ++c) {
             const double cur = c == 0 ? relx : rely;
-            double t = fp64_inner ? 0.5 * P.rtol / (cur > 0 ? cur : 1.0) : 1e-4;
+            double t = fp64_inner ? 0.5 * P.rtol / (cur > 0 ? cur : 1.0) : 1e-5;
             if (fp64_inner && t < 1e-14) t = 1e-14;
             if (t > 0.5) t = 0.5;
             tol_rel[c] = t;
