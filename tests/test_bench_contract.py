@@ -36,3 +36,34 @@ def test_reference_arm_prints_one_contract_line():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_clock_sampler_reports_the_timed_window_only():
+    """The clock record reports the samples time-stamped inside the timed window (nvidia-smi's
+    timestamp column), here a clock stuck low before the window and a throttle reason after it."""
+    import datetime
+    import tempfile
+    import time
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    cs = bench.ClockSampler.__new__(bench.ClockSampler)
+    cs.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    t0 = time.time()
+    for k in range(12):
+        ts = datetime.datetime.fromtimestamp(t0 + 0.2 * k).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        mhz = 1000 if k < 3 else 2070
+        thermal = "Active" if k >= 10 else "Not Active"
+        cs.f.write(f"{ts}, 0, {mhz}, 2070, 500.0, 0x0, Not Active, {thermal}, Not Active, Not Active\n")
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            pass
+
+    cs.p = _Done()
+    c = cs.stop((t0 + 0.5, t0 + 1.9))
+    assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 7}
