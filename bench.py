@@ -90,6 +90,9 @@ def parse():
                     help="serve: also step the first K requests one at a time in plain FP64 (same SE target)")
     ap.add_argument("--serve-round-paths", type=int, default=1 << 27,
                     help="serve: paths per round, oldest requests first (0: all pending chunks)")
+    ap.add_argument("--split", default="problems", choices=["problems", "nodes"],
+                    help="under torchrun: one problem per rank (weak scaling, the default), or one "
+                         "problem's interface nodes split over the ranks (strong scaling)")
     ap.add_argument("--mix-n", type=int, default=64)
     ap.add_argument("--mix-batched-only", action="store_true",
                     help="mix: skip the one-at-a-time comparisons (profiling case)")
@@ -130,6 +133,28 @@ def reduce_over_ranks(dist, T, path_steps, estimates, device):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(w, op=dist.ReduceOp.SUM)
     return float(t[0]), float(w[0]), float(w[1])
+
+
+def node_ranges(M, world):
+    """Contiguous interface-node ranges [lo, hi) of a partition of [0, M) into `world` parts
+    whose sizes differ by at most one."""
+    return [(M * r // world, M * (r + 1) // world) for r in range(world)]
+
+
+def allgather_node_estimates(dist, est, ranges, rank, device):
+    """Assemble the M x 2 estimates on every rank from each rank's own range: one all-gather of
+    the full arrays, then each range taken from its owner's copy."""
+    import torch
+    if dist is None:
+        return est
+    mine = torch.as_tensor(est, dtype=torch.float64).to(device)
+    parts = [torch.empty_like(mine) for _ in ranges]
+    dist.all_gather(parts, mine)
+    out = mine.clone()
+    for r, (lo, hi) in enumerate(ranges):
+        if r != rank:
+            out[lo:hi] = parts[r][lo:hi]
+    return out.cpu().numpy()
 
 
 class ClockSampler:
@@ -846,6 +871,71 @@ def run_sweep(args):
     return 0
 
 
+def run_split_nodes(args):
+    """One problem shared by all ranks (strong scaling): each rank estimates its range of the
+    interface nodes (sdd_interface_mc_range), one all-gather assembles the M x 2 estimates, and
+    every rank takes the rest of the step (sdd_step_from_interface), so every rank holds the same
+    new mesh.  Rank 0 prints the job's estimates/s of the one problem."""
+    import numpy as np
+    import torch
+
+    import paper_1504_00084_gb300 as S
+    import workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    ClockSampler.warm()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prob = workload(args, 0)  # the same problem (same seed) on every rank
+    x0, y0 = W.identity_mesh(prob)
+    h = S.SddProblem(S.params_from(prob), x0, y0, stream=torch.cuda.current_stream())
+    h.set_monitor_analytic(prob.monitor_kind, prob.monitor_params)
+    M = h.M
+    lo, hi = node_ranges(M, world)[rank]
+    ranges = node_ranges(M, world)
+
+    def split_step():
+        est = np.zeros((M, 2))
+        h.interface_mc_range(lo, hi, est)
+        est = allgather_node_estimates(dist, est, ranges, rank, f"cuda:{local}")
+        h.step_from_interface(est)
+
+    for _ in range(args.warmup):
+        split_step()
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.time()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        split_step()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    T = time.perf_counter() - t0
+    clocks = sampler.stop((w0, time.time()))
+    T_all, _, _ = reduce_over_ranks(dist, T, 0, 0, f"cuda:{local}")
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    cfg = config_of(prob, M)
+    cfg["split"] = f"interface nodes over {world} ranks, one all-gather of M x 2 estimates per step"
+    print(json.dumps({"metric": METRIC, "value": M * args.steps / T_all, "unit": UNIT, "n_gpus": world,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T_all / args.steps,
+                      "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype":
+                      {"fp32": "f32", "fp64": "f64", "kahan": "f32"}[args.precision], "data": "synthetic",
+                      "config": cfg, "clocks": clocks, "timing": "host wall clock around the whole split step"}))
+    return 0
+
+
 def main():
     args = parse()
     if args.mc_only > 0:
@@ -858,6 +948,8 @@ def main():
         return run_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.split == "nodes":
+        return run_split_nodes(args)
     return run_ours(args)
 
 

@@ -185,6 +185,28 @@ sdd_status sdd_interface_mc(sdd_problem* p, double* est_xy, double* se_xy, int64
  * y_out (nx*ny each, nullable).  Does not advance time. */
 sdd_status sdd_subdomain_solve(sdd_problem* p, const double* iface_xy, double* x_out, double* y_out);
 
+/* A time step split by interface nodes (for a problem shared by several GPUs): the estimates of
+ * Eq. (5a) at different interface nodes are independent given the frozen monitor and mesh
+ * (Sec. 3.4: each node's paths use the counter (k, p, m, n) of their own node id m), so each
+ * part of [0, M) can be computed apart and the parts assembled.
+ *
+ * sdd_interface_mc_range: sdd_interface_mc for the nodes node_begin .. node_end - 1 only
+ * (0 <= node_begin <= node_end <= M): the same paths, estimates and standard errors those nodes
+ * get in sdd_interface_mc, bit for bit.  est_xy, se_xy (M x 2 doubles) and paths_used (M int64)
+ * are full-size arrays (nullable; host or device) of which only the range's entries are
+ * written.  SDD_ERR_INVALID_ARG for a range outside [0, M] or a problem with interface sampling
+ * (iface_stride > 1: interpolated nodes need every range's estimates); SDD_ERR_SE_NOT_REACHED as
+ * sdd_interface_mc, for the range's nodes.  Does not advance time.
+ *
+ * sdd_step_from_interface: the rest of the step sdd_step takes after its interface Monte Carlo:
+ * the subdomain solves (Sec. 3.5) with iface_xy (M x 2 doubles, host or device, required when
+ * M > 0) as the interface data, then time and the step index advance and the new mesh is
+ * written to x_out, y_out (nullable).  Given the estimates of every node (e.g. the ranges of
+ * sdd_interface_mc_range assembled), the new mesh is bitwise that of sdd_step. */
+sdd_status sdd_interface_mc_range(sdd_problem* p, int32_t node_begin, int32_t node_end, double* est_xy,
+                                  double* se_xy, int64_t* paths_used);
+sdd_status sdd_step_from_interface(sdd_problem* p, const double* iface_xy, double* x_out, double* y_out);
+
 /* One alternating step t^n -> t^{n+1} (Sec. 3.6): monitor on x^n at t^n (analytic kinds),
  * interface MC, subdomain solves, then x^n <- x^{n+1}, n <- n + 1.  x_out, y_out nullable.
  * On an invalid monitor or mesh (as sdd_interface_mc) returns SDD_ERR_INVALID_ARG and takes no

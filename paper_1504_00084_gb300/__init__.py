@@ -91,7 +91,7 @@ EXPORTS = [
     "sdd_set_monitor", "sdd_set_monitor_analytic", "sdd_interface_mc", "sdd_subdomain_solve",
     "sdd_step", "sdd_get_stats", "sdd_get_interface_nodes", "sdd_interface_layout",
     "sdd_adaptive_next_total", "sdd_get_monitor", "sdd_debug_paths", "sdd_debug_philox",
-    "sdd_debug_unit_math",
+    "sdd_debug_unit_math", "sdd_interface_mc_range", "sdd_step_from_interface",
     "sdd_status_string", "sdd_last_error", "sdd_interface_mc_noalloc",
     "sdd_batch_create", "sdd_batch_step", "sdd_batch_get_stats", "sdd_batch_destroy", "sdd_batch_tune",
     "sdd_mesh_quality",
@@ -128,6 +128,8 @@ def _load():
         "sdd_debug_paths": ([P, I32, I64, I64, P, P, P], I32),
         "sdd_debug_philox": ([P, P, I64, P], I32),
         "sdd_debug_unit_math": ([P, I64, P], I32),
+        "sdd_interface_mc_range": ([P, I32, I32, P, P, P], I32),
+        "sdd_step_from_interface": ([P, P, P, P], I32),
         "sdd_debug_bounds_violations": ([], I64),
         "sdd_interface_mc_noalloc": ([ctypes.POINTER(SddParams), P, P, P, I32, P, P, P], I32),
         "sdd_batch_create": ([P, I32, P, I32, ctypes.POINTER(P)], I32),
@@ -259,6 +261,18 @@ def sdd_interface_mc(h: int, est_xy=None, se_xy=None, paths_used=None, allow_se_
     ok = (SDD_OK, SDD_ERR_SE_NOT_REACHED) if allow_se_not_reached else (SDD_OK,)
     return _check(lib.sdd_interface_mc(h, _ptr(est_xy), _ptr(se_xy), _ptr(paths_used)),
                   "sdd_interface_mc", ok)
+
+
+def sdd_interface_mc_range(h: int, node_begin: int, node_end: int, est_xy=None, se_xy=None, paths_used=None,
+                           allow_se_not_reached=True) -> int:
+    ok = (SDD_OK, SDD_ERR_SE_NOT_REACHED) if allow_se_not_reached else (SDD_OK,)
+    return _check(lib.sdd_interface_mc_range(h, node_begin, node_end, _ptr(est_xy), _ptr(se_xy), _ptr(paths_used)),
+                  "sdd_interface_mc_range", ok)
+
+
+def sdd_step_from_interface(h: int, iface_xy, x_out=None, y_out=None) -> int:
+    return _check(lib.sdd_step_from_interface(h, _ptr(iface_xy), _ptr(x_out), _ptr(y_out)),
+                  "sdd_step_from_interface")
 
 
 def sdd_subdomain_solve(h: int, iface_xy=None, x_out=None, y_out=None) -> int:
@@ -409,6 +423,22 @@ class SddProblem:
         n = np.zeros(self.M, dtype=np.int64)
         status = sdd_interface_mc(self.h, est, se, n)
         return est, se, n, status
+
+    def interface_mc_range(self, node_begin: int, node_end: int, est=None, se=None, n=None):
+        """Interface Monte Carlo of nodes node_begin .. node_end - 1 into full-size arrays (created
+        when not given); only the range's rows are written."""
+        est = np.zeros((self.M, 2)) if est is None else est
+        se = np.zeros((self.M, 2)) if se is None else se
+        n = np.zeros(self.M, dtype=np.int64) if n is None else n
+        status = sdd_interface_mc_range(self.h, node_begin, node_end, est, se, n)
+        return est, se, n, status
+
+    def step_from_interface(self, iface):
+        x = np.zeros((self.ny, self.nx))
+        y = np.zeros((self.ny, self.nx))
+        iface = np.ascontiguousarray(iface, dtype=np.float64)
+        status = sdd_step_from_interface(self.h, iface, x, y)
+        return x, y, status
 
     def subdomain_solve(self, iface=None):
         x = np.zeros((self.ny, self.nx))

@@ -293,7 +293,9 @@ sdd_status timed_mc_round(sdd_problem* p, int slot)
     return SDD_OK;
 }
 
-sdd_status run_mc(sdd_problem* p)
+// Interface Monte Carlo of the nodes [lo, hi) (hi < 0: all M); the other nodes take no paths and
+// their outputs are not meaningful.
+sdd_status run_mc(sdd_problem* p, int lo = 0, int hi = -1)
 {
     const TraceRange trace("sdd: interface Monte Carlo");
     const int M = p->M;
@@ -314,8 +316,9 @@ sdd_status run_mc(sdd_problem* p)
     const bool adaptive = p->prm.se_target > 0;
     const int64_t n0 = p->prm.paths_per_node;
     const int64_t maxp = adaptive ? p->prm.max_paths_per_node : n0;
+    if (hi < 0) hi = M;
     SDD_CK(launch_mc_init(M, n0, maxp, p->acc, p->n_done, p->steps, p->paths_run, p->next_total, p->stream,
-                          p->n_interp > 0 ? p->iface_role : nullptr));
+                          p->n_interp > 0 ? p->iface_role : nullptr, lo, hi));
     p->launches += 1;
     int n_timed = 0;
     PlanParams PP{};
@@ -386,7 +389,7 @@ sdd_status run_mc(sdd_problem* p)
         SDD_CK(cudaEventElapsedTime(&ms, p->ev[2 * k], p->ev[2 * k + 1]));
         p->stats.mc_kernel_ms += ms;
     }
-    for (int m = 0; m < M; ++m) {
+    for (int m = lo; m < hi; ++m) {
         p->stats.path_steps += st[m];
         p->stats.paths += np[m];
         const double s = se[2 * m] > se[2 * m + 1] ? se[2 * m] : se[2 * m + 1];
@@ -449,6 +452,21 @@ sdd_status run_solve(sdd_problem* p)
     return bad ? fail(SDD_ERR_NOT_CONVERGED, "a subdomain solve reached solve_max_iter") : SDD_OK;
 }
 
+// The new mesh becomes the current one; time and the step index advance.
+sdd_status advance(sdd_problem* p, double* x_out, double* y_out)
+{
+    double* t;
+    t = p->x; p->x = p->xn; p->xn = t;
+    t = p->y; p->y = p->yn; p->yn = t;
+    p->step += 1;
+    p->have_est = false;
+    p->stats.step_index = (int32_t)p->step;
+    p->stats.t = p->prm.t0 + (double)p->step * p->prm.dt;
+    const size_t N = (size_t)p->prm.nx * p->prm.ny;
+    SDD_TRY(copy_out(p, x_out, p->x, N * 8));
+    SDD_TRY(copy_out(p, y_out, p->y, N * 8));
+    return SDD_OK;
+}
 }  // namespace
 
 // ---- Problem allocation (shared with the batch and server translation units) -------------
@@ -819,17 +837,40 @@ sdd_status sdd_step(sdd_problem* p, double* x_out, double* y_out)
     if (s_mc != SDD_OK && s_mc != SDD_ERR_SE_NOT_REACHED) return s_mc;
     const sdd_status s_sv = run_solve(p);
     if (s_sv != SDD_OK && s_sv != SDD_ERR_NOT_CONVERGED) return s_sv;
-    double* t;
-    t = p->x; p->x = p->xn; p->xn = t;
-    t = p->y; p->y = p->yn; p->yn = t;
-    p->step += 1;
-    p->have_est = false;
-    p->stats.step_index = (int32_t)p->step;
-    p->stats.t = p->prm.t0 + (double)p->step * p->prm.dt;
-    const size_t N = (size_t)p->prm.nx * p->prm.ny;
-    SDD_TRY(copy_out(p, x_out, p->x, N * 8));
-    SDD_TRY(copy_out(p, y_out, p->y, N * 8));
+    SDD_TRY(advance(p, x_out, y_out));
     if (s_mc != SDD_OK) return fail(s_mc, "max_paths_per_node reached before se_target");
+    return s_sv;
+}
+
+sdd_status sdd_interface_mc_range(sdd_problem* p, int32_t node_begin, int32_t node_end, double* est_xy,
+                                  double* se_xy, int64_t* paths_used)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    if (node_begin < 0 || node_end < node_begin || node_end > p->M)
+        return fail(SDD_ERR_INVALID_ARG, "node range outside [0, M]");
+    if (p->n_interp > 0)
+        return fail(SDD_ERR_INVALID_ARG, "interface sampling: interpolated nodes need the estimates of every range");
+    SDD_TRY(run_prep(p));
+    if (node_end == node_begin) return SDD_OK;
+    const sdd_status s = run_mc(p, node_begin, node_end);
+    if (s != SDD_OK && s != SDD_ERR_SE_NOT_REACHED) return s;
+    const size_t b = (size_t)node_begin, n = (size_t)(node_end - node_begin);
+    SDD_TRY(copy_out(p, est_xy ? est_xy + 2 * b : nullptr, p->est + 2 * b, n * 16));
+    SDD_TRY(copy_out(p, se_xy ? se_xy + 2 * b : nullptr, p->se + 2 * b, n * 16));
+    SDD_TRY(copy_out(p, paths_used ? paths_used + b : nullptr, p->n_done + b, n * 8));
+    p->have_est = false;  // the problem's own estimates cover this range only
+    return s;
+}
+
+sdd_status sdd_step_from_interface(sdd_problem* p, const double* iface_xy, double* x_out, double* y_out)
+{
+    if (!p) return fail(SDD_ERR_INVALID_ARG, "problem is NULL");
+    if (!iface_xy && p->M > 0) return fail(SDD_ERR_INVALID_ARG, "iface_xy is NULL");
+    SDD_TRY(run_prep(p));
+    if (p->M > 0) SDD_TRY(copy_in(p, p->est, iface_xy, (size_t)p->M * 16));
+    const sdd_status s_sv = run_solve(p);
+    if (s_sv != SDD_OK && s_sv != SDD_ERR_NOT_CONVERGED) return s_sv;
+    SDD_TRY(advance(p, x_out, y_out));
     return s_sv;
 }
 

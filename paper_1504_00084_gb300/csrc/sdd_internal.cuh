@@ -345,9 +345,10 @@ cudaError_t launch_scatter(int nx, int ny, int periodic, double Lx, double Ly, c
                            int M, const double* est, double* xnew, double* ynew, cudaStream_t s,
                            const double* bnd64 = nullptr);
 // role (nullable): per node, -1 = estimated by Monte Carlo, >= 0 = interpolated (never planned)
+// Nodes outside [lo, hi) (hi < 0: M) and interpolated nodes (role >= 0) are scheduled no paths.
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
                            int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s,
-                           const int32_t* role = nullptr);
+                           const int32_t* role = nullptr, int lo = 0, int hi = -1);
 cudaError_t launch_interp(const InterpRule* rules, int n, double* est, double* se, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& P, cudaStream_t s);
 template <typename T>

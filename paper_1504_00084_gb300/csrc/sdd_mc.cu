@@ -1053,7 +1053,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(const PlanParams P)
 }
 
 __global__ void mc_init_kernel(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
-                               int64_t* steps, int64_t* paths_run, int64_t* next_total, const int32_t* role)
+                               int64_t* steps, int64_t* paths_run, int64_t* next_total, const int32_t* role,
+                               int lo, int hi)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= M) return;
@@ -1061,8 +1062,8 @@ __global__ void mc_init_kernel(int M, int64_t n0, int64_t max_paths, double* acc
     n_done[m] = 0;
     steps[m] = 0;
     paths_run[m] = 0;
-    const bool interpolated = role && role[m] >= 0;
-    next_total[m] = interpolated ? 0 : (n0 < max_paths ? n0 : max_paths);
+    const bool skipped = (role && role[m] >= 0) || m < lo || m >= hi;  // interpolated, or another range's
+    next_total[m] = skipped ? 0 : (n0 < max_paths ? n0 : max_paths);
 }
 
 // Interface sampling (Sec. 3.6): interpolated nodes from the estimates of their anchors, in the
@@ -1326,10 +1327,10 @@ template int mc_max_blocks_per_sm<double>(int, bool, bool, int);
 
 cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, int64_t* n_done,
                            int64_t* steps, int64_t* paths_run, int64_t* next_total, cudaStream_t s,
-                           const int32_t* role)
+                           const int32_t* role, int lo, int hi)
 {
     mc_init_kernel<<<(M + 255) / 256, 256, 0, s>>>(M, n0, max_paths, acc, n_done, steps, paths_run,
-                                                   next_total, role);
+                                                   next_total, role, lo, hi < 0 ? M : hi);
     return cudaGetLastError();
 }
 
