@@ -76,6 +76,7 @@ struct sdd_batch {
     int32_t* blk_off_dev = nullptr;
     int total_blocks = 0;
     bool any_moving = false;
+    int mc_mode = -1;            // problem switches shared by every problem (launch_mc's batch_mode), or -1
     int32_t* h_n_active = nullptr;
     // graph
     cudaGraphExec_t graph = nullptr;
@@ -197,7 +198,7 @@ sdd_status launch_batch_mc(sdd_batch* b)
     P.node_of = b->node_of; P.p_begin = b->p_begin; P.p_count = b->p_count; P.task_off = b->task_off;
     P.n_active = b->n_active; P.task_counter = b->task_counter; P.slots = b->slots;
     P.task_paths = b->task_paths;
-    B_CK(launch_mc<T>(P, b->acc_mode, false, true, b->mc_grid, b->stream, b->tpb));
+    B_CK(launch_mc<T>(P, b->acc_mode, false, true, b->mc_grid, b->stream, b->tpb, b->mc_mode));
     return SDD_OK;
 }
 
@@ -414,6 +415,12 @@ sdd_status sdd_batch_create(sdd_problem* const* problems, int32_t n, void* strea
         }
         b->total_blocks = blk_off.back();
         e = cudaMemcpy(b->blk_off_dev, blk_off.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+        // the problem switches, when every problem shares them (the path kernel then has them compiled in)
+        for (int i = 0; i < n; ++i) {
+            const sdd_params& q = problems[i]->prm;
+            const int mode = (q.periodic ? 1 : 0) | (q.form ? 2 : 0) | (q.bb_test ? 4 : 0);
+            b->mc_mode = i == 0 ? mode : (b->mc_mode == mode ? mode : -1);
+        }
     }
     if (e == cudaSuccess && b->total_subs > 0) {
         // longest-first: subdomains by interior size, descending (ties in problem, subdomain order)

@@ -352,8 +352,10 @@ cudaError_t launch_mc_init(int M, int64_t n0, int64_t max_paths, double* acc, in
 cudaError_t launch_interp(const InterpRule* rules, int n, double* est, double* se, cudaStream_t s);
 cudaError_t launch_plan(const PlanParams& P, cudaStream_t s);
 template <typename T>
+// tpb: threads per block of batched launches (128, 256, 512); batch_mode: the problem switches
+// every problem of a batch shares (bit 0 periodic, 1 generator form, 2 bridge test), or -1
 cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s,
-                      int tpb = 256);  // tpb: threads per block of batched launches (128, 256, 512)
+                      int tpb = 256, int batch_mode = -1);
 template <typename T> int mc_max_blocks_per_sm(int acc_mode, bool debug, bool batch, int tpb = 256);
 cudaError_t launch_reduce(const ReduceParams& P, int M, cudaStream_t s);
 cudaError_t launch_output(int M, const double* acc, const int64_t* n_done, const double* shift,

@@ -947,7 +947,7 @@ __global__ void __launch_bounds__(TPB, (mc_min_blocks<T, TPB>())) mc_kernel(cons
         const int64_t pe = pb + tp < chunk_end ? pb + tp : chunk_end;
         if constexpr (BATCH) {
             const McProblem<T> R = P.probs[P.node_prob[g]];
-            run_task<T, ACC, DEBUG, false, -1>(P, R, g - R.node_offset, g, task, pb, pe, Q);
+            run_task<T, ACC, DEBUG, false, FL>(P, R, g - R.node_offset, g, task, pb, pe, Q);
         } else {
             run_task<T, ACC, DEBUG, true, FL>(P, P.prob, g, g, task, pb, pe, Q);
         }
@@ -1251,16 +1251,30 @@ void prefer_l1_for()
     prefer_l1(reinterpret_cast<const void*>(&mc_kernel<T, ACC, DEBUG, BATCH, TPB, FL>), TPB);
 }
 
-template <typename T, int TPB>
-void launch_batch_mc_kernel(const McParams<T>& P, bool kahan, int grid, cudaStream_t s)
+template <typename T, int TPB, int FL>
+void launch_batch_mc_fl(const McParams<T>& P, bool kahan, int grid, cudaStream_t s)
 {
     if (kahan) {
-        prefer_l1_for<T, kAccKahan32, false, true, TPB, -1>();
-        mc_kernel<T, kAccKahan32, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+        prefer_l1_for<T, kAccKahan32, false, true, TPB, FL>();
+        mc_kernel<T, kAccKahan32, false, true, TPB, FL><<<grid, TPB, 0, s>>>(P);
     } else {
-        prefer_l1_for<T, kAcc64, false, true, TPB, -1>();
-        mc_kernel<T, kAcc64, false, true, TPB><<<grid, TPB, 0, s>>>(P);
+        prefer_l1_for<T, kAcc64, false, true, TPB, FL>();
+        mc_kernel<T, kAcc64, false, true, TPB, FL><<<grid, TPB, 0, s>>>(P);
     }
+}
+
+// A batch whose problems all share the Dirichlet / bridge-test / generator-form-0 switches
+// (mode kModeDirichletBridge) runs the FP32 instantiation with them compiled in.
+template <typename T, int TPB>
+void launch_batch_mc_kernel(const McParams<T>& P, bool kahan, int grid, cudaStream_t s, int mode)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (mode == kModeDirichletBridge) {
+            launch_batch_mc_fl<T, TPB, kModeDirichletBridge>(P, kahan, grid, s);
+            return;
+        }
+    }
+    launch_batch_mc_fl<T, TPB, -1>(P, kahan, grid, s);
 }
 
 // Single-problem FP32 launches of the common switch settings run a kernel with them compiled in
@@ -1287,13 +1301,13 @@ void launch_single_mc(const McParams<T>& P, int grid, cudaStream_t s)
 
 template <typename T>
 cudaError_t launch_mc(const McParams<T>& P, int acc_mode, bool debug, bool batch, int grid, cudaStream_t s,
-                      int tpb)
+                      int tpb, int batch_mode)
 {
     const bool kahan = acc_mode == kAccKahan32;
     if (batch) {
-        if (tpb == 128) launch_batch_mc_kernel<T, 128>(P, kahan, grid, s);
-        else if (tpb == 512) launch_batch_mc_kernel<T, 512>(P, kahan, grid, s);
-        else launch_batch_mc_kernel<T, kMcThreads>(P, kahan, grid, s);
+        if (tpb == 128) launch_batch_mc_kernel<T, 128>(P, kahan, grid, s, batch_mode);
+        else if (tpb == 512) launch_batch_mc_kernel<T, 512>(P, kahan, grid, s, batch_mode);
+        else launch_batch_mc_kernel<T, kMcThreads>(P, kahan, grid, s, batch_mode);
     } else if (debug) {
         if (kahan) {
             prefer_l1_for<T, kAccKahan32, true, false, kMcThreads, -1>();
@@ -1320,8 +1334,8 @@ int mc_max_blocks_per_sm(int acc_mode, bool debug, bool batch, int tpb)
     return nb > 0 ? nb : 1;
 }
 
-template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, bool, int, cudaStream_t, int);
-template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, bool, int, cudaStream_t, int);
+template cudaError_t launch_mc<float>(const McParams<float>&, int, bool, bool, int, cudaStream_t, int, int);
+template cudaError_t launch_mc<double>(const McParams<double>&, int, bool, bool, int, cudaStream_t, int, int);
 template int mc_max_blocks_per_sm<float>(int, bool, bool, int);
 template int mc_max_blocks_per_sm<double>(int, bool, bool, int);
 
