@@ -414,8 +414,17 @@ sdd_status launch_round(sdd_server* s, int hw)
     P.shift = s->shift;
     P.node_of = s->node_of; P.p_begin = s->p_begin; P.p_count = s->p_count; P.task_off = s->task_off;
     P.n_active = s->n_active; P.task_counter = s->task_counter; P.slots = s->slots;
+    // the problem switches, when every running request shares them (the path kernel then has
+    // them compiled in; each request's results are the same either way)
+    int mode = -1;
+    bool first = true;
+    for (const Request* r : s->running) {
+        const int m = (r->prm.periodic ? 1 : 0) | (r->prm.form ? 2 : 0) | (r->prm.bb_test ? 4 : 0);
+        mode = first ? m : (mode == m ? m : -1);
+        first = false;
+    }
     S_CK(cudaEventRecord(s->ev_a, s->stream));
-    S_CK(launch_mc<T>(P, s->acc_mode, false, true, s->mc_grid, s->stream));
+    S_CK(launch_mc<T>(P, s->acc_mode, false, true, s->mc_grid, s->stream, 256, mode));
     S_CK(cudaEventRecord(s->ev_b, s->stream));
     ReduceParams RP{};
     RP.node_of = s->node_of; RP.p_count = s->p_count; RP.task_off = s->task_off; RP.n_active = s->n_active;
