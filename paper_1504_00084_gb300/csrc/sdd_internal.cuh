@@ -7,7 +7,8 @@
 //                 Euler-Maruyama, exit tests, terminal values, deterministic reductions,
 //                 round plan, interface-sampling interpolation
 //   sdd_solve.cu  subdomain solves (Sec. 3.5): backward Euler by multigrid-preconditioned CG with
-//                 FP64 refinement, or forward-Euler substeps; one CTA per subdomain
+//                 FP64 refinement, or forward-Euler substeps; one CTA (or a cluster of four,
+//                 for large subdomains) per subdomain
 // Host code:
 //   sdd_api.cu    the C ABI of single problems; sdd_batch.cu batches; sdd_server.cu serving;
 //                 sdd_noalloc.cu the allocation-free interface Monte Carlo

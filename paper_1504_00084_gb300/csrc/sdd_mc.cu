@@ -180,11 +180,6 @@ template <> struct Consts<double> {
     static constexpr double bridge_skip = 40.0;
 };
 
-__device__ __forceinline__ Mon4<float> load_mon(const Mon4<float>* p)
-{
-    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-    return Mon4<float>{v.x, v.y, v.z, v.w};
-}
 // Two consecutive Mon4<float> records (32 bytes, 32-byte aligned) in one read-only 256-bit load.
 __device__ __forceinline__ void ld_cell_half(const float* p, Mon4<float>& r0, Mon4<float>& r1)
 {

@@ -6,7 +6,8 @@
 //                       repeat it bit for bit.
 //   prep_pack_kernel  : finite-difference gradient of omega in the computational
 //                       coordinates (Sec. 3.4), the packed {omega, omega_xi, omega_eta}
-//                       record of every node in the path precision, and the previous mesh
+//                       records in the path precision (FP64: one per node; FP32: the four
+//                       corners of every node's cell), and the previous mesh
 //                       as a displacement from the identity.
 //   scatter kernels   : the new mesh's Dirichlet data -- physical boundary (identity) and
 //                       interface estimates with periodic offsets (Sec. 3.5).
