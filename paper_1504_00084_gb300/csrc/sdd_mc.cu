@@ -149,7 +149,8 @@ __device__ __forceinline__ float2 sqrt_pos2(float2 a)
 // Natural logarithm of a uniform u in [2^-24, 1) (the FP32 deviates of uniform_open): with
 // u = 2^e m, m in [sqrt(1/2), sqrt(2)) and f = m - 1 (exact), ln u = e ln 2 + ln(1 + f), and
 // ln(1 + f) = f + f^2 P(f) with P the degree-8 polynomial fitted to (ln(1 + f) - f) / f^2 on that
-// range (weighted least squares on Chebyshev nodes, coefficients rounded to FP32); e ln 2 is added
+// range (weighted least squares on Chebyshev nodes, coefficients rounded to FP32: fit_log_unit.py
+// beside this file prints them); e ln 2 is added
 // as e ln2_hi + (e ln2_lo + ...), ln2_hi = ln 2 rounded to FP32.  Checked over all 2^23 such
 // uniforms against the rounded FP64 logarithm: within 1 ulp, rounded correctly for 93 % of them.
 // No zero, negative, infinite or subnormal arguments (uniform_open makes none).
