@@ -41,14 +41,14 @@ OPS_PER_PATH_STEP = 158
 # Issued warp instructions per path-step of the current FP32 path kernel on the benchmarked
 # configuration (ncu, smsp__inst_executed.sum / path-steps on a full 2^19-path round); the
 # issue fraction below divides by 4 warp instructions per clock per SM.
-WARP_INST_PER_PATH_STEP = 8.75
+WARP_INST_PER_PATH_STEP = 8.61
 LANES_PER_SM_CLK, ISSUE_PER_SM_CLK, SM_MAX_MHZ = 128, 4, 2070.0
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of one path-kernel launch on this grid, from an ncu
 # capture of the current kernel on a full round (2^19 paths per node): the cold fill of the packed
 # monitor cell records (64 B per node) and mesh displacements (8 B per node), ~4.8 MB of FP32 data
 # per 257x257 grid, which does not grow with the number of paths.
-MC_TRAFFIC_BYTES_PER_LAUNCH = 4.82e6
+MC_TRAFFIC_BYTES_PER_LAUNCH = 4.80e6
 
 
 def parse():

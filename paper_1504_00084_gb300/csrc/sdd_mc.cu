@@ -591,7 +591,10 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
             const float2 pr = __fmul2_rn(n, o);
             bool exited = fminf(pr.x, pr.y) < 0.0f;
             int s = -1;
-            if (!exited && Mode<FL>::bridge(P)) {
+            // The bridge test runs on every lane, without a branch: a lane that already left by
+            // the endpoint test computes it too (its probabilities may be inf or NaN there) and
+            // ignores the result.
+            if (Mode<FL>::bridge(P)) {
                 const float sc = __fdividef(-1.4426950408889634f, q);
                 const float2 oi = __ffma2_rn(make_float2(xi, eta), make_float2(-1.0f, -1.0f), make_float2(1.0f, 1.0f));
                 const float2 a02 = __fmul2_rn(__fmul2_rn(make_float2(xi, eta), n), make_float2(sc, sc));
@@ -606,14 +609,14 @@ __device__ __forceinline__ int path_substep(const McProblem<T>& P, uint32_t m, u
                 float surv = s01.x * s01.y;
                 surv *= s23.x;
                 surv *= s23.y;
-                if (ub > surv) {
-                    exited = true;
-                    float pm = p0;
-                    s = 0;
-                    if (p1 > pm) { pm = p1; s = 1; }
-                    if (p2 > pm) { pm = p2; s = 2; }
-                    if (p3 > pm) { pm = p3; s = 3; }
-                }
+                const bool bexit = !exited && ub > surv;
+                float pm = p0;  // the side of the largest crossing probability
+                int sb = 0;
+                if (p1 > pm) { pm = p1; sb = 1; }
+                if (p2 > pm) { pm = p2; sb = 2; }
+                if (p3 > pm) { pm = p3; sb = 3; }
+                s = bexit ? sb : -1;
+                exited = exited || bexit;
             }
             if (exited) {
                 vx = n.x;
