@@ -38,6 +38,7 @@ UNIT = "interface-node estimates/s"
 # drift and diffusion (one sqrt) 5, Euler-Maruyama update 4, endpoint test 6, Brownian-bridge
 # test (distances, four exponentials, survival product, compare) 28, loop and path bookkeeping 8.
 OPS_PER_PATH_STEP = 158
+
 # Issued warp instructions per path-step of the current FP32 path kernel on the benchmarked
 # configuration (ncu, smsp__inst_executed.sum / path-steps on a full 2^19-path round); the
 # issue fraction below divides by 4 warp instructions per clock per SM.
@@ -49,6 +50,26 @@ L2_FLUSH_BYTES = 256 << 20
 # monitor cell records (64 B per node) and mesh displacements (8 B per node), ~4.8 MB of FP32 data
 # per 257x257 grid, which does not grow with the number of paths.
 MC_TRAFFIC_BYTES_PER_LAUNCH = 4.80e6
+
+
+def ops_per_path_step(prob):
+    """Algorithmic operations of a path-step for this problem's switches: a periodic path takes no
+    endpoint test (6) and no bridge test (28), and neither it nor a Dirichlet path without the
+    bridge test draws the bridge's uniform (3)."""
+    ops = OPS_PER_PATH_STEP
+    if prob.periodic:
+        ops -= 6 + 28 + 3
+    elif not prob.bb_test:
+        ops -= 28 + 3
+    return ops
+
+
+def counters_apply(prob, args):
+    """The ncu-derived constants (instructions per path-step, DRAM bytes per launch) were taken on
+    the Dirichlet front with the bridge test in the default form and Kahan sums; other switches
+    compile another kernel, for which they would be a guess."""
+    return (args.precision == "kahan" and not prob.periodic and prob.bb_test and prob.form == 0
+            and prob.bicubic and args.iface_stride <= 1)
 
 
 def parse():
@@ -507,7 +528,9 @@ def run_ours(args):
     mhz = clocks["sm_mhz"] if clocks and clocks.get("sm_mhz") else SM_MAX_MHZ
     alu_peak = sms * LANES_PER_SM_CLK * mhz * 1e6  # lane-ops/s
     ps_rate = path_steps / (mc_ms / 1e3) if mc_ms > 0 else 0.0
-    achieved = OPS_PER_PATH_STEP * ps_rate
+    ops = ops_per_path_step(prob)
+    achieved = ops * ps_rate
+    measured = counters_apply(prob, args)
     out = {"metric": METRIC, "value": est_all / T_all, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * T_all / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
@@ -520,17 +543,18 @@ def run_ours(args):
            "gpu_launches": int(launches),
            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": alu_peak / 1e12,
                         "unit": "Tops/s (32-bit lane ops)", "frac": achieved / alu_peak,
-                        "traffic": MC_TRAFFIC_BYTES_PER_LAUNCH if args.precision == "kahan" else None,
+                        "traffic": MC_TRAFFIC_BYTES_PER_LAUNCH if measured else None,
                         "traffic_unit": "bytes per launch", "kernel": "mc_kernel<float>",
-                        "ops_per_path_step": OPS_PER_PATH_STEP,
+                        "ops_per_path_step": ops,
                         "ops_basis": "algorithmic operations of a path-step, each special function once",
                         "path_steps_per_s_in_kernel": ps_rate,
                         "kernel_ms": mc_ms, "kernel_launches": mc_launches,
                         "kernel_share_of_step": (mc_ms / 1e3) / T if T > 0 else None,
                         "peak_basis": f"{sms} SMs (queried) x {LANES_PER_SM_CLK} lanes x {mhz:.0f} MHz "
                                       f"(median sampled SM clock under load)",
-                        "issue": {"warp_inst_per_path_step": WARP_INST_PER_PATH_STEP,
-                                  "frac": WARP_INST_PER_PATH_STEP * ps_rate / (sms * ISSUE_PER_SM_CLK * mhz * 1e6),
+                        "issue": {"warp_inst_per_path_step": WARP_INST_PER_PATH_STEP if measured else None,
+                                  "frac": (WARP_INST_PER_PATH_STEP * ps_rate / (sms * ISSUE_PER_SM_CLK * mhz * 1e6)
+                                           if measured else None),
                                   "basis": "issued warp instructions (ncu count of this kernel) over "
                                            "4 per clock per SM: the instruction-level fraction"}},
            "clocks": clocks, "e2e": e2e,

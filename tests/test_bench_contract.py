@@ -67,3 +67,26 @@ def test_clock_sampler_reports_the_timed_window_only():
     cs.p = _Done()
     c = cs.stop((t0 + 0.5, t0 + 1.9))
     assert c == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 7}
+
+
+def test_roofline_basis_follows_the_problem_switches():
+    """The algorithmic count drops the exit tests a path does not take (Sec. 3.4: a periodic path
+    has no boundary, and the bridge test is a switch), and the ncu-derived instruction and DRAM
+    figures are reported only for the kernel they were taken on."""
+    import argparse
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+
+    front = W.c1_front(W.PREC_FP32_KAHAN)
+    assert bench.ops_per_path_step(front) == bench.OPS_PER_PATH_STEP == 158
+    assert bench.ops_per_path_step(front.replace(bb_test=0)) == 158 - 28 - 3
+    assert bench.ops_per_path_step(front.replace(periodic=1)) == 158 - 6 - 28 - 3
+    args = argparse.Namespace(precision="kahan", iface_stride=0)
+    assert bench.counters_apply(front, args)
+    for other in (front.replace(periodic=1), front.replace(bb_test=0), front.replace(form=1),
+                  front.replace(bicubic=0)):
+        assert not bench.counters_apply(other, args)
+    assert not bench.counters_apply(front, argparse.Namespace(precision="fp64", iface_stride=0))
+    assert not bench.counters_apply(front, argparse.Namespace(precision="kahan", iface_stride=4))
