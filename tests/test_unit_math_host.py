@@ -1,8 +1,13 @@
-"""The path kernel's FP32 logarithm (log_unit in sdd_mc.cu), checked on the host: its polynomial
-coefficients are the ones fit_log_unit.py derives (a weighted least-squares fit of
-(log1p f - f) / f^2, rounded to FP32), and the kernel's sequence of operations, emulated here with
-exactly rounded FP32 fused multiply-adds, stays within 1 ulp of the logarithm over a sample of the
-uniforms the kernel draws (the GPU test checks all 2^23 of them on the device)."""
+"""The path kernel's own FP32 functions (sdd_mc.cu), checked on the host.
+
+- log_unit: its polynomial coefficients are the ones fit_log_unit.py derives (a weighted
+  least-squares fit of (log1p f - f) / f^2, rounded to FP32), and the kernel's sequence of
+  operations, emulated with exactly rounded FP32 fused multiply-adds, stays within 1 ulp of the
+  logarithm over a sample of the uniforms the kernel draws.
+- sincos_2pi: its series coefficients are (pi/2)^n / n! rounded to FP32, and the emulated steps
+  (quadrant reduction, paired series, sign bits) stay within 1 ulp of 1 of sin and cos of 2 pi u.
+
+The GPU test checks both over all 2^23 uniforms on the device."""
 import math
 import os
 import re
@@ -17,10 +22,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1504_00084_gb300", "csrc")
 
 
-def _kernel_source():
+def _kernel_source(signature="__device__ __forceinline__ float log_unit(float u)"):
     with open(os.path.join(CSRC, "sdd_mc.cu")) as f:
         src = f.read()
-    body = src[src.index("__device__ __forceinline__ float log_unit(float u)"):]
+    body = src[src.index(signature):]
     return body[:body.index("\n}\n")]
 
 
@@ -111,3 +116,60 @@ def test_emulated_kernel_logarithm_within_one_ulp():
         got = _log_unit(u)
         exact = math.log(u)
         assert abs(got - exact) <= _ulp(exact), (k, u, got, exact)
+
+
+def _sincos_coefficients():
+    """(sine, cosine) pairs of the paired Horner steps, in the order the kernel applies them."""
+    body = _kernel_source("__device__ __forceinline__ void sincos_2pi(float u, float* sn, float* cs)")
+    hexf = r"(-?0x[0-9a-fA-F.]+p[-+]?\d+)f"
+    pairs = re.findall(r"make_float2\(" + hexf + r", " + hexf + r"\)", body)
+    return [(float.fromhex(a), float.fromhex(b)) for a, b in pairs]
+
+
+def test_sincos_coefficients_are_the_taylor_series():
+    pairs = _sincos_coefficients()
+    # first pair: the leading (degree 9, degree 10) coefficients, then one pair per step down to
+    # (pi/2, -(pi/2)^2 / 2)
+    sine_deg = [9, 7, 5, 3, 1]
+    cos_deg = [10, 8, 6, 4, 2]
+    assert len(pairs) == 5
+    for (cs_, cc_), ds, dc in zip(pairs, sine_deg, cos_deg):
+        want_s = (-1) ** ((ds - 1) // 2) * (math.pi / 2) ** ds / math.factorial(ds)
+        want_c = (-1) ** (dc // 2) * (math.pi / 2) ** dc / math.factorial(dc)
+        assert cs_ == _f32(want_s) and cc_ == _f32(want_c), (ds, dc)
+
+
+def _sincos_2pi(u):
+    """The kernel's steps: t = 4u, q = rint(t), r = t - q, the two series in r, quadrant swap and
+    sign bits from q."""
+    pairs = _sincos_coefficients()
+    t = _f32(4.0 * u)
+    q = float(round(t))  # Python rounds halves to even, as rintf
+    qint = int(q)
+    r = _f32(t - q)
+    r2 = _f32(r * r)
+    x, y = pairs[0]
+    x, y = _fmaf(x, r2, pairs[1][0]), _fmaf(y, r2, pairs[1][1])
+    for a, b in pairs[2:]:
+        x, y = _fmaf(x, r2, a), _fmaf(y, r2, b)
+    x, y = _fmaf(x, r, 0.0), _fmaf(y, r2, 1.0)
+    s_, c_ = (y, x) if qint & 1 else (x, y)
+    s_ = -s_ if (qint >> 1) & 1 else s_
+    c_ = -c_ if ((qint + 1) >> 1) & 1 else c_
+    return s_, c_
+
+
+def test_emulated_kernel_sincos_within_one_ulp_of_one():
+    rng = np.random.default_rng(20150402)
+    m = list(rng.integers(0, 1 << 23, size=800))
+    # quadrant boundaries (u near k/8 and k/4) and both ends
+    for k in range(1, 8):
+        c = round(k / 8 * (1 << 23) - 0.5)
+        m += [c - 1, c, c + 1]
+    m += [0, (1 << 23) - 1]
+    tol = 2.0 ** -23
+    for k in m:
+        u = _f32(_f32(1.0 + k * 2.0 ** -23) - float.fromhex("0x1.fffffep-1"))
+        s_, c_ = _sincos_2pi(u)
+        assert abs(s_ - math.sin(2 * math.pi * u)) <= tol, (k, u, s_)
+        assert abs(c_ - math.cos(2 * math.pi * u)) <= tol, (k, u, c_)
